@@ -1,0 +1,319 @@
+"""Benchmark of the single-pulse-search hot path on one Apertif-shaped beam.
+
+One step = one 1.024 s batch (1536 channels x 12500 samples, uint8) searched
+over 2048 DM trials (0..409.4, step 0.2) and 7 boxcar widths (1..64):
+brute-force de-dispersion, then the fused boxcar + S/N + peak kernel and the
+detection reduction.  The two-step subband path (32 subbands, 64 coarse DMs)
+is timed on the same batch and reported beside it.
+
+Metric: DM-trial samples per second (n_dms * n_samples per step / step time),
+device time from CUDA events on the launching stream, inputs resident in HBM,
+four distinct input batches rotated and L2 flushed (a 256 MiB write) before
+every step, outside the timed events.  `e2e` repeats the metric through the
+host entry point (pinned host batch in, S/N table out).
+
+Multi-GPU (torchrun): independent replicas, one beam per GPU, no collective
+on the data path; value = all ranks' samples / the slowest rank's time.
+
+--impl reference times the CPU oracle (test infrastructure, never the product
+path) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DM-trial samples/s (dedisp+boxcar+SNR)"
+UNIT = "DM-trial samples/s"
+N_SM = 152
+INT32_LANES_PER_SM_CLK = 128
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-subband", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("SPS_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int, device=None) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), max=float(f[2]), power=float(f[3]), hw=f[5], hwt=f[6], swt=f[7],
+                                 cap=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        loaded = [r for r in rows if r["power"] > 200.0] or rows
+        reasons = set()
+        for r in loaded:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("cap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in loaded), "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(loaded)}
+
+
+def cpu_oracle_rate(wl, x, target_s=12.0, max_rows=None):
+    """DM-trial samples/s of the oracle (dedispersion + S/N) on a bounded row sample."""
+    import oracle
+    d = oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms)
+    probe_rows = np.arange(0, wl.dms.size, wl.dms.size // 8)[:8]
+    t0 = time.perf_counter()
+    D = oracle.dedisperse(x, d[probe_rows], wl.n_t)
+    oracle.snr(D, wl.widths)
+    per_row = (time.perf_counter() - t0) / probe_rows.size
+    n = int(max(8, min(wl.dms.size if max_rows is None else max_rows, target_s / max(per_row, 1e-6))))
+    rows = np.linspace(0, wl.dms.size - 1, n).astype(np.int64)
+    t0 = time.perf_counter()
+    D = oracle.dedisperse(x, d[rows], wl.n_t)
+    oracle.snr(D, wl.widths)
+    dt = time.perf_counter() - t0
+    return rows.size * wl.n_t / dt, dt, rows.size
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as the reference arm, on the host cores (rank 0 only)."""
+    from paper_1811_04165_gb300 import synth
+    import oracle
+    if rank != 0:
+        return
+    wl = synth.apertif_beam()
+    d = oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms)
+    x = synth.filterbank(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_t + int(d.max()), wl.seed, wl.pulses)
+    rows_per_step = 16
+    rng = np.random.Generator(np.random.PCG64(11))
+    times = []
+    for s in range(args.warmup + args.steps):
+        rows = np.sort(rng.choice(wl.dms.size, rows_per_step, replace=False))
+        t0 = time.perf_counter()
+        D = oracle.dedisperse(x, d[rows], wl.n_t)
+        oracle.snr(D, wl.widths)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    dt = sum(times)
+    value = rows_per_step * wl.n_t * len(times) / dt
+    sample = f"{rows_per_step} random DM trials x {wl.n_t} samples x {wl.channels} channels per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": workload_config(wl, "brute"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(wl, mode):
+    return {"workload": wl.name, "channels": wl.channels, "band_mhz": [wl.f_lo, wl.f_hi], "t_samp_s": wl.t_samp,
+            "samples_per_batch": wl.n_t, "dm_trials": int(wl.dms.size), "dm_step": 0.2,
+            "widths": [int(w) for w in wl.widths], "dedispersion": mode,
+            "l2": "flushed before every step (256 MiB write) + 4 rotating input batches",
+            "parallelism": "replicas (one beam per GPU)"}
+
+
+def time_path(torch, plan, xs, outs, steps, warmup, ws, flush, with_events=True):
+    """Per-step CUDA-event times (ms) of [dedisperse, snr+detect] on the current stream."""
+    import paper_1811_04165_gb300 as sps
+    st = torch.cuda.current_stream()
+    res = []
+    for s in range(warmup + steps):
+        x = xs[s % len(xs)]
+        flush.fill_(s & 0xFF)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        sps.sps_dedisperse(plan, x, outs["D"], workspace=ws, stream=st)
+        e1.record(st)
+        sps.sps_snr(plan, outs["D"], outs["snr"], outs["peak_t"], outs["peak_val"], outs["best"], stream=st)
+        e2.record(st)
+        if s >= warmup:
+            res.append((e0, e1, e2))
+    torch.cuda.synchronize()
+    return [(a.elapsed_time(b), b.elapsed_time(c)) for a, b, c in res]
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import paper_1811_04165_gb300 as sps
+    from paper_1811_04165_gb300 import synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = synth.apertif_beam(seed=2 + rank)
+    plan = sps.Plan.from_workload(wl, mode=sps.MODE_BRUTE)
+    pitch = plan.pitch
+    n_in = plan.input_samples
+    n_batches = 4
+    xs_host = [synth.filterbank(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, n_in, wl.seed + 100 * b, wl.pulses,
+                                pitch=pitch) for b in range(n_batches)]
+    xs = [torch.from_numpy(x).to(dev) for x in xs_host]
+    outs = plan.alloc_outputs()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    # ---- timed region: K steps of the brute-force path
+    barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        times = time_path(torch, plan, xs, outs, args.steps, args.warmup, None, flush)
+    barrier(world)
+    dedisp_ms = [a for a, _ in times]
+    snr_ms = [b for _, b in times]
+    step_ms = [a + b for a, b in times]
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    samples = wl.dm_trial_samples
+    value = world * samples * args.steps / total_s
+    ms_per_step = 1e3 * total_s / args.steps
+
+    # ---- roofline of the dominant kernel (brute-force de-dispersion)
+    adds = float(wl.dms.size) * wl.n_t * wl.channels
+    dd_ms = statistics.mean(dedisp_ms)
+    peak_tadd = N_SM * INT32_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = adds / (dd_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "u8_pass_kernel (brute force)", "achieved": achieved, "peak": peak_tadd,
+                "unit": "Tadd/s", "frac": achieved / peak_tadd, "traffic": None,
+                "algorithmic_adds_per_launch": adds, "ms_per_launch": dd_ms,
+                "peak_derivation": "152 SMs x 128 INT32 lanes/clk x 2070 MHz"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": workload_config(wl, "brute"),
+            "kernels_ms": {"dedisperse": dd_ms, "snr_detect": statistics.mean(snr_ms)},
+            "real_time_beams": 1024.0 / ms_per_step, "gpu_launches": 3 * args.steps,
+            "roofline": roofline, "clocks": clk.summary()}
+
+    # ---- the two-step subband path on the same batch
+    if not args.no_subband:
+        wls = synth.apertif_beam(seed=2 + rank, subband=True)
+        ps = sps.Plan.from_workload(wls)
+        ws = ps.workspace()
+        outs_s = ps.alloc_outputs()
+        ts = time_path(torch, ps, xs, outs_s, args.steps, args.warmup, ws, flush)
+        sub_ms = statistics.mean(a + b for a, b in ts)
+        line["subband"] = {"value": samples / (sub_ms * 1e-3), "unit": UNIT, "ms_per_step": sub_ms,
+                           "dedisperse_ms": statistics.mean(a for a, _ in ts),
+                           "snr_detect_ms": statistics.mean(b for _, b in ts),
+                           "subbands": 32, "coarse_dms": 64}
+
+    # ---- end to end through the host entry point
+    xh = [torch.from_numpy(x).pin_memory() for x in xs_host]
+    shp = (plan.n_widths, plan.n_dms)
+    hs = torch.empty(shp, dtype=torch.float64).pin_memory()
+    ht = torch.empty(shp, dtype=torch.int32).pin_memory()
+    hv = torch.empty(shp, dtype=torch.int32).pin_memory()
+    hb = torch.empty(4, dtype=torch.int32).pin_memory()
+    xd = torch.empty((wl.channels, pitch), dtype=torch.uint8, device=dev)
+    e2e_t = []
+    for s in range(args.warmup + args.steps):
+        flush.fill_(s & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sps.sps_search_host(plan, xh[s % n_batches], xd, outs["D"], outs["snr"], outs["peak_t"], outs["peak_val"],
+                            outs["best"], hs, ht, hv, hb)
+        if s >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_total = max_over_ranks(sum(e2e_t), world, dev)
+    line["e2e"] = {"value": world * samples * args.steps / e2e_total, "unit": UNIT,
+                   "h2d_bytes_per_step": wl.channels * pitch,
+                   "d2h_bytes_per_step": int(hs.numel() * 8 + ht.numel() * 4 + hv.numel() * 4 + 16),
+                   "ms_per_step": 1e3 * e2e_total / args.steps}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, rows = cpu_oracle_rate(wl, xs_host[0])
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{rows} of {wl.dms.size} DM trials, full batch, dedispersion + S/N, "
+                                          f"{dt:.1f} s single-threaded"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * sps.h -- C ABI of the GB300 single-pulse-search library (libsps.so).
+ *
+ * The library implements the data-parallel hot path of the AMBER single-pulse
+ * search (Mikhailov & Sclocco, "AMBER auto-tuning optimization with genetic
+ * algorithms"):
+ *   incoherent de-dispersion of a uint8 filterbank over many DM trials
+ *   (brute force, the one-step path of Sec. 5, or the two-step subband path of
+ *   Sec. 2 and its first footnote), boxcar integration over a set of widths
+ *   (the "smoothing" of Sec. 2) and per-(DM, width) S/N with peak extraction
+ *   (the S/N step of Sec. 2); beside it the paper's genetic-algorithm tuner of
+ *   all kernels' launch parameters together (Sec. 3.2), exhaustive search and
+ *   pure random search (Sec. 4).
+ *
+ * Conventions shared by every entry point:
+ *   - Status codes only; nothing is thrown across the ABI.  A failed call
+ *     leaves its outputs unspecified and records a message for
+ *     sps_last_error() (per calling thread).
+ *   - "device" pointers are CUDA global-memory addresses on the plan's device
+ *     (the device current when the plan was created); "host" pointers are CPU
+ *     memory.  The caller owns every buffer passed in; the library never frees
+ *     or retains them beyond the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device entry points enqueue asynchronously on it and do not
+ *     synchronise; results are ready when the stream has drained.
+ *   - All integer results are exact; they are bit-identical for any launch
+ *     configuration.
+ *   - A plan is immutable after sps_plan_create / sps_plan_set_config and may
+ *     be used from several streams at once, given distinct output/workspace
+ *     buffers.
+ */
+#ifndef SPS_H
+#define SPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPS_OK = 0,
+  SPS_ERR_INVALID_ARG = 1,  /* a size, pointer, alignment or ordering check failed */
+  SPS_ERR_UNSUPPORTED = 2,  /* valid request outside what the kernels implement   */
+  SPS_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed                 */
+  SPS_ERR_OOM = 4,          /* device or host allocation failed                     */
+  SPS_ERR_TIMEOUT = 5,      /* a tuning evaluation exceeded its time limit          */
+  SPS_ERR_NO_DEVICE = 6     /* no CUDA device is visible                            */
+} sps_status;
+
+enum { SPS_MODE_BRUTE = 0, SPS_MODE_SUBBAND = 1 };
+
+typedef struct sps_plan sps_plan; /* opaque */
+
+/* Survey description (Table 2 analogue).
+ * Channel c (0 = lowest frequency) is centred at f_lo + (c + 1/2)(f_hi - f_lo)/channels.
+ * The dispersion delay of channel c at trial DM is
+ *   d = round_half_away(DM * 4.148808e3 * (f_c^-2 - f_top^-2) / t_samp)  samples,
+ * f_top = the top channel's centre; the DM list must be ascending and >= 0.
+ * SUBBAND mode (Sec. 2, first footnote): n_subbands divides channels, subband s
+ * holds channels [s*C/S, (s+1)*C/S) with its top channel as reference;
+ *   step one shifts channels inside a subband with the coarse DM of the trial,
+ *   step two shifts subbands with the full trial DM.
+ * coarse_dms (ascending) lists the step-one DMs; coarse_of[i] (non-decreasing,
+ * < n_coarse) maps trial i to its coarse DM, NULL = i / (n_dms / n_coarse). */
+typedef struct {
+  int32_t channels;
+  double f_lo_mhz;
+  double f_hi_mhz;
+  double t_samp_s;
+  int32_t n_samples;        /* N_t: output samples per batch                       */
+  const double* dms;        /* host, n_dms entries                                 */
+  int32_t n_dms;
+  const int32_t* widths;    /* host, ascending, 1 <= w <= n_samples                */
+  int32_t n_widths;
+  int32_t mode;             /* SPS_MODE_BRUTE or SPS_MODE_SUBBAND                  */
+  int32_t n_subbands;       /* SUBBAND only                                        */
+  const double* coarse_dms; /* SUBBAND only, host, n_coarse entries                */
+  int32_t n_coarse;
+  const int32_t* coarse_of; /* SUBBAND only, host, n_dms entries or NULL           */
+} sps_plan_desc;
+
+/* Launch and tiling parameters of one de-dispersion kernel (the Table 3 genes,
+ * re-cast for sm_103a).  Block tile = (warps_dm * dms_per_thread) DMs by
+ * (warps_time * 32 * samples_per_thread) samples; channels (or subbands) are
+ * staged through shared memory `chunk` at a time. */
+typedef struct {
+  int32_t dms_per_thread;     /* register tile along DM                            */
+  int32_t samples_per_thread; /* register tile along time (4*k for the uint8 path)  */
+  int32_t warps_dm;           /* warps of a block along DM                          */
+  int32_t warps_time;         /* warps of a block along time                        */
+  int32_t chunk;              /* channels (subbands) staged per shared-memory pass  */
+} sps_dedisp_config;
+
+/* Launch parameters of the fused boxcar + S/N kernel. */
+typedef struct {
+  int32_t threads;            /* threads per block (one block per DM row)           */
+} sps_snr_config;
+
+typedef struct {
+  sps_dedisp_config brute;    /* one-step de-dispersion                             */
+  sps_dedisp_config step1;    /* subband step one                                   */
+  sps_dedisp_config step2;    /* subband step two                                   */
+  sps_snr_config snr;         /* boxcar + S/N                                       */
+} sps_kernel_config;
+
+/* ---------------------------------------------------------------- plan */
+
+/* Build a plan on the current CUDA device: channel frequencies and integer
+ * delay tables in FP64 (host), uploaded to device memory the plan owns, plus
+ * the default kernel configuration.  Copies every array of `desc`.
+ * Errors: INVALID_ARG for inconsistent sizes, unsorted DMs, widths outside
+ * [1, n_samples] or subbands not dividing channels; UNSUPPORTED when a
+ * subband holds more than 257 channels (its sums must fit 16 bits);
+ * NO_DEVICE / OOM / CUDA from device set-up. */
+sps_status sps_plan_create(const sps_plan_desc* desc, sps_plan** out);
+sps_status sps_plan_destroy(sps_plan* plan);
+
+/* N_in: input samples each channel row must hold (N_t + the largest total delay). */
+int64_t sps_plan_input_samples(const sps_plan* plan);
+/* N_1: samples per step-one row (N_t + largest step-two delay); 0 in BRUTE mode. */
+int64_t sps_plan_step1_samples(const sps_plan* plan);
+
+/* Host copy of the brute-force delay table [n_dms][channels] (BRUTE mode) or of
+ * the composed two-step table d1[k(i)][c] + d2[i][s(c)] (SUBBAND mode). */
+sps_status sps_plan_delay_table(const sps_plan* plan, int32_t* host_out);
+/* SUBBAND mode: host copies of d1 [n_coarse][channels] and d2 [n_dms][n_subbands]. */
+sps_status sps_plan_subband_tables(const sps_plan* plan, int32_t* host_d1, int32_t* host_d2);
+
+/* Bytes of device workspace sps_dedisperse / sps_search need (0 in BRUTE mode;
+ * the step-one output Y in SUBBAND mode). */
+sps_status sps_plan_workspace_bytes(const sps_plan* plan, size_t* bytes);
+
+sps_status sps_plan_get_config(const sps_plan* plan, sps_kernel_config* out);
+/* Validates every field against the device's limits before accepting it. */
+sps_status sps_plan_set_config(sps_plan* plan, const sps_kernel_config* cfg);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* De-dispersion (Sec. 1 "shift and integration of frequency channels"):
+ *   D[i][t] = sum_c x[c][t + d(i, c)],  0 <= t < N_t,  i < n_dms,
+ * with d the brute-force table, or, in SUBBAND mode, step one then step two.
+ * x: device, uint8 [channels][x_pitch], x_pitch >= N_in, a multiple of 16, x
+ *    16-byte aligned; samples at and beyond N_in are ignored.
+ * D: device, int32 [n_dms][N_t], 16-byte aligned.
+ * workspace: device, >= sps_plan_workspace_bytes, 16-byte aligned (may be NULL
+ *    when that is 0). */
+sps_status sps_dedisperse(const sps_plan* plan, const uint8_t* x, int64_t x_pitch, int32_t* D,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/* Subband step one alone (Sec. 2, first footnote):
+ *   Y[k][s][t] = sum_{c in s} x[c][t + d1(k, c)],  t < N_1,
+ * Y: device, uint16 [n_coarse][n_subbands][y_pitch], y_pitch = N_1 rounded up
+ * to a multiple of 8 (sps_plan_workspace_bytes covers it). */
+sps_status sps_subband_step1(const sps_plan* plan, const uint8_t* x, int64_t x_pitch, uint16_t* Y,
+                             void* stream);
+/* Subband step two alone: D[i][t] = sum_s Y[k(i)][s][t + d2(i, s)], t < N_t. */
+sps_status sps_subband_step2(const sps_plan* plan, const uint16_t* Y, int32_t* D, void* stream);
+
+/* Boxcar integration, materialised (for checking):
+ *   B[w][i][t] = sum_{u < width_w} D[i][t + u] for t <= N_t - width_w, else 0.
+ * D: device int32 [n_dms][N_t]; B: device int32 [n_widths][n_dms][N_t]. */
+sps_status sps_integrate(const sps_plan* plan, const int32_t* D, int32_t* B, void* stream);
+
+/* Fused boxcar + S/N + peak (nothing materialised).  For each width w and DM i,
+ * over the N = N_t - width + 1 valid boxcar samples B:
+ *   snr = (N*max(B) - sum B) / sqrt(N*sum B^2 - (sum B)^2),
+ * i.e. (peak - mean) / population sigma, from exact integer moments; 0 when
+ * the series is constant.  peak_t = first t with B[t] = max(B).
+ * snr: device double [n_widths][n_dms]; peak_t, peak_val: device int32, same
+ * shape.  best (may be NULL): device int32[4] = {DM index, width index,
+ * peak_t, peak_val} of the largest S/N (ties: smaller DM, then smaller width). */
+sps_status sps_snr(const sps_plan* plan, const int32_t* D, double* snr, int32_t* peak_t,
+                   int32_t* peak_val, int32_t* best, void* stream);
+
+/* The whole hot path on device buffers: sps_dedisperse then sps_snr. */
+sps_status sps_search(const sps_plan* plan, const uint8_t* x, int64_t x_pitch, int32_t* D,
+                      void* workspace, size_t workspace_bytes, double* snr, int32_t* peak_t,
+                      int32_t* peak_val, int32_t* best, void* stream);
+
+/* The whole hot path from host memory: copies x_host (pinned memory keeps the
+ * copy asynchronous) into x_dev, searches, copies snr / peak_t / peak_val /
+ * best back into host memory and waits for `stream`.  Device buffers are as
+ * for sps_search; any host output may be NULL to skip its copy. */
+sps_status sps_search_host(const sps_plan* plan, const uint8_t* x_host, int64_t x_pitch,
+                           uint8_t* x_dev, int32_t* D, void* workspace, size_t workspace_bytes,
+                           double* snr_dev, int32_t* peak_t_dev, int32_t* peak_val_dev,
+                           int32_t* best_dev, double* snr_host, int32_t* peak_t_host,
+                           int32_t* peak_val_host, int32_t* best_host, void* stream);
+
+/* ---------------------------------------------------------------- misc */
+
+const char* sps_status_string(sps_status s);
+/* Message of the last failed call on this thread ("" if none). */
+const char* sps_last_error(void);
+/* ABI version of this header (major * 100 + minor). */
+int32_t sps_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPS_H */

@@ -1,0 +1,324 @@
+"""GB300 single-pulse search: the hot path of the AMBER pipeline as hand-written
+sm_103a CUDA behind a C ABI (``include/sps.h``, ``libsps.so``).
+
+This module is a thin ctypes binding: it checks tensors and passes raw device
+pointers and the current CUDA stream to the library.  Every step of the path
+runs in the library's kernels; there is no CPU fallback, and importing the
+binding's first call fails loudly (ImportError) when ``libsps.so`` has not been
+built.
+
+Functions carry the C names (``sps_plan_create`` ... ``sps_search_host``);
+:class:`Plan` wraps a plan handle.  Shapes follow the C ABI:
+  x        uint8  [channels, pitch]   pitch >= plan.input_samples, pitch % 16 == 0
+  D        int32  [n_dms, n_samples]
+  Y        uint16 [n_coarse, n_subbands, y_pitch]   (subband step one)
+  B        int32  [n_widths, n_dms, n_samples]
+  snr      float64 [n_widths, n_dms]; peak_t, peak_val int32 [n_widths, n_dms]
+  best     int32  [4] = (DM index, width index, peak_t, peak_val)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from ._lib import SpsError, check, lib, lib_path  # noqa: F401
+
+MODE_BRUTE = 0
+MODE_SUBBAND = 1
+
+
+class DedispConfig(ctypes.Structure):
+    _fields_ = [("dms_per_thread", ctypes.c_int32), ("samples_per_thread", ctypes.c_int32),
+                ("warps_dm", ctypes.c_int32), ("warps_time", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return tuple(getattr(self, f) for f, _ in self._fields_)
+
+
+class SnrConfig(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.threads,)
+
+
+class KernelConfig(ctypes.Structure):
+    _fields_ = [("brute", DedispConfig), ("step1", DedispConfig), ("step2", DedispConfig),
+                ("snr", SnrConfig)]
+
+    def as_dict(self):
+        return {k: getattr(self, k).as_tuple() for k, _ in self._fields_}
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("channels", ctypes.c_int32), ("f_lo_mhz", ctypes.c_double),
+                ("f_hi_mhz", ctypes.c_double), ("t_samp_s", ctypes.c_double),
+                ("n_samples", ctypes.c_int32), ("dms", ctypes.c_void_p), ("n_dms", ctypes.c_int32),
+                ("widths", ctypes.c_void_p), ("n_widths", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("n_subbands", ctypes.c_int32), ("coarse_dms", ctypes.c_void_p),
+                ("n_coarse", ctypes.c_int32), ("coarse_of", ctypes.c_void_p)]
+
+
+class _Lazy:
+    """Resolves libsps.so on first use; raises ImportError if it was not built."""
+
+    def __getattr__(self, name):
+        return getattr(lib(), name)
+
+
+_L = _Lazy()
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, name, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a, dtype, name, shape=None):
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != dtype or not a.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous CPU tensor of {dtype}")
+        if shape is not None and tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name} must have shape {tuple(shape)}")
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(f"{name} must be a torch CPU tensor")
+
+
+@dataclass
+class _Arrays:  # keeps the descriptor's host arrays alive during sps_plan_create
+    dms: np.ndarray
+    widths: np.ndarray
+    coarse: np.ndarray | None
+    coarse_of: np.ndarray | None
+
+
+def sps_plan_create(channels, f_lo_mhz, f_hi_mhz, t_samp_s, n_samples, dms, widths,
+                    mode=MODE_BRUTE, n_subbands=0, coarse_dms=None, coarse_of=None):
+    arr = _Arrays(np.ascontiguousarray(dms, np.float64), np.ascontiguousarray(widths, np.int32),
+                  None if coarse_dms is None else np.ascontiguousarray(coarse_dms, np.float64),
+                  None if coarse_of is None else np.ascontiguousarray(coarse_of, np.int32))
+    d = PlanDesc()
+    d.channels, d.f_lo_mhz, d.f_hi_mhz, d.t_samp_s = int(channels), float(f_lo_mhz), float(f_hi_mhz), float(t_samp_s)
+    d.n_samples = int(n_samples)
+    d.dms, d.n_dms = arr.dms.ctypes.data, arr.dms.size
+    d.widths, d.n_widths = arr.widths.ctypes.data, arr.widths.size
+    d.mode, d.n_subbands = int(mode), int(n_subbands)
+    d.coarse_dms = arr.coarse.ctypes.data if arr.coarse is not None else None
+    d.n_coarse = arr.coarse.size if arr.coarse is not None else 0
+    d.coarse_of = arr.coarse_of.ctypes.data if arr.coarse_of is not None else None
+    h = ctypes.c_void_p()
+    check(_L.sps_plan_create(ctypes.byref(d), ctypes.byref(h)), "sps_plan_create")
+    return h
+
+
+def sps_plan_destroy(h):
+    check(_L.sps_plan_destroy(h), "sps_plan_destroy")
+
+
+def sps_dedisperse(plan, x, D, workspace=None, stream=None):
+    p = plan.handle
+    ws = _dev(workspace, workspace.dtype, "workspace") if workspace is not None else ctypes.c_void_p()
+    wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    check(_L.sps_dedisperse(p, _dev(x, _torch().uint8, "x"), ctypes.c_int64(x.shape[1]),
+                            _dev(D, _torch().int32, "D", (plan.n_dms, plan.n_samples)), ws,
+                            ctypes.c_size_t(wsb), _stream(stream)), "sps_dedisperse")
+
+
+def sps_subband_step1(plan, x, Y, stream=None):
+    check(_L.sps_subband_step1(plan.handle, _dev(x, _torch().uint8, "x"), ctypes.c_int64(x.shape[1]),
+                               _dev(Y, _torch().uint16, "Y", plan.y_shape), _stream(stream)),
+          "sps_subband_step1")
+
+
+def sps_subband_step2(plan, Y, D, stream=None):
+    check(_L.sps_subband_step2(plan.handle, _dev(Y, _torch().uint16, "Y", plan.y_shape),
+                               _dev(D, _torch().int32, "D", (plan.n_dms, plan.n_samples)),
+                               _stream(stream)), "sps_subband_step2")
+
+
+def sps_integrate(plan, D, B, stream=None):
+    check(_L.sps_integrate(plan.handle, _dev(D, _torch().int32, "D", (plan.n_dms, plan.n_samples)),
+                           _dev(B, _torch().int32, "B", (plan.n_widths, plan.n_dms, plan.n_samples)),
+                           _stream(stream)), "sps_integrate")
+
+
+def sps_snr(plan, D, snr, peak_t, peak_val, best=None, stream=None):
+    t = _torch()
+    shp = (plan.n_widths, plan.n_dms)
+    check(_L.sps_snr(plan.handle, _dev(D, t.int32, "D", (plan.n_dms, plan.n_samples)),
+                     _dev(snr, t.float64, "snr", shp), _dev(peak_t, t.int32, "peak_t", shp),
+                     _dev(peak_val, t.int32, "peak_val", shp),
+                     _dev(best, t.int32, "best", (4,)) if best is not None else ctypes.c_void_p(),
+                     _stream(stream)), "sps_snr")
+
+
+def sps_search(plan, x, D, snr, peak_t, peak_val, best=None, workspace=None, stream=None):
+    t = _torch()
+    shp = (plan.n_widths, plan.n_dms)
+    ws = _dev(workspace, workspace.dtype, "workspace") if workspace is not None else ctypes.c_void_p()
+    wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    check(_L.sps_search(plan.handle, _dev(x, t.uint8, "x"), ctypes.c_int64(x.shape[1]),
+                        _dev(D, t.int32, "D", (plan.n_dms, plan.n_samples)), ws, ctypes.c_size_t(wsb),
+                        _dev(snr, t.float64, "snr", shp), _dev(peak_t, t.int32, "peak_t", shp),
+                        _dev(peak_val, t.int32, "peak_val", shp),
+                        _dev(best, t.int32, "best", (4,)) if best is not None else ctypes.c_void_p(),
+                        _stream(stream)), "sps_search")
+
+
+def sps_search_host(plan, x_host, x_dev, D, snr_dev, peak_t_dev, peak_val_dev, best_dev,
+                    snr_host, peak_t_host, peak_val_host, best_host, workspace=None, stream=None):
+    t = _torch()
+    shp = (plan.n_widths, plan.n_dms)
+    ws = _dev(workspace, workspace.dtype, "workspace") if workspace is not None else ctypes.c_void_p()
+    wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    if tuple(x_host.shape) != tuple(x_dev.shape):
+        raise ValueError("x_host and x_dev must have the same shape")
+    check(_L.sps_search_host(
+        plan.handle, _host(x_host, t.uint8, "x_host"), ctypes.c_int64(x_dev.shape[1]),
+        _dev(x_dev, t.uint8, "x_dev"), _dev(D, t.int32, "D", (plan.n_dms, plan.n_samples)), ws,
+        ctypes.c_size_t(wsb), _dev(snr_dev, t.float64, "snr_dev", shp),
+        _dev(peak_t_dev, t.int32, "peak_t_dev", shp), _dev(peak_val_dev, t.int32, "peak_val_dev", shp),
+        _dev(best_dev, t.int32, "best_dev", (4,)), _host(snr_host, t.float64, "snr_host", shp),
+        _host(peak_t_host, t.int32, "peak_t_host", shp), _host(peak_val_host, t.int32, "peak_val_host", shp),
+        _host(best_host, t.int32, "best_host", (4,)), _stream(stream)), "sps_search_host")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Plan:
+    """A search plan (frequencies, delay tables, kernel configuration) on the current device."""
+
+    def __init__(self, channels, f_lo_mhz, f_hi_mhz, t_samp_s, n_samples, dms, widths,
+                 mode=MODE_BRUTE, n_subbands=0, coarse_dms=None, coarse_of=None):
+        self.handle = sps_plan_create(channels, f_lo_mhz, f_hi_mhz, t_samp_s, n_samples, dms, widths,
+                                      mode, n_subbands, coarse_dms, coarse_of)
+        self.channels = int(channels)
+        self.n_samples = int(n_samples)
+        self.dms = np.asarray(dms, np.float64).copy()
+        self.widths = np.asarray(widths, np.int32).copy()
+        self.n_dms = self.dms.size
+        self.n_widths = self.widths.size
+        self.mode = int(mode)
+        self.n_subbands = int(n_subbands)
+        self.n_coarse = 0 if coarse_dms is None else len(coarse_dms)
+
+    @classmethod
+    def from_workload(cls, wl, mode=None):
+        if mode is None:
+            mode = MODE_SUBBAND if wl.n_subbands else MODE_BRUTE
+        if mode == MODE_SUBBAND:
+            return cls(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_t, wl.dms, wl.widths, MODE_SUBBAND,
+                       wl.n_subbands, wl.coarse_dms)
+        return cls(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_t, wl.dms, wl.widths)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _L.sps_plan_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    @property
+    def input_samples(self) -> int:
+        return int(_L.sps_plan_input_samples(self.handle))
+
+    @property
+    def step1_samples(self) -> int:
+        return int(_L.sps_plan_step1_samples(self.handle))
+
+    @property
+    def pitch(self) -> int:
+        return (self.input_samples + 15) // 16 * 16
+
+    @property
+    def y_shape(self):
+        n1 = self.step1_samples
+        return (self.n_coarse, self.n_subbands, (n1 + 7) // 8 * 8)
+
+    @property
+    def workspace_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        check(_L.sps_plan_workspace_bytes(self.handle, ctypes.byref(n)), "sps_plan_workspace_bytes")
+        return int(n.value)
+
+    def workspace(self):
+        """A device workspace tensor of the required size (uint16 elements)."""
+        import torch
+        n = self.workspace_bytes
+        return torch.empty(max(n // 2, 8), dtype=torch.uint16, device="cuda")
+
+    def delay_table(self) -> np.ndarray:
+        out = np.empty((self.n_dms, self.channels), np.int32)
+        check(_L.sps_plan_delay_table(self.handle, out.ctypes.data), "sps_plan_delay_table")
+        return out
+
+    def subband_tables(self):
+        d1 = np.empty((self.n_coarse, self.channels), np.int32)
+        d2 = np.empty((self.n_dms, self.n_subbands), np.int32)
+        check(_L.sps_plan_subband_tables(self.handle, d1.ctypes.data, d2.ctypes.data),
+              "sps_plan_subband_tables")
+        return d1, d2
+
+    @property
+    def config(self) -> KernelConfig:
+        c = KernelConfig()
+        check(_L.sps_plan_get_config(self.handle, ctypes.byref(c)), "sps_plan_get_config")
+        return c
+
+    @config.setter
+    def config(self, c: KernelConfig):
+        check(_L.sps_plan_set_config(self.handle, ctypes.byref(c)), "sps_plan_set_config")
+
+    # convenience wrappers allocating outputs
+    def alloc_outputs(self):
+        import torch
+        shp = (self.n_widths, self.n_dms)
+        return dict(D=torch.empty((self.n_dms, self.n_samples), dtype=torch.int32, device="cuda"),
+                    snr=torch.empty(shp, dtype=torch.float64, device="cuda"),
+                    peak_t=torch.empty(shp, dtype=torch.int32, device="cuda"),
+                    peak_val=torch.empty(shp, dtype=torch.int32, device="cuda"),
+                    best=torch.empty(4, dtype=torch.int32, device="cuda"))
+
+    def search(self, x, out=None, workspace=None, stream=None):
+        out = out or self.alloc_outputs()
+        if workspace is None and self.mode == MODE_SUBBAND:
+            workspace = self.workspace()
+        sps_search(self, x, out["D"], out["snr"], out["peak_t"], out["peak_val"], out["best"],
+                   workspace=workspace, stream=stream)
+        return out
+
+
+def upload_filterbank(x_np: np.ndarray, pitch: int | None = None):
+    """Copy a host uint8 [channels, samples] array into a pitched device tensor."""
+    import torch
+    C, n = x_np.shape
+    pitch = pitch or (n + 15) // 16 * 16
+    t = torch.zeros((C, pitch), dtype=torch.uint8)
+    t[:, :n] = torch.from_numpy(np.ascontiguousarray(x_np))
+    return t.to("cuda")

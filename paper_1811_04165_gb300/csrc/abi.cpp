@@ -1,0 +1,301 @@
+// extern "C" entry points of libsps.so: argument checks, then kernel launches.
+#include <cstring>
+#include <string>
+
+#include "sps_internal.h"
+
+namespace sps {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+sps_status fail(sps_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+sps_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return SPS_ERR_CUDA;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+sps_status plan_create(const sps_plan_desc* d, sps_plan** out);
+sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg);
+
+namespace {
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+sps_status check_plan(const sps_plan* p) {
+  if (!p) return fail(SPS_ERR_INVALID_ARG, "null plan");
+  return SPS_OK;
+}
+
+sps_status check_x(const sps_plan* p, const uint8_t* x, int64_t pitch) {
+  if (!x) return fail(SPS_ERR_INVALID_ARG, "null input");
+  if (!aligned16(x)) return fail(SPS_ERR_INVALID_ARG, "input must be 16-byte aligned");
+  if (pitch < p->n_in || pitch % 16) return fail(SPS_ERR_INVALID_ARG, "x_pitch must be >= N_in and a multiple of 16");
+  return SPS_OK;
+}
+
+size_t workspace_needed(const sps_plan* p) {
+  if (p->mode != SPS_MODE_SUBBAND) return 0;
+  return (size_t)p->coarse_dms.size() * p->n_subbands * p->y_pitch * sizeof(uint16_t);
+}
+
+sps_status run_step1(const sps_plan* p, const uint8_t* x, int64_t pitch, uint16_t* Y, cudaStream_t st) {
+  U8PassArgs a{};
+  a.x = x;
+  a.pitch = pitch;
+  a.in_len = (int32_t)p->n_in;
+  a.delays = p->d_d1;
+  a.n_dm = (int32_t)p->coarse_dms.size();
+  a.channels = p->channels;
+  a.group_channels = p->channels / p->n_subbands;
+  a.n_groups = p->n_subbands;
+  a.n_out = (int32_t)p->n_1;
+  a.out_pitch = p->y_pitch;
+  a.dmax_tile = p->dmax_step1;
+  a.out = Y;
+  a.out_u16 = 1;
+  return launch_u8_pass(a, p->cfg.step1, st);
+}
+
+sps_status run_step2(const sps_plan* p, const uint16_t* Y, int32_t* D, cudaStream_t st) {
+  Step2Args a{};
+  a.y = Y;
+  a.y_pitch = p->y_pitch;
+  a.y_len = (int32_t)p->n_1;
+  a.d2 = p->d_d2;
+  a.tiles = p->d_step2_tiles;
+  a.n_tiles = p->n_step2_tiles;
+  a.n_subbands = p->n_subbands;
+  a.n_t = p->n_t;
+  a.dmax_tile = p->dmax_step2;
+  a.flush_every = p->step2_flush;
+  a.D = D;
+  return launch_step2(a, p->cfg.step2, st);
+}
+
+sps_status run_dedisperse(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
+                          size_t ws_bytes, cudaStream_t st) {
+  sps_status s = check_x(p, x, pitch);
+  if (s) return s;
+  if (!D || !aligned16(D)) return fail(SPS_ERR_INVALID_ARG, "D must be non-null and 16-byte aligned");
+  if (p->mode == SPS_MODE_BRUTE) {
+    U8PassArgs a{};
+    a.x = x;
+    a.pitch = pitch;
+    a.in_len = (int32_t)p->n_in;
+    a.delays = p->d_delays;
+    a.n_dm = (int32_t)p->dms.size();
+    a.channels = p->channels;
+    a.group_channels = p->channels;
+    a.n_groups = 1;
+    a.n_out = p->n_t;
+    a.out_pitch = p->n_t;
+    a.dmax_tile = p->dmax_brute;
+    a.out = D;
+    a.out_u16 = 0;
+    return launch_u8_pass(a, p->cfg.brute, st);
+  }
+  const size_t need = workspace_needed(p);
+  if (!ws || ws_bytes < need || !aligned16(ws))
+    return fail(SPS_ERR_INVALID_ARG, "workspace missing, too small or not 16-byte aligned");
+  s = run_step1(p, x, pitch, static_cast<uint16_t*>(ws), st);
+  if (s) return s;
+  return run_step2(p, static_cast<const uint16_t*>(ws), D, st);
+}
+
+sps_status run_snr(const sps_plan* p, const int32_t* D, double* snr, int32_t* peak_t, int32_t* peak_val,
+                   int32_t* best, cudaStream_t st) {
+  if (!D || !snr || !peak_t || !peak_val) return fail(SPS_ERR_INVALID_ARG, "null pointer");
+  SnrArgs a{};
+  a.D = D;
+  a.n_dms = (int32_t)p->dms.size();
+  a.n_t = p->n_t;
+  a.widths = p->d_widths;
+  a.n_widths = (int32_t)p->widths.size();
+  a.snr = snr;
+  a.peak_t = peak_t;
+  a.peak_val = peak_val;
+  sps_status s = launch_snr(a, p->cfg.snr, st);
+  if (s || !best) return s;
+  return launch_detect(snr, peak_t, peak_val, a.n_dms, a.n_widths, best, st);
+}
+
+}  // namespace
+}  // namespace sps
+
+using namespace sps;
+
+extern "C" {
+
+sps_status sps_plan_create(const sps_plan_desc* desc, sps_plan** out) {
+  clear_error();
+  return plan_create(desc, out);
+}
+
+sps_status sps_plan_destroy(sps_plan* p) {
+  if (!p) return SPS_OK;
+  int cur = 0;
+  bool swap = cudaGetDevice(&cur) == cudaSuccess && cur != p->device;
+  if (swap) cudaSetDevice(p->device);
+  cudaFree(p->d_delays);
+  cudaFree(p->d_d1);
+  cudaFree(p->d_d2);
+  cudaFree(p->d_widths);
+  cudaFree(p->d_step2_tiles);
+  if (swap) cudaSetDevice(cur);
+  delete p;
+  return SPS_OK;
+}
+
+int64_t sps_plan_input_samples(const sps_plan* p) { return p ? p->n_in : -1; }
+
+int64_t sps_plan_step1_samples(const sps_plan* p) { return p ? p->n_1 : -1; }
+
+sps_status sps_plan_delay_table(const sps_plan* p, int32_t* out) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  if (!out) return fail(SPS_ERR_INVALID_ARG, "null output");
+  const int32_t C = p->channels, n = (int32_t)p->dms.size();
+  if (p->mode == SPS_MODE_BRUTE) {
+    std::memcpy(out, p->delays.data(), p->delays.size() * sizeof(int32_t));
+  } else {
+    const int32_t S = p->n_subbands, per = C / S;
+    for (int32_t i = 0; i < n; i++)
+      for (int32_t c = 0; c < C; c++)
+        out[(size_t)i * C + c] = p->d1[(size_t)p->coarse_of[i] * C + c] + p->d2[(size_t)i * S + c / per];
+  }
+  return SPS_OK;
+}
+
+sps_status sps_plan_subband_tables(const sps_plan* p, int32_t* d1, int32_t* d2) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  if (p->mode != SPS_MODE_SUBBAND) return fail(SPS_ERR_INVALID_ARG, "plan is not in SUBBAND mode");
+  if (!d1 || !d2) return fail(SPS_ERR_INVALID_ARG, "null output");
+  std::memcpy(d1, p->d1.data(), p->d1.size() * sizeof(int32_t));
+  std::memcpy(d2, p->d2.data(), p->d2.size() * sizeof(int32_t));
+  return SPS_OK;
+}
+
+sps_status sps_plan_workspace_bytes(const sps_plan* p, size_t* bytes) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  if (!bytes) return fail(SPS_ERR_INVALID_ARG, "null output");
+  *bytes = workspace_needed(p);
+  return SPS_OK;
+}
+
+sps_status sps_plan_get_config(const sps_plan* p, sps_kernel_config* out) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  if (!out) return fail(SPS_ERR_INVALID_ARG, "null output");
+  *out = p->cfg;
+  return SPS_OK;
+}
+
+sps_status sps_plan_set_config(sps_plan* p, const sps_kernel_config* cfg) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  if (!cfg) return fail(SPS_ERR_INVALID_ARG, "null config");
+  return apply_config(p, *cfg);
+}
+
+sps_status sps_dedisperse(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
+                          size_t ws_bytes, void* stream) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  return run_dedisperse(p, x, pitch, D, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+sps_status sps_subband_step1(const sps_plan* p, const uint8_t* x, int64_t pitch, uint16_t* Y, void* stream) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  if (p->mode != SPS_MODE_SUBBAND) return fail(SPS_ERR_INVALID_ARG, "plan is not in SUBBAND mode");
+  if (sps_status s = check_x(p, x, pitch)) return s;
+  if (!Y || !aligned16(Y)) return fail(SPS_ERR_INVALID_ARG, "Y must be non-null and 16-byte aligned");
+  return run_step1(p, x, pitch, Y, (cudaStream_t)stream);
+}
+
+sps_status sps_subband_step2(const sps_plan* p, const uint16_t* Y, int32_t* D, void* stream) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  if (p->mode != SPS_MODE_SUBBAND) return fail(SPS_ERR_INVALID_ARG, "plan is not in SUBBAND mode");
+  if (!Y || !aligned16(Y) || !D || !aligned16(D)) return fail(SPS_ERR_INVALID_ARG, "Y and D must be 16-byte aligned");
+  return run_step2(p, Y, D, (cudaStream_t)stream);
+}
+
+sps_status sps_integrate(const sps_plan* p, const int32_t* D, int32_t* B, void* stream) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  if (!D || !B) return fail(SPS_ERR_INVALID_ARG, "null pointer");
+  return launch_integrate(D, (int32_t)p->dms.size(), p->n_t, p->d_widths, (int32_t)p->widths.size(), B,
+                          (cudaStream_t)stream);
+}
+
+sps_status sps_snr(const sps_plan* p, const int32_t* D, double* snr, int32_t* peak_t, int32_t* peak_val,
+                   int32_t* best, void* stream) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  return run_snr(p, D, snr, peak_t, peak_val, best, (cudaStream_t)stream);
+}
+
+sps_status sps_search(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
+                      size_t ws_bytes, double* snr, int32_t* peak_t, int32_t* peak_val, int32_t* best,
+                      void* stream) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  sps_status s = run_dedisperse(p, x, pitch, D, ws, ws_bytes, (cudaStream_t)stream);
+  if (s) return s;
+  return run_snr(p, D, snr, peak_t, peak_val, best, (cudaStream_t)stream);
+}
+
+sps_status sps_search_host(const sps_plan* p, const uint8_t* x_host, int64_t pitch, uint8_t* x_dev, int32_t* D,
+                           void* ws, size_t ws_bytes, double* snr_dev, int32_t* peak_t_dev,
+                           int32_t* peak_val_dev, int32_t* best_dev, double* snr_host, int32_t* peak_t_host,
+                           int32_t* peak_val_host, int32_t* best_host, void* stream) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  if (!x_host) return fail(SPS_ERR_INVALID_ARG, "null host input");
+  if (sps_status s = check_x(p, x_dev, pitch)) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n_out = (size_t)p->dms.size() * p->widths.size();
+  SPS_CUDA(cudaMemcpyAsync(x_dev, x_host, (size_t)p->channels * pitch, cudaMemcpyHostToDevice, st));
+  sps_status s = run_dedisperse(p, x_dev, pitch, D, ws, ws_bytes, st);
+  if (s) return s;
+  s = run_snr(p, D, snr_dev, peak_t_dev, peak_val_dev, best_dev, st);
+  if (s) return s;
+  if (snr_host) SPS_CUDA(cudaMemcpyAsync(snr_host, snr_dev, n_out * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (peak_t_host)
+    SPS_CUDA(cudaMemcpyAsync(peak_t_host, peak_t_dev, n_out * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (peak_val_host)
+    SPS_CUDA(cudaMemcpyAsync(peak_val_host, peak_val_dev, n_out * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (best_host && best_dev) SPS_CUDA(cudaMemcpyAsync(best_host, best_dev, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SPS_CUDA(cudaStreamSynchronize(st));
+  return SPS_OK;
+}
+
+const char* sps_status_string(sps_status s) {
+  switch (s) {
+    case SPS_OK: return "ok";
+    case SPS_ERR_INVALID_ARG: return "invalid argument";
+    case SPS_ERR_UNSUPPORTED: return "unsupported";
+    case SPS_ERR_CUDA: return "CUDA error";
+    case SPS_ERR_OOM: return "out of memory";
+    case SPS_ERR_TIMEOUT: return "timeout";
+    case SPS_ERR_NO_DEVICE: return "no device";
+  }
+  return "unknown status";
+}
+
+const char* sps_last_error(void) { return g_last_error.c_str(); }
+
+int32_t sps_abi_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,260 @@
+// Plan construction: channel frequencies, integer delay tables and sizes.
+//
+// The paper (Sec. 1) describes de-dispersion only as the shift and
+// integration of frequency channels; the delay law and its rounding are the
+// cold-plasma dispersion law evaluated in FP64 and rounded half away from zero:
+//   d(DM, c) = round(DM * k_DM * (f_c^-2 - f_top^-2) / t_samp),
+// channel centres f_c ascending, the top channel as reference.  For the
+// two-step path (Sec. 2, first footnote; Table 2 SUBBANDS, SUBBANDING_DMS,
+// DMS) the intra-subband delay uses the coarse DM and the subband's top
+// channel, the inter-subband delay the full trial DM.
+// This file must be compiled without floating-point contraction so that the
+// tables do not depend on the host architecture.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "sps_internal.h"
+
+namespace {
+
+constexpr double kDispersion = 4.148808e3;  // s MHz^2 pc^-1 cm^3
+
+double centre_mhz(double f_lo, double f_hi, int32_t channels, int32_t c) {
+  double width = (f_hi - f_lo) / (double)channels;
+  return f_lo + ((double)c + 0.5) * width;
+}
+
+// samples of delay per unit DM between frequency f and reference f_ref
+double samples_per_dm(double f, double f_ref, double t_samp) {
+  double a = 1.0 / (f * f);
+  double b = 1.0 / (f_ref * f_ref);
+  return kDispersion * (a - b) / t_samp;
+}
+
+int32_t round_delay(double dm, double k) { return (int32_t)std::llround(dm * k); }
+
+template <class T>
+sps_status upload(const std::vector<T>& h, T** d) {
+  if (h.empty()) { *d = nullptr; return SPS_OK; }
+  cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(T));
+  if (e == cudaErrorMemoryAllocation) return sps::fail(SPS_ERR_OOM, "device allocation of a plan table failed");
+  if (e != cudaSuccess) return sps::cuda_fail(e, "cudaMalloc(plan table)");
+  SPS_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SPS_OK;
+}
+
+// Largest delay spread inside any block of `tile` consecutive rows of a
+// row-major table [rows][cols] whose columns are non-decreasing down the rows.
+int32_t tile_spread(const std::vector<int32_t>& t, int32_t rows, int32_t cols, int32_t tile) {
+  int32_t best = 0;
+  for (int32_t r0 = 0; r0 < rows; r0 += tile) {
+    int32_t r1 = std::min(r0 + tile, rows) - 1;
+    for (int32_t c = 0; c < cols; c++)
+      best = std::max(best, t[(size_t)r1 * cols + c] - t[(size_t)r0 * cols + c]);
+  }
+  return best;
+}
+
+}  // namespace
+
+int64_t sps_plan::max_delay_brute() const {
+  int64_t m = 0;
+  for (int32_t v : delays) m = std::max<int64_t>(m, v);
+  return m;
+}
+
+namespace sps {
+
+sps_kernel_config default_config() {
+  sps_kernel_config c{};
+  c.brute = {4, 16, 8, 1, 16};
+  c.step1 = {4, 16, 8, 1, 16};
+  c.step2 = {4, 16, 8, 1, 8};
+  c.snr = {256};
+  return c;
+}
+
+// Recompute everything that depends on the kernel configuration.
+sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg) {
+  std::string why;
+  if (p->mode == SPS_MODE_BRUTE && !u8_config_supported(cfg.brute, &why))
+    return fail(SPS_ERR_INVALID_ARG, "brute config: " + why);
+  if (p->mode == SPS_MODE_SUBBAND) {
+    if (!u8_config_supported(cfg.step1, &why)) return fail(SPS_ERR_INVALID_ARG, "step1 config: " + why);
+    if (!step2_config_supported(cfg.step2, &why)) return fail(SPS_ERR_INVALID_ARG, "step2 config: " + why);
+  }
+  if (!snr_config_supported(cfg.snr, &why)) return fail(SPS_ERR_INVALID_ARG, "snr config: " + why);
+
+  int32_t n_dms = (int32_t)p->dms.size();
+  int32_t dmax_b = 0, dmax_1 = 0, dmax_2 = 0;
+  std::vector<int32_t> tiles;
+  if (p->mode == SPS_MODE_BRUTE) {
+    dmax_b = tile_spread(p->delays, n_dms, p->channels, cfg.brute.warps_dm * cfg.brute.dms_per_thread);
+  } else {
+    int32_t n_coarse = (int32_t)p->coarse_dms.size();
+    dmax_1 = tile_spread(p->d1, n_coarse, p->channels, cfg.step1.warps_dm * cfg.step1.dms_per_thread);
+    // step-two tiles: runs of trials sharing one coarse DM, at most Di long
+    int32_t di = cfg.step2.warps_dm * cfg.step2.dms_per_thread;
+    int32_t S = p->n_subbands;
+    for (int32_t i = 0; i < n_dms;) {
+      int32_t k = p->coarse_of[i], j = i;
+      while (j < n_dms && p->coarse_of[j] == k && j - i < di) j++;
+      tiles.push_back(k);
+      tiles.push_back(i);
+      tiles.push_back(j - i);
+      for (int32_t s = 0; s < S; s++)
+        dmax_2 = std::max(dmax_2, p->d2[(size_t)(j - 1) * S + s] - p->d2[(size_t)i * S + s]);
+      i = j;
+    }
+  }
+  int dev_max_smem = 0;
+  SPS_CUDA(cudaDeviceGetAttribute(&dev_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+  if (p->mode == SPS_MODE_BRUTE && u8_smem_bytes(cfg.brute, dmax_b) > (size_t)dev_max_smem)
+    return fail(SPS_ERR_INVALID_ARG, "brute config needs more shared memory than a block may use");
+  if (p->mode == SPS_MODE_SUBBAND) {
+    if (u8_smem_bytes(cfg.step1, dmax_1) > (size_t)dev_max_smem)
+      return fail(SPS_ERR_INVALID_ARG, "step1 config needs more shared memory than a block may use");
+    if (step2_smem_bytes(cfg.step2, dmax_2) > (size_t)dev_max_smem)
+      return fail(SPS_ERR_INVALID_ARG, "step2 config needs more shared memory than a block may use");
+  }
+  if (p->mode == SPS_MODE_SUBBAND) {
+    int32_t* dt = nullptr;
+    sps_status st = upload(tiles, &dt);
+    if (st != SPS_OK) return st;
+    if (p->d_step2_tiles) cudaFree(p->d_step2_tiles);
+    p->d_step2_tiles = dt;
+    p->n_step2_tiles = (int32_t)(tiles.size() / 3);
+    p->step2_tiles_host = tiles;
+  }
+  p->cfg = cfg;
+  p->dmax_brute = dmax_b;
+  p->dmax_step1 = dmax_1;
+  p->dmax_step2 = dmax_2;
+  return SPS_OK;
+}
+
+sps_status plan_create(const sps_plan_desc* d, sps_plan** out) {
+  if (!d || !out) return fail(SPS_ERR_INVALID_ARG, "null descriptor or output pointer");
+  *out = nullptr;
+  if (d->channels < 1) return fail(SPS_ERR_INVALID_ARG, "channels must be >= 1");
+  if (!(d->f_lo_mhz > 0.0) || !(d->f_hi_mhz > d->f_lo_mhz))
+    return fail(SPS_ERR_INVALID_ARG, "need 0 < f_lo < f_hi");
+  if (!(d->t_samp_s > 0.0)) return fail(SPS_ERR_INVALID_ARG, "t_samp must be > 0");
+  if (d->n_samples < 1) return fail(SPS_ERR_INVALID_ARG, "n_samples must be >= 1");
+  if (d->n_dms < 1 || !d->dms) return fail(SPS_ERR_INVALID_ARG, "need at least one DM");
+  if (d->n_widths < 1 || !d->widths) return fail(SPS_ERR_INVALID_ARG, "need at least one width");
+  for (int32_t i = 0; i < d->n_dms; i++) {
+    if (!(d->dms[i] >= 0.0) || !std::isfinite(d->dms[i])) return fail(SPS_ERR_INVALID_ARG, "DMs must be finite and >= 0");
+    if (i && d->dms[i] < d->dms[i - 1]) return fail(SPS_ERR_INVALID_ARG, "DMs must be ascending");
+  }
+  for (int32_t w = 0; w < d->n_widths; w++) {
+    if (d->widths[w] < 1 || d->widths[w] > d->n_samples)
+      return fail(SPS_ERR_INVALID_ARG, "widths must lie in [1, n_samples]");
+    if (w && d->widths[w] <= d->widths[w - 1]) return fail(SPS_ERR_INVALID_ARG, "widths must be strictly ascending");
+  }
+  if (d->mode != SPS_MODE_BRUTE && d->mode != SPS_MODE_SUBBAND)
+    return fail(SPS_ERR_INVALID_ARG, "unknown mode");
+
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(SPS_ERR_NO_DEVICE, "no CUDA device visible");
+  }
+
+  sps_plan* p = new (std::nothrow) sps_plan();
+  if (!p) return fail(SPS_ERR_OOM, "host allocation failed");
+  SPS_CUDA(cudaGetDevice(&p->device));
+  p->mode = d->mode;
+  p->channels = d->channels;
+  p->f_lo = d->f_lo_mhz;
+  p->f_hi = d->f_hi_mhz;
+  p->t_samp = d->t_samp_s;
+  p->n_t = d->n_samples;
+  p->dms.assign(d->dms, d->dms + d->n_dms);
+  p->widths.assign(d->widths, d->widths + d->n_widths);
+  const int32_t C = d->channels, n_dms = d->n_dms;
+  const double f_ref = centre_mhz(p->f_lo, p->f_hi, C, C - 1);
+  int64_t max_total = 0;
+
+  if (d->mode == SPS_MODE_BRUTE) {
+    p->delays.resize((size_t)n_dms * C);
+    for (int32_t c = 0; c < C; c++) {
+      double k = samples_per_dm(centre_mhz(p->f_lo, p->f_hi, C, c), f_ref, p->t_samp);
+      for (int32_t i = 0; i < n_dms; i++) p->delays[(size_t)i * C + c] = round_delay(p->dms[i], k);
+    }
+    max_total = p->max_delay_brute();
+  } else {
+    const int32_t S = d->n_subbands;
+    if (S < 1 || C % S) { delete p; return fail(SPS_ERR_INVALID_ARG, "n_subbands must divide channels"); }
+    if (C / S > 257) {
+      delete p;
+      return fail(SPS_ERR_UNSUPPORTED, "a subband may hold at most 257 channels (16-bit step-one sums)");
+    }
+    if (d->n_coarse < 1 || !d->coarse_dms) { delete p; return fail(SPS_ERR_INVALID_ARG, "need coarse DMs"); }
+    for (int32_t k = 0; k < d->n_coarse; k++) {
+      if (!(d->coarse_dms[k] >= 0.0) || (k && d->coarse_dms[k] < d->coarse_dms[k - 1])) {
+        delete p;
+        return fail(SPS_ERR_INVALID_ARG, "coarse DMs must be >= 0 and ascending");
+      }
+    }
+    p->n_subbands = S;
+    p->coarse_dms.assign(d->coarse_dms, d->coarse_dms + d->n_coarse);
+    p->coarse_of.resize(n_dms);
+    if (d->coarse_of) {
+      for (int32_t i = 0; i < n_dms; i++) {
+        int32_t k = d->coarse_of[i];
+        if (k < 0 || k >= d->n_coarse || (i && k < d->coarse_of[i - 1])) {
+          delete p;
+          return fail(SPS_ERR_INVALID_ARG, "coarse_of must be non-decreasing and < n_coarse");
+        }
+        p->coarse_of[i] = k;
+      }
+    } else {
+      if (n_dms % d->n_coarse) { delete p; return fail(SPS_ERR_INVALID_ARG, "n_coarse must divide n_dms when coarse_of is NULL"); }
+      for (int32_t i = 0; i < n_dms; i++) p->coarse_of[i] = i / (n_dms / d->n_coarse);
+    }
+    const int32_t per = C / S;
+    p->d1.resize((size_t)d->n_coarse * C);
+    p->d2.resize((size_t)n_dms * S);
+    for (int32_t c = 0; c < C; c++) {
+      int32_t s = c / per;
+      double ftop = centre_mhz(p->f_lo, p->f_hi, C, (s + 1) * per - 1);
+      double k1 = samples_per_dm(centre_mhz(p->f_lo, p->f_hi, C, c), ftop, p->t_samp);
+      for (int32_t k = 0; k < d->n_coarse; k++) p->d1[(size_t)k * C + c] = round_delay(p->coarse_dms[k], k1);
+    }
+    for (int32_t s = 0; s < S; s++) {
+      double ftop = centre_mhz(p->f_lo, p->f_hi, C, (s + 1) * per - 1);
+      double k2 = samples_per_dm(ftop, f_ref, p->t_samp);
+      for (int32_t i = 0; i < n_dms; i++) p->d2[(size_t)i * S + s] = round_delay(p->dms[i], k2);
+    }
+    int64_t m1 = 0, m2 = 0;
+    for (int32_t v : p->d1) m1 = std::max<int64_t>(m1, v);
+    for (int32_t v : p->d2) m2 = std::max<int64_t>(m2, v);
+    p->n_1 = p->n_t + m2;
+    p->y_pitch = (p->n_1 + 7) / 8 * 8;
+    max_total = m1 + m2;
+    // 16-bit step-two accumulation: subbands per flush so that the lane sum
+    // of step-one values (each <= 255 * per) stays below 65536
+    p->step2_flush = std::max<int32_t>(1, 65535 / (255 * per));
+  }
+  p->n_in = p->n_t + max_total;
+  if (p->n_in > INT32_MAX / 2) { delete p; return fail(SPS_ERR_UNSUPPORTED, "input rows too long"); }
+  int64_t max_sum = (int64_t)255 * C * p->widths.back();
+  if (max_sum > INT32_MAX) { delete p; return fail(SPS_ERR_UNSUPPORTED, "boxcar sums could exceed int32"); }
+
+  sps_status st = upload(p->widths, &p->d_widths);
+  if (st == SPS_OK) st = upload(p->delays, &p->d_delays);
+  if (st == SPS_OK) st = upload(p->d1, &p->d_d1);
+  if (st == SPS_OK) st = upload(p->d2, &p->d_d2);
+  if (st == SPS_OK) st = apply_config(p, default_config());
+  if (st != SPS_OK) {
+    sps_plan_destroy(p);
+    return st;
+  }
+  *out = p;
+  return SPS_OK;
+}
+
+}  // namespace sps

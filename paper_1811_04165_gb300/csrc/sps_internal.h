@@ -1,0 +1,122 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/sps.h"
+
+namespace sps {
+
+// Records a message for sps_last_error() and returns the status.
+sps_status fail(sps_status s, const std::string& msg);
+sps_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define SPS_CUDA(call)                                        \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return ::sps::cuda_fail(e_, #call); \
+  } while (0)
+
+// Kernel-side description of one de-dispersion pass over uint8 channels
+// (brute force, or subband step one with one output row per (coarse, subband)).
+struct U8PassArgs {
+  const uint8_t* x;        // [channels][pitch]
+  int64_t pitch;           // bytes per channel row
+  int32_t in_len;          // valid samples per row (bytes beyond read as 0)
+  const int32_t* delays;   // [n_dm][channels]
+  int32_t n_dm;            // delay-table rows
+  int32_t channels;        // total channels (delay-table row length)
+  int32_t group_channels;  // channels summed into one output row
+  int32_t n_groups;        // output rows per DM (1 for brute force)
+  int32_t n_out;           // output samples per row
+  int64_t out_pitch;       // output row pitch in elements
+  int32_t dmax_tile;       // largest delay spread inside one DM tile of this config
+  void* out;               // int32 rows (brute) or uint16 rows (step one)
+  int32_t out_u16;         // 1: write uint16 sums (step one)
+};
+
+// Step two over uint16 subband series.
+struct Step2Args {
+  const uint16_t* y;       // [n_coarse][S][y_pitch]
+  int64_t y_pitch;         // elements
+  int32_t y_len;           // valid samples per Y row (N_1)
+  const int32_t* d2;       // [n_dms][S]
+  const int32_t* tiles;    // [n_tiles][3] = {coarse k, first DM, DM count}
+  int32_t n_tiles;
+  int32_t n_subbands;
+  int32_t n_t;             // output samples per row
+  int32_t dmax_tile;       // largest step-two delay spread inside a tile
+  int32_t flush_every;     // subbands per 16-bit accumulation
+  int32_t* D;              // [n_dms][n_t]
+};
+
+struct SnrArgs {
+  const int32_t* D;        // [n_dms][n_t]
+  int32_t n_dms;
+  int32_t n_t;
+  const int32_t* widths;   // device [n_widths]
+  int32_t n_widths;
+  double* snr;             // [n_widths][n_dms]
+  int32_t* peak_t;
+  int32_t* peak_val;
+};
+
+// Kernel launchers (dedisperse.cu, snr.cu).  They validate the configuration
+// against the kernel's compiled variants and return UNSUPPORTED otherwise.
+sps_status launch_u8_pass(const U8PassArgs& a, const sps_dedisp_config& cfg, cudaStream_t st);
+sps_status launch_step2(const Step2Args& a, const sps_dedisp_config& cfg, cudaStream_t st);
+sps_status launch_snr(const SnrArgs& a, const sps_snr_config& cfg, cudaStream_t st);
+sps_status launch_integrate(const int32_t* D, int32_t n_dms, int32_t n_t, const int32_t* widths,
+                            int32_t n_widths, int32_t* B, cudaStream_t st);
+sps_status launch_detect(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
+                         int32_t n_dms, int32_t n_widths, int32_t* best, cudaStream_t st);
+bool u8_config_supported(const sps_dedisp_config& cfg, std::string* why);
+bool step2_config_supported(const sps_dedisp_config& cfg, std::string* why);
+bool snr_config_supported(const sps_snr_config& cfg, std::string* why);
+size_t u8_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
+size_t step2_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
+
+}  // namespace sps
+
+struct sps_plan {
+  int device = 0;
+  int32_t mode = SPS_MODE_BRUTE;
+  int32_t channels = 0;
+  double f_lo = 0, f_hi = 0, t_samp = 0;
+  int32_t n_t = 0;
+  std::vector<double> dms;
+  std::vector<int32_t> widths;
+  int32_t n_subbands = 0;
+  std::vector<double> coarse_dms;
+  std::vector<int32_t> coarse_of;
+
+  // host tables
+  std::vector<int32_t> delays;  // BRUTE: [n_dms][C]
+  std::vector<int32_t> d1;      // SUBBAND: [n_coarse][C]
+  std::vector<int32_t> d2;      // SUBBAND: [n_dms][S]
+  std::vector<int32_t> step2_tiles_host;
+  int64_t n_in = 0;             // input samples per channel
+  int64_t n_1 = 0;              // SUBBAND: step-one samples
+  int64_t y_pitch = 0;          // SUBBAND: elements per Y row
+  int32_t step2_flush = 1;
+
+  // device copies (owned)
+  int32_t* d_delays = nullptr;
+  int32_t* d_d1 = nullptr;
+  int32_t* d_d2 = nullptr;
+  int32_t* d_widths = nullptr;
+  int32_t* d_step2_tiles = nullptr;
+  int32_t n_step2_tiles = 0;
+
+  sps_kernel_config cfg{};
+  // delay spread of one DM tile for the current configuration
+  int32_t dmax_brute = 0, dmax_step1 = 0, dmax_step2 = 0;
+
+  int64_t max_delay_brute() const;
+};

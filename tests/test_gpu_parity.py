@@ -1,0 +1,336 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI.
+
+Integer results (D, Y, B, peak_t, peak_val, the detection) must be bit-exact;
+S/N within relative 1e-5 of the FP64 oracle (absolute 1e-9 near zero).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_04165_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SNR_RTOL = 1e-5
+SNR_ATOL = 1e-9
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _plan(lib, wl, mode=None, **kw):
+    return lib.Plan.from_workload(wl, mode=mode) if not kw else lib.Plan(**kw)
+
+
+def _x_for(plan, wl, seed=None, pulses=None):
+    n_in = plan.input_samples
+    x = synth.filterbank(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, n_in, wl.seed if seed is None else seed,
+                         wl.pulses if pulses is None else pulses, pitch=plan.pitch)
+    return x
+
+
+def _to_np(t):
+    torch = _torch()
+    if t.dtype == torch.uint16:
+        return t.view(torch.int16).cpu().numpy().view(np.uint16)
+    return t.cpu().numpy()
+
+
+def _check_snr(got_snr, got_pt, got_pv, want_snr, want_pt, want_pv):
+    assert np.array_equal(got_pt, want_pt)
+    assert np.array_equal(got_pv, want_pv)
+    err = np.abs(got_snr - want_snr)
+    assert np.all(err <= SNR_RTOL * np.abs(want_snr) + SNR_ATOL), float(err.max())
+
+
+# ----------------------------------------------------------------------------- tables
+def test_plan_tables_equal_oracle(lib):
+    wl = synth.apertif_beam()
+    p = lib.Plan.from_workload(wl)
+    want = oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms)
+    assert np.array_equal(p.delay_table(), want)
+    assert p.input_samples == wl.n_t + want.max()
+    ws = synth.apertif_beam(subband=True)
+    ps = lib.Plan.from_workload(ws)
+    d1, d2 = oracle.subband_tables(ws.f_lo, ws.f_hi, ws.channels, ws.t_samp, ws.n_subbands, ws.coarse_dms,
+                                   ws.dms)
+    g1, g2 = ps.subband_tables()
+    assert np.array_equal(g1, d1) and np.array_equal(g2, d2)
+    n_1, n_in = oracle.subband_lengths(ws.n_t, d1, d2)
+    assert (ps.step1_samples, ps.input_samples) == (n_1, n_in)
+
+
+# ----------------------------------------------------------------------------- brute force
+def test_tiny_brute_whole_path(lib):
+    torch = _torch()
+    wl = synth.tiny_brute()
+    p = lib.Plan.from_workload(wl)
+    x = _x_for(p, wl)
+    out = p.search(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    D, s, pt, pv, (bi, bw) = oracle.search_brute(x[:, :p.input_samples], wl.f_lo, wl.f_hi, wl.t_samp,
+                                                  wl.dms, wl.widths, wl.n_t)
+    assert np.array_equal(_to_np(out["D"]), D)
+    _check_snr(_to_np(out["snr"]), _to_np(out["peak_t"]), _to_np(out["peak_val"]), s, pt, pv)
+    assert _to_np(out["best"]).tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])]
+    assert (bi, int(wl.widths[bw])) == (25, 4)
+
+
+CONFIGS = [  # (dms_per_thread, samples_per_thread, warps_dm, warps_time, chunk)
+    (1, 4, 1, 1, 2), (1, 8, 2, 2, 6), (2, 4, 4, 2, 16), (2, 16, 2, 1, 32), (4, 4, 2, 2, 10),
+    (4, 8, 4, 2, 16), (4, 16, 8, 1, 16), (8, 4, 2, 4, 8), (8, 8, 1, 8, 16), (1, 32, 16, 1, 4),
+    (2, 32, 4, 1, 24),
+]
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_brute_configs_ragged(lib, cfg):
+    # 37 channels (odd, not a multiple of any chunk), 29 DMs, 1003 samples: ragged everywhere
+    torch = _torch()
+    dms = synth.dm_grid(29, 3.1)
+    p = lib.Plan(37, 1300.0, 1500.0, 65.536e-6, 1003, dms, [1, 3, 8, 50])
+    c = p.config
+    c.brute = lib.DedispConfig(*cfg)
+    p.config = c
+    x = synth.filterbank(37, 1300.0, 1500.0, 65.536e-6, p.input_samples, 99, pitch=p.pitch + 32)
+    xd = torch.from_numpy(x).cuda()
+    D = torch.full((29, 1003), -7, dtype=torch.int32, device="cuda")
+    lib.sps_dedisperse(p, xd, D)
+    torch.cuda.synchronize()
+    want = oracle.dedisperse(x, oracle.delay_table(1300.0, 1500.0, 37, 65.536e-6, dms), 1003)
+    assert np.array_equal(_to_np(D), want)
+
+
+def test_brute_saturated_and_edges(lib):
+    torch = _torch()
+    # all-255 input: every sum is 255 * C, exercising the 16-bit lanes at their limit
+    dms = synth.dm_grid(16, 5.0)
+    C = 600  # more than two 16-bit folds
+    p = lib.Plan(C, 1250.0, 1550.0, 81.92e-6, 500, dms, [1, 7])
+    x = np.full((C, p.pitch), 255, np.uint8)
+    D = torch.empty((16, 500), dtype=torch.int32, device="cuda")
+    lib.sps_dedisperse(p, torch.from_numpy(x).cuda(), D)
+    torch.cuda.synchronize()
+    assert np.all(_to_np(D) == 255 * C)
+    # a single channel, single DM, single sample
+    p1 = lib.Plan(1, 1250.0, 1550.0, 81.92e-6, 1, [0.0], [1])
+    x1 = np.zeros((1, 16), np.uint8)
+    x1[0, 0] = 201
+    D1 = torch.empty((1, 1), dtype=torch.int32, device="cuda")
+    lib.sps_dedisperse(p1, torch.from_numpy(x1).cuda(), D1)
+    torch.cuda.synchronize()
+    assert _to_np(D1).tolist() == [[201]]
+
+
+def test_apertif_brute_sampled_rows(lib):
+    """Full Apertif-shaped beam in the launch configuration the benchmark times."""
+    torch = _torch()
+    wl = synth.apertif_beam()
+    p = lib.Plan.from_workload(wl)
+    x = _x_for(p, wl)
+    out = p.search(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    D = _to_np(out["D"])
+    d = oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms)
+    rng = np.random.Generator(np.random.PCG64(7))
+    rows = np.unique(np.concatenate([[0, 1, 31, 32, 2047], rng.integers(0, 2048, 11)]))
+    want = oracle.dedisperse(x, d[rows], wl.n_t)
+    assert np.array_equal(D[rows], want)
+    # DM 0 is the plain channel sum at any size
+    assert np.array_equal(D[0], x[:, :wl.n_t].astype(np.int64).sum(axis=0))
+    s, pt, pv = oracle.snr(want, wl.widths)
+    _check_snr(_to_np(out["snr"])[:, rows], _to_np(out["peak_t"])[:, rows], _to_np(out["peak_val"])[:, rows],
+               s, pt, pv)
+    # the strongest injected pulse is the detection
+    best = _to_np(out["best"])
+    strongest = max(wl.pulses, key=lambda q: q.amp * np.sqrt(q.width))
+    assert abs(wl.dms[best[0]] - strongest.dm) <= 0.2 + 1e-9
+    assert abs(best[2] - strongest.t0) <= strongest.width
+    # the detection agrees with the oracle over a window of trials around it
+    lo, hi = max(best[0] - 8, 0), min(best[0] + 9, 2048)
+    wd = oracle.dedisperse(x, d[lo:hi], wl.n_t)
+    ws, wpt, wpv = oracle.snr(wd, wl.widths)
+    oi, ow = oracle.detect(ws)
+    assert (best[0], best[1]) == (lo + oi, ow)
+
+
+# ----------------------------------------------------------------------------- subband
+def _small_subband(S, n_dms=48, n_coarse=6, C=96, n_t=777):
+    dms = synth.dm_grid(n_dms, 1.7)
+    return synth.Workload("small-subband", C, 1250.0, 1550.0, 81.92e-6, n_t, dms,
+                          np.array([1, 2, 5], np.int32), seed=20 + S, n_subbands=S,
+                          coarse_dms=dms[::n_dms // n_coarse].copy())
+
+
+@pytest.mark.parametrize("S", [1, 2, 8, 32, 96])
+def test_subband_small_exact(lib, S):
+    torch = _torch()
+    wl = _small_subband(S)
+    p = lib.Plan.from_workload(wl)
+    x = _x_for(p, wl, pulses=[synth.Pulse(40.0, 3.0, 30.0, 300.0)])
+    xd = torch.from_numpy(x).cuda()
+    Y = torch.empty(p.y_shape, dtype=torch.uint16, device="cuda")
+    lib.sps_subband_step1(p, xd, Y)
+    D = torch.empty((wl.dms.size, wl.n_t), dtype=torch.int32, device="cuda")
+    lib.sps_subband_step2(p, Y, D)
+    D2 = torch.empty_like(D)
+    lib.sps_dedisperse(p, xd, D2, workspace=p.workspace())
+    torch.cuda.synchronize()
+    d1, d2 = oracle.subband_tables(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, S, wl.coarse_dms, wl.dms)
+    n_1, _ = oracle.subband_lengths(wl.n_t, d1, d2)
+    Yo = oracle.subband_step1(x, d1, S, n_1)
+    k = oracle.coarse_index(wl.dms.size, wl.coarse_dms.size)
+    Do = oracle.subband_step2(Yo, d2, k, wl.n_t)
+    assert np.array_equal(_to_np(Y)[:, :, :n_1].astype(np.int32), Yo)
+    assert np.array_equal(_to_np(D), Do)
+    assert np.array_equal(_to_np(D2), Do)
+    # the plan's composed table reproduces the same sums in one pass
+    assert np.array_equal(oracle.dedisperse(x, p.delay_table(), wl.n_t), Do)
+
+
+@pytest.mark.parametrize("cfg1,cfg2", [
+    ((1, 4, 1, 1, 2), (1, 4, 1, 1, 1)),
+    ((2, 8, 2, 2, 6), (2, 8, 2, 2, 3)),
+    ((4, 16, 8, 1, 16), (8, 4, 4, 2, 5)),
+    ((8, 8, 1, 4, 8), (4, 16, 2, 4, 4)),
+])
+def test_subband_configs(lib, cfg1, cfg2):
+    torch = _torch()
+    wl = _small_subband(8, n_dms=40, n_coarse=5, C=64, n_t=1001)
+    p = lib.Plan.from_workload(wl)
+    c = p.config
+    c.step1 = lib.DedispConfig(*cfg1)
+    c.step2 = lib.DedispConfig(*cfg2)
+    p.config = c
+    x = _x_for(p, wl)
+    D = torch.empty((wl.dms.size, wl.n_t), dtype=torch.int32, device="cuda")
+    lib.sps_dedisperse(p, torch.from_numpy(x).cuda(), D, workspace=p.workspace())
+    torch.cuda.synchronize()
+    assert np.array_equal(_to_np(D), oracle.dedisperse(x, p.delay_table(), wl.n_t))
+    d1, d2 = oracle.subband_tables(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, 8, wl.coarse_dms, wl.dms)
+    n_1, _ = oracle.subband_lengths(wl.n_t, d1, d2)
+    Do = oracle.subband_step2(oracle.subband_step1(x, d1, 8, n_1), d2,
+                              oracle.coarse_index(wl.dms.size, wl.coarse_dms.size), wl.n_t)
+    assert np.array_equal(_to_np(D), Do)
+
+
+def test_apertif_subband_sampled(lib):
+    torch = _torch()
+    wl = synth.apertif_beam(subband=True)
+    p = lib.Plan.from_workload(wl)
+    x = _x_for(p, wl)
+    xd = torch.from_numpy(x).cuda()
+    Y = torch.empty(p.y_shape, dtype=torch.uint16, device="cuda")
+    lib.sps_subband_step1(p, xd, Y)
+    out = p.search(xd)
+    torch.cuda.synchronize()
+    d1, d2 = oracle.subband_tables(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, 32, wl.coarse_dms, wl.dms)
+    n_1, _ = oracle.subband_lengths(wl.n_t, d1, d2)
+    ks = [0, 17, 63]
+    Yo = oracle.subband_step1(x, d1[ks], 32, n_1)
+    assert np.array_equal(_to_np(Y)[ks, :, :n_1].astype(np.int32), Yo)
+    rows = np.array([0, 5, 31, 32, 1000, 2016, 2047])
+    k = oracle.coarse_index(2048, 64)
+    Yfull = np.zeros((64, 32, n_1), np.int32)
+    need = np.unique(k[rows])
+    Yfull[need] = oracle.subband_step1(x, d1[need], 32, n_1)
+    Do = oracle.subband_step2(Yfull, d2[rows], k[rows], wl.n_t)
+    assert np.array_equal(_to_np(out["D"])[rows], Do)
+
+
+# ----------------------------------------------------------------------------- boxcar, S/N
+def test_integrate_and_snr_exact(lib):
+    torch = _torch()
+    rng = np.random.Generator(np.random.PCG64(3))
+    n_dms, n_t = 37, 2003
+    widths = [1, 2, 3, 16, 64, 2003]
+    p = lib.Plan(8, 1250.0, 1550.0, 81.92e-6, n_t, synth.dm_grid(n_dms, 1.0), widths)
+    D = rng.integers(0, 255 * 1536, (n_dms, n_t)).astype(np.int32)
+    D[3] = 7  # constant row: S/N 0
+    D[4] = 0
+    D[4, 1000] = 123456  # single spike: closed form
+    Dd = torch.from_numpy(D).cuda()
+    B = torch.empty((len(widths), n_dms, n_t), dtype=torch.int32, device="cuda")
+    lib.sps_integrate(p, Dd, B)
+    out = p.alloc_outputs()
+    lib.sps_snr(p, Dd, out["snr"], out["peak_t"], out["peak_val"], out["best"])
+    torch.cuda.synchronize()
+    Bn = _to_np(B)
+    for wi, w in enumerate(widths):
+        for i in range(n_dms):
+            want = oracle.boxcar(D[i], w)
+            assert np.array_equal(Bn[wi, i, :want.size], want)
+            assert np.all(Bn[wi, i, want.size:] == 0)
+    s, pt, pv = oracle.snr(D, widths)
+    _check_snr(_to_np(out["snr"]), _to_np(out["peak_t"]), _to_np(out["peak_val"]), s, pt, pv)
+    bi, bw = oracle.detect(s)
+    assert _to_np(out["best"]).tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])]
+    assert np.all(_to_np(out["snr"])[:, 3] == 0.0)
+
+
+@pytest.mark.parametrize("threads", [32, 96, 256, 1024])
+def test_snr_thread_counts(lib, threads):
+    torch = _torch()
+    rng = np.random.Generator(np.random.PCG64(threads))
+    n_dms, n_t = 9, 12500
+    p = lib.Plan(8, 1250.0, 1550.0, 81.92e-6, n_t, synth.dm_grid(n_dms, 1.0), [1, 2, 4, 8, 16, 32, 64])
+    c = p.config
+    c.snr = lib.SnrConfig(threads)
+    p.config = c
+    D = rng.integers(150000, 250000, (n_dms, n_t)).astype(np.int32)
+    D[:, 5000:5008] += 40000  # a burst so that maxima are distinct
+    out = p.alloc_outputs()
+    lib.sps_snr(p, torch.from_numpy(D).cuda(), out["snr"], out["peak_t"], out["peak_val"], out["best"])
+    torch.cuda.synchronize()
+    s, pt, pv = oracle.snr(D, p.widths)
+    _check_snr(_to_np(out["snr"]), _to_np(out["peak_t"]), _to_np(out["peak_val"]), s, pt, pv)
+
+
+# ----------------------------------------------------------------------------- host entry point
+def test_search_host_matches_device_path(lib):
+    torch = _torch()
+    wl = synth.tiny_brute()
+    p = lib.Plan.from_workload(wl)
+    x = _x_for(p, wl)
+    dev = p.search(torch.from_numpy(x).cuda())
+    out = p.alloc_outputs()
+    shp = (p.n_widths, p.n_dms)
+    hs = torch.empty(shp, dtype=torch.float64).pin_memory()
+    ht = torch.empty(shp, dtype=torch.int32).pin_memory()
+    hv = torch.empty(shp, dtype=torch.int32).pin_memory()
+    hb = torch.empty(4, dtype=torch.int32).pin_memory()
+    xh = torch.from_numpy(x).pin_memory()
+    xd = torch.empty_like(xh, device="cuda")
+    lib.sps_search_host(p, xh, xd, out["D"], out["snr"], out["peak_t"], out["peak_val"], out["best"],
+                        hs, ht, hv, hb)
+    torch.cuda.synchronize()
+    assert np.array_equal(hs.numpy(), _to_np(dev["snr"]))
+    assert np.array_equal(ht.numpy(), _to_np(dev["peak_t"]))
+    assert np.array_equal(hb.numpy(), _to_np(dev["best"]))
+
+
+def test_argument_errors(lib):
+    torch = _torch()
+    wl = synth.tiny_brute()
+    p = lib.Plan.from_workload(wl)
+    x = torch.zeros((wl.channels, p.pitch), dtype=torch.uint8, device="cuda")
+    D = torch.empty((wl.dms.size, wl.n_t), dtype=torch.int32, device="cuda")
+    with pytest.raises(lib.SpsError) as e:
+        lib.sps_dedisperse(p, x[:, : p.pitch - 16].contiguous(), D)
+    assert e.value.status == 1
+    xs = torch.zeros(wl.channels * p.pitch + 16, dtype=torch.uint8, device="cuda")[1:1 + wl.channels * p.pitch]
+    with pytest.raises(lib.SpsError):
+        lib.sps_dedisperse(p, xs.view(wl.channels, p.pitch), D)
+    c = p.config
+    c.brute = lib.DedispConfig(3, 4, 1, 1, 2)  # no compiled variant
+    with pytest.raises(lib.SpsError):
+        p.config = c
+    ws = synth.apertif_beam(subband=True)
+    ps = lib.Plan.from_workload(ws)
+    with pytest.raises(lib.SpsError):  # subband mode needs its workspace
+        lib.sps_dedisperse(ps, torch.zeros((ws.channels, ps.pitch), dtype=torch.uint8, device="cuda"),
+                           torch.empty((2048, ws.n_t), dtype=torch.int32, device="cuda"))
