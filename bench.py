@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-subband", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dms", type=int, default=2048,
+                    help="DM trials (fewer only for small profiling cases; bench lines use 2048)")
     return ap.parse_args()
 
 
@@ -224,6 +227,9 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = synth.apertif_beam(seed=2 + rank)
+    if args.dms != 2048:
+        wl.dms = wl.dms[:args.dms].copy()
+        wl.name += f"-first{args.dms}dm"
     plan = sps.Plan.from_workload(wl, mode=sps.MODE_BRUTE)
     pitch = plan.pitch
     n_in = plan.input_samples
@@ -267,7 +273,7 @@ def main():
             "roofline": roofline, "clocks": clk.summary()}
 
     # ---- the two-step subband path on the same batch
-    if not args.no_subband:
+    if not args.no_subband and args.dms == 2048:
         wls = synth.apertif_beam(seed=2 + rank, subband=True)
         ps = sps.Plan.from_workload(wls)
         ws = ps.workspace()
@@ -280,6 +286,10 @@ def main():
                            "subbands": 32, "coarse_dms": 64}
 
     # ---- end to end through the host entry point
+    if args.no_e2e:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     xh = [torch.from_numpy(x).pin_memory() for x in xs_host]
     shp = (plan.n_widths, plan.n_dms)
     hs = torch.empty(shp, dtype=torch.float64).pin_memory()

@@ -128,8 +128,9 @@ sps_status sps_plan_delay_table(const sps_plan* plan, int32_t* host_out);
 /* SUBBAND mode: host copies of d1 [n_coarse][channels] and d2 [n_dms][n_subbands]. */
 sps_status sps_plan_subband_tables(const sps_plan* plan, int32_t* host_d1, int32_t* host_d2);
 
-/* Bytes of device workspace sps_dedisperse / sps_search need (0 in BRUTE mode;
- * the step-one output Y in SUBBAND mode). */
+/* Bytes of device workspace sps_dedisperse / sps_search need: three copies of
+ * the batch shifted by 1, 2 and 3 samples (3 * channels * N_in rounded up to
+ * 16), plus, in SUBBAND mode, the step-one output Y. */
 sps_status sps_plan_workspace_bytes(const sps_plan* plan, size_t* bytes);
 
 sps_status sps_plan_get_config(const sps_plan* plan, sps_kernel_config* out);
@@ -144,17 +145,18 @@ sps_status sps_plan_set_config(sps_plan* plan, const sps_kernel_config* cfg);
  * x: device, uint8 [channels][x_pitch], x_pitch >= N_in, a multiple of 16, x
  *    16-byte aligned; samples at and beyond N_in are ignored.
  * D: device, int32 [n_dms][N_t], 16-byte aligned.
- * workspace: device, >= sps_plan_workspace_bytes, 16-byte aligned (may be NULL
- *    when that is 0). */
+ * workspace: device, >= sps_plan_workspace_bytes, 16-byte aligned; its
+ *    contents need not be initialised and are overwritten. */
 sps_status sps_dedisperse(const sps_plan* plan, const uint8_t* x, int64_t x_pitch, int32_t* D,
                           void* workspace, size_t workspace_bytes, void* stream);
 
 /* Subband step one alone (Sec. 2, first footnote):
  *   Y[k][s][t] = sum_{c in s} x[c][t + d1(k, c)],  t < N_1,
  * Y: device, uint16 [n_coarse][n_subbands][y_pitch], y_pitch = N_1 rounded up
- * to a multiple of 8 (sps_plan_workspace_bytes covers it). */
+ * to a multiple of 8; workspace as for sps_dedisperse (its shifted copies are
+ * used, its Y part is not). */
 sps_status sps_subband_step1(const sps_plan* plan, const uint8_t* x, int64_t x_pitch, uint16_t* Y,
-                             void* stream);
+                             void* workspace, size_t workspace_bytes, void* stream);
 /* Subband step two alone: D[i][t] = sum_s Y[k(i)][s][t + d2(i, s)], t < N_t. */
 sps_status sps_subband_step2(const sps_plan* plan, const uint16_t* Y, int32_t* D, void* stream);
 
@@ -168,6 +170,8 @@ sps_status sps_integrate(const sps_plan* plan, const int32_t* D, int32_t* B, voi
  *   snr = (N*max(B) - sum B) / sqrt(N*sum B^2 - (sum B)^2),
  * i.e. (peak - mean) / population sigma, from exact integer moments; 0 when
  * the series is constant.  peak_t = first t with B[t] = max(B).
+ * D must hold what sps_dedisperse produces for this plan: values in
+ * [0, 255 * channels]; the kernel sizes its partial sums from that bound.
  * snr: device double [n_widths][n_dms]; peak_t, peak_val: device int32, same
  * shape.  best (may be NULL): device int32[4] = {DM index, width index,
  * peak_t, peak_val} of the largest S/N (ties: smaller DM, then smaller width). */
@@ -190,6 +194,11 @@ sps_status sps_search_host(const sps_plan* plan, const uint8_t* x_host, int64_t 
                            int32_t* peak_val_host, int32_t* best_host, void* stream);
 
 /* ---------------------------------------------------------------- misc */
+
+/* Reads (synchronously) the plan's device status word, which kernels set when
+ * a bounded wait for an asynchronous copy runs out; clears it if `clear`.
+ * Returns TIMEOUT when it is non-zero. */
+sps_status sps_plan_status(const sps_plan* plan, uint32_t* host_status, int32_t clear);
 
 const char* sps_status_string(sps_status s);
 /* Message of the last failed call on this thread ("" if none). */

@@ -138,6 +138,8 @@ def sps_plan_destroy(h):
 
 def sps_dedisperse(plan, x, D, workspace=None, stream=None):
     p = plan.handle
+    if workspace is None:
+        workspace = plan.workspace()
     ws = _dev(workspace, workspace.dtype, "workspace") if workspace is not None else ctypes.c_void_p()
     wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
     check(_L.sps_dedisperse(p, _dev(x, _torch().uint8, "x"), ctypes.c_int64(x.shape[1]),
@@ -145,9 +147,13 @@ def sps_dedisperse(plan, x, D, workspace=None, stream=None):
                             ctypes.c_size_t(wsb), _stream(stream)), "sps_dedisperse")
 
 
-def sps_subband_step1(plan, x, Y, stream=None):
+def sps_subband_step1(plan, x, Y, workspace=None, stream=None):
+    if workspace is None:
+        workspace = plan.workspace()
     check(_L.sps_subband_step1(plan.handle, _dev(x, _torch().uint8, "x"), ctypes.c_int64(x.shape[1]),
-                               _dev(Y, _torch().uint16, "Y", plan.y_shape), _stream(stream)),
+                               _dev(Y, _torch().uint16, "Y", plan.y_shape),
+                               _dev(workspace, workspace.dtype, "workspace"),
+                               ctypes.c_size_t(workspace.numel() * workspace.element_size()), _stream(stream)),
           "sps_subband_step1")
 
 
@@ -175,6 +181,8 @@ def sps_snr(plan, D, snr, peak_t, peak_val, best=None, stream=None):
 
 def sps_search(plan, x, D, snr, peak_t, peak_val, best=None, workspace=None, stream=None):
     t = _torch()
+    if workspace is None:
+        workspace = plan.workspace()
     shp = (plan.n_widths, plan.n_dms)
     ws = _dev(workspace, workspace.dtype, "workspace") if workspace is not None else ctypes.c_void_p()
     wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
@@ -189,6 +197,8 @@ def sps_search(plan, x, D, snr, peak_t, peak_val, best=None, workspace=None, str
 def sps_search_host(plan, x_host, x_dev, D, snr_dev, peak_t_dev, peak_val_dev, best_dev,
                     snr_host, peak_t_host, peak_val_host, best_host, workspace=None, stream=None):
     t = _torch()
+    if workspace is None:
+        workspace = plan.workspace()
     shp = (plan.n_widths, plan.n_dms)
     ws = _dev(workspace, workspace.dtype, "workspace") if workspace is not None else ctypes.c_void_p()
     wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
@@ -268,10 +278,20 @@ class Plan:
         return int(n.value)
 
     def workspace(self):
-        """A device workspace tensor of the required size (uint16 elements)."""
+        """A device workspace tensor of the required size (cached per plan)."""
         import torch
         n = self.workspace_bytes
-        return torch.empty(max(n // 2, 8), dtype=torch.uint16, device="cuda")
+        ws = getattr(self, "_ws", None)
+        if ws is None or ws.numel() < n:
+            ws = torch.empty(max(n, 16), dtype=torch.uint8, device="cuda")
+            self._ws = ws
+        return ws
+
+    def status(self, clear: bool = True) -> int:
+        """Device status word (non-zero when a kernel's bounded wait ran out); synchronises."""
+        v = ctypes.c_uint32()
+        _L.sps_plan_status(self.handle, ctypes.byref(v), int(clear))
+        return int(v.value)
 
     def delay_table(self) -> np.ndarray:
         out = np.empty((self.n_dms, self.channels), np.int32)
@@ -307,7 +327,7 @@ class Plan:
 
     def search(self, x, out=None, workspace=None, stream=None):
         out = out or self.alloc_outputs()
-        if workspace is None and self.mode == MODE_SUBBAND:
+        if workspace is None:
             workspace = self.workspace()
         sps_search(self, x, out["D"], out["snr"], out["peak_t"], out["peak_val"], out["best"],
                    workspace=workspace, stream=stream)

@@ -25,12 +25,13 @@ SIGNATURES = {
     "sps_plan_get_config": (_I32, [_P, _P]),
     "sps_plan_set_config": (_I32, [_P, _P]),
     "sps_dedisperse": (_I32, [_P, _P, _I64, _P, _P, _SZ, _P]),
-    "sps_subband_step1": (_I32, [_P, _P, _I64, _P, _P]),
+    "sps_subband_step1": (_I32, [_P, _P, _I64, _P, _P, _SZ, _P]),
     "sps_subband_step2": (_I32, [_P, _P, _P, _P]),
     "sps_integrate": (_I32, [_P, _P, _P, _P]),
     "sps_snr": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
     "sps_search": (_I32, [_P, _P, _I64, _P, _P, _SZ, _P, _P, _P, _P, _P]),
     "sps_search_host": (_I32, [_P, _P, _I64, _P, _P, _P, _SZ, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "sps_plan_status": (_I32, [_P, _P, _I32]),
     "sps_status_string": (ctypes.c_char_p, [_I32]),
     "sps_last_error": (ctypes.c_char_p, []),
     "sps_abi_version": (_I32, []),

@@ -41,19 +41,38 @@ sps_status check_x(const sps_plan* p, const uint8_t* x, int64_t pitch) {
   return SPS_OK;
 }
 
+// Workspace layout: the three shifted copies of the batch (both modes), then,
+// in SUBBAND mode, the step-one output Y.
+size_t x4_bytes(const sps_plan* p) { return (size_t)3 * p->channels * p->pitch4; }
+
+size_t y_offset(const sps_plan* p) { return (x4_bytes(p) + 255) / 256 * 256; }
+
 size_t workspace_needed(const sps_plan* p) {
-  if (p->mode != SPS_MODE_SUBBAND) return 0;
-  return (size_t)p->coarse_dms.size() * p->n_subbands * p->y_pitch * sizeof(uint16_t);
+  if (p->mode != SPS_MODE_SUBBAND) return x4_bytes(p);
+  return y_offset(p) + (size_t)p->coarse_dms.size() * p->n_subbands * p->y_pitch * sizeof(uint16_t);
 }
 
-sps_status run_step1(const sps_plan* p, const uint8_t* x, int64_t pitch, uint16_t* Y, cudaStream_t st) {
+U8PassArgs u8_args(const sps_plan* p, const uint8_t* x, int64_t pitch, const uint8_t* x4) {
   U8PassArgs a{};
   a.x = x;
   a.pitch = pitch;
-  a.in_len = (int32_t)p->n_in;
-  a.delays = p->d_d1;
-  a.n_dm = (int32_t)p->coarse_dms.size();
+  a.x4 = x4;
+  a.pitch4 = p->pitch4;
+  a.win_limit = (int32_t)p->pitch4;
+  a.b0 = p->d_b0;
+  a.offs = p->d_offs;
   a.channels = p->channels;
+  a.status = p->d_status;
+  return a;
+}
+
+sps_status run_step1(const sps_plan* p, const uint8_t* x, int64_t pitch, uint8_t* x4, uint16_t* Y,
+                     cudaStream_t st) {
+  sps_status s = launch_expand(x, pitch, (int32_t)p->n_in, p->channels, x4, p->pitch4, st);
+  if (s) return s;
+  U8PassArgs a = u8_args(p, x, pitch, x4);
+  a.di_pad = u8_di_pad(p->cfg.step1);
+  a.n_dm = (int32_t)p->coarse_dms.size();
   a.group_channels = p->channels / p->n_subbands;
   a.n_groups = p->n_subbands;
   a.n_out = (int32_t)p->n_1;
@@ -80,19 +99,24 @@ sps_status run_step2(const sps_plan* p, const uint16_t* Y, int32_t* D, cudaStrea
   return launch_step2(a, p->cfg.step2, st);
 }
 
+sps_status check_workspace(const sps_plan* p, void* ws, size_t ws_bytes) {
+  if (!ws || ws_bytes < workspace_needed(p) || !aligned16(ws))
+    return fail(SPS_ERR_INVALID_ARG, "workspace missing, smaller than sps_plan_workspace_bytes or not 16-byte aligned");
+  return SPS_OK;
+}
+
 sps_status run_dedisperse(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
                           size_t ws_bytes, cudaStream_t st) {
   sps_status s = check_x(p, x, pitch);
   if (s) return s;
   if (!D || !aligned16(D)) return fail(SPS_ERR_INVALID_ARG, "D must be non-null and 16-byte aligned");
+  if ((s = check_workspace(p, ws, ws_bytes))) return s;
+  uint8_t* x4 = static_cast<uint8_t*>(ws);
   if (p->mode == SPS_MODE_BRUTE) {
-    U8PassArgs a{};
-    a.x = x;
-    a.pitch = pitch;
-    a.in_len = (int32_t)p->n_in;
-    a.delays = p->d_delays;
+    if ((s = launch_expand(x, pitch, (int32_t)p->n_in, p->channels, x4, p->pitch4, st))) return s;
+    U8PassArgs a = u8_args(p, x, pitch, x4);
+    a.di_pad = u8_di_pad(p->cfg.brute);
     a.n_dm = (int32_t)p->dms.size();
-    a.channels = p->channels;
     a.group_channels = p->channels;
     a.n_groups = 1;
     a.n_out = p->n_t;
@@ -102,12 +126,9 @@ sps_status run_dedisperse(const sps_plan* p, const uint8_t* x, int64_t pitch, in
     a.out_u16 = 0;
     return launch_u8_pass(a, p->cfg.brute, st);
   }
-  const size_t need = workspace_needed(p);
-  if (!ws || ws_bytes < need || !aligned16(ws))
-    return fail(SPS_ERR_INVALID_ARG, "workspace missing, too small or not 16-byte aligned");
-  s = run_step1(p, x, pitch, static_cast<uint16_t*>(ws), st);
-  if (s) return s;
-  return run_step2(p, static_cast<const uint16_t*>(ws), D, st);
+  uint16_t* Y = reinterpret_cast<uint16_t*>(x4 + y_offset(p));
+  if ((s = run_step1(p, x, pitch, x4, Y, st))) return s;
+  return run_step2(p, Y, D, st);
 }
 
 sps_status run_snr(const sps_plan* p, const int32_t* D, double* snr, int32_t* peak_t, int32_t* peak_val,
@@ -115,6 +136,8 @@ sps_status run_snr(const sps_plan* p, const int32_t* D, double* snr, int32_t* pe
   if (!D || !snr || !peak_t || !peak_val) return fail(SPS_ERR_INVALID_ARG, "null pointer");
   SnrArgs a{};
   a.D = D;
+  a.max_boxcar = (int64_t)255 * p->channels * p->widths.back();
+  a.status = p->d_status;
   a.n_dms = (int32_t)p->dms.size();
   a.n_t = p->n_t;
   a.widths = p->d_widths;
@@ -149,6 +172,9 @@ sps_status sps_plan_destroy(sps_plan* p) {
   cudaFree(p->d_d2);
   cudaFree(p->d_widths);
   cudaFree(p->d_step2_tiles);
+  cudaFree(p->d_status);
+  cudaFree(p->d_b0);
+  cudaFree(p->d_offs);
   if (swap) cudaSetDevice(cur);
   delete p;
   return SPS_OK;
@@ -214,13 +240,15 @@ sps_status sps_dedisperse(const sps_plan* p, const uint8_t* x, int64_t pitch, in
   return run_dedisperse(p, x, pitch, D, ws, ws_bytes, (cudaStream_t)stream);
 }
 
-sps_status sps_subband_step1(const sps_plan* p, const uint8_t* x, int64_t pitch, uint16_t* Y, void* stream) {
+sps_status sps_subband_step1(const sps_plan* p, const uint8_t* x, int64_t pitch, uint16_t* Y, void* ws,
+                             size_t ws_bytes, void* stream) {
   clear_error();
   if (sps_status s = check_plan(p)) return s;
   if (p->mode != SPS_MODE_SUBBAND) return fail(SPS_ERR_INVALID_ARG, "plan is not in SUBBAND mode");
   if (sps_status s = check_x(p, x, pitch)) return s;
   if (!Y || !aligned16(Y)) return fail(SPS_ERR_INVALID_ARG, "Y must be non-null and 16-byte aligned");
-  return run_step1(p, x, pitch, Y, (cudaStream_t)stream);
+  if (sps_status s = check_workspace(p, ws, ws_bytes)) return s;
+  return run_step1(p, x, pitch, static_cast<uint8_t*>(ws), Y, (cudaStream_t)stream);
 }
 
 sps_status sps_subband_step2(const sps_plan* p, const uint16_t* Y, int32_t* D, void* stream) {
@@ -236,7 +264,7 @@ sps_status sps_integrate(const sps_plan* p, const int32_t* D, int32_t* B, void* 
   if (sps_status s = check_plan(p)) return s;
   if (!D || !B) return fail(SPS_ERR_INVALID_ARG, "null pointer");
   return launch_integrate(D, (int32_t)p->dms.size(), p->n_t, p->d_widths, (int32_t)p->widths.size(), B,
-                          (cudaStream_t)stream);
+                          p->d_status, (cudaStream_t)stream);
 }
 
 sps_status sps_snr(const sps_plan* p, const int32_t* D, double* snr, int32_t* peak_t, int32_t* peak_val,
@@ -279,6 +307,15 @@ sps_status sps_search_host(const sps_plan* p, const uint8_t* x_host, int64_t pit
   if (best_host && best_dev) SPS_CUDA(cudaMemcpyAsync(best_host, best_dev, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   SPS_CUDA(cudaStreamSynchronize(st));
   return SPS_OK;
+}
+
+sps_status sps_plan_status(const sps_plan* p, uint32_t* host_status, int32_t clear) {
+  clear_error();
+  if (sps_status s = check_plan(p)) return s;
+  if (!host_status) return fail(SPS_ERR_INVALID_ARG, "null output");
+  SPS_CUDA(cudaMemcpy(host_status, p->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (clear) SPS_CUDA(cudaMemset(p->d_status, 0, sizeof(uint32_t)));
+  return *host_status ? fail(SPS_ERR_TIMEOUT, "a kernel's bounded wait ran out") : SPS_OK;
 }
 
 const char* sps_status_string(sps_status s) {

@@ -10,21 +10,26 @@
 // memory wavefronts and integer issue, not by HBM (about 300 adds per input
 // byte at 1536 channels), so there are no tensor cores here.
 //   * A block owns Di = warps_dm * ND DM trials by Tt = warps_time * 128 * NW
-//     samples and walks the channels `chunk` at a time.  For each channel the
-//     window [t0 + d(i0, c), t0 + Tt + d(i_last, c)) is staged once (16-byte
-//     global loads) and read by all Di trials.
-//   * Four copies of each window are kept, copy j shifted by j bytes, so that
+//     samples and walks its channels `chunk` at a time.  For each channel the
+//     window [t0 + d(i0, c), t0 + Tt + d(i_last, c)) is staged once and read by
+//     all Di trials.
+//   * Four copies of each window are staged, copy j shifted by j bytes, so that
 //     every 4-sample read is one aligned, conflict-free 32-bit shared load
-//     whatever the delay's alignment.
+//     whatever the delay's alignment.  A pre-pass (expand_kernel) writes the
+//     shifted copies 1..3 of the whole batch once; all four copies and the
+//     chunk's shared-memory offset table arrive by bulk asynchronous copies
+//     (TMA) into a two-stage ring guarded by mbarriers, so the warps only add.
 //   * SWAR: a word of 4 samples is split into even and odd bytes in 16-bit
 //     lanes (one AND, one byte permute) and two channels are added per 3-input
 //     add.  16-bit lanes stay exact for 257 channels of 255; partial sums are
 //     folded into int32 registers every <= 256 channels.
-//   * A per-chunk table of shared-memory offsets (one per trial and channel)
-//     turns each trial's access into a broadcast load plus immediate offsets.
+//   * The offset of (trial, channel) inside the staged windows does not depend
+//     on the time tile (tiles start at multiples of 128), so the plan
+//     precomputes it once per configuration.
 #include <algorithm>
 
 #include "sps_internal.h"
+#include "tma.cuh"
 
 namespace sps {
 namespace {
@@ -34,45 +39,76 @@ constexpr int kMaxThreads = 512;
 
 __device__ __forceinline__ uint32_t odd_bytes(uint32_t w) { return __byte_perm(w, 0u, 0x4341); }
 
-// Bytes [p, p + 20) of channel row `c`, zero at and beyond `len`.
-__device__ __forceinline__ void load_raw20(const uint8_t* row, int64_t p, int32_t len, uint32_t r[5]) {
-  if (p + 20 <= len) {
-    uint4 v = __ldg(reinterpret_cast<const uint4*>(row + p));
-    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
-    r[4] = __ldg(reinterpret_cast<const uint32_t*>(row + p + 16));
-  } else {
-#pragma unroll
-    for (int k = 0; k < 5; k++) {
-      uint32_t w = 0;
-#pragma unroll
-      for (int b = 0; b < 4; b++) {
-        int64_t q = p + 4 * k + b;
-        uint32_t v = q < len ? (uint32_t)__ldg(row + q) : 0u;
-        w |= v << (8 * b);
-      }
-      r[k] = w;
-    }
-  }
-}
-
 template <int ND, int NW>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  const int Di = wd * ND;
+  extern __shared__ __align__(128) uint8_t smem[];
   const int wt = (int)(blockDim.x >> 5) / wd;
   const int Tt = wt * 128 * NW;
+  const int Di = wd * ND;
   const int copy_stride = cc_max * wb;
-  uint32_t* tbl = reinterpret_cast<uint32_t*>(smem + 4 * copy_stride);
+  const int stage_bytes = 4 * copy_stride + cc_max * a.di_pad * 4;
+  int32_t* b0s = reinterpret_cast<int32_t*>(smem + 2 * stage_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes + ((a.group_channels * 4 + 15) & ~15));
+  __shared__ int aborted;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int dm_sub = warp % wd, t_sub = warp / wd;
-  const int t0 = blockIdx.x * Tt;
-  const int i0 = blockIdx.y * Di;
+  const int tile = blockIdx.x;
+  const int i0 = tile * Di;
+  const int t0 = blockIdx.y * Tt;
   const int g = blockIdx.z;
-  const int c_lo = g * a.group_channels, c_hi = c_lo + a.group_channels;
+  const int G = a.group_channels;
+  const int c_lo = g * G;
+  const int n_chunks = (G + cc_max - 1) / cc_max;
+  const int pairs = (G + 1) >> 1;
   const uint32_t toff = (uint32_t)(t_sub * 128 * NW + lane * 4);
-  const int32_t* drow0 = a.delays + (int64_t)i0 * a.channels;
+
+  for (int c = tid; c < G; c += blockDim.x) b0s[c] = a.b0[(int64_t)tile * a.channels + c_lo + c];
+  if (tid == 0) {
+    aborted = 0;
+    mbar_init(&bars[0], blockDim.x >> 5);
+    mbar_init(&bars[1], blockDim.x >> 5);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // Every warp stages its share of chunk `ch` (channels warp, warp + nwarps,
+  // ...) into stage ch & 1: the four shifted copies of each channel window;
+  // warp 0 also copies the chunk's offset table.  Each warp's lane 0 arrives
+  // on the stage barrier with the bytes its warp issued.
+  const int nwarps = (int)(blockDim.x >> 5);
+  auto issue = [&](int ch) {
+    const int st = ch & 1;
+    uint8_t* sb = smem + st * stage_bytes;
+    const int cb = ch * cc_max, cc = min(cc_max, G - cb);
+    const int npair = (cc + 1) >> 1;
+    const uint32_t tbl_bytes = (uint32_t)(npair * a.di_pad * 8);
+    // lanes 4q..4q+3 of a warp handle copies 0..3 of channels warp + (q + 8k) * nwarps
+    const int q = lane >> 2, j = lane & 3;
+    uint32_t mine = 0;
+    for (int l = warp + q * nwarps; l < cc; l += 8 * nwarps)
+      mine += (uint32_t)min(wb, a.win_limit - (t0 + b0s[cb + l]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&bars[st], mine + (warp == 0 ? tbl_bytes : 0u));
+    }
+    __syncwarp();
+    for (int l = warp + q * nwarps; l < cc; l += 8 * nwarps) {
+      const int c = c_lo + cb + l;
+      const int start = t0 + b0s[cb + l];
+      const uint32_t bytes = (uint32_t)min(wb, a.win_limit - start);
+      const uint8_t* src = j == 0 ? a.x + (int64_t)c * a.pitch + start
+                                  : a.x4 + ((int64_t)(j - 1) * a.channels + c) * a.pitch4 + start;
+      bulk_g2s(sb + j * copy_stride + l * wb, src, bytes, &bars[st]);
+    }
+    if (warp == 0 && lane == 0) {
+      const uint32_t* src = a.offs + (((int64_t)tile * a.n_groups + g) * pairs + (cb >> 1)) * a.di_pad * 2;
+      bulk_g2s(sb + 4 * copy_stride, src, tbl_bytes, &bars[st]);
+    }
+  };
 
   uint32_t lo[ND][NW], hi[ND][NW];
   int32_t acc[ND][NW][4];
@@ -84,7 +120,6 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
 #pragma unroll
       for (int q = 0; q < 4; q++) acc[r][m][q] = 0;
     }
-
   auto fold = [&]() {
 #pragma unroll
     for (int r = 0; r < ND; r++)
@@ -98,75 +133,60 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
       }
   };
 
+  issue(0);
+  if (n_chunks > 1) issue(1);
+
   int pending = 0;
-  const int segs = wb >> 4;
-  for (int cb = c_lo; cb < c_hi; cb += cc_max) {
-    const int cc = min(cc_max, c_hi - cb);
+  int ch = 0;
+  for (; ch < n_chunks; ch++) {
+    const int st = ch & 1;
+    const int cc = min(cc_max, G - ch * cc_max);
     if (pending + cc > 256) { fold(); pending = 0; }
-    __syncthreads();  // the previous chunk's readers are done with the buffers
-
-    // Stage the windows: copy j holds raw byte (start + p + j) at position p.
-    for (int e = tid; e < cc * segs; e += blockDim.x) {
-      const int cl = e / segs, q = e - cl * segs;
-      const int c = cb + cl;
-      const int64_t start = (int64_t)((t0 + drow0[c]) & ~15);
-      uint32_t r[5];
-      load_raw20(a.x + (int64_t)c * a.pitch, start + 16 * q, a.in_len, r);
-      uint8_t* dst = smem + cl * wb + 16 * q;
-      *reinterpret_cast<uint4*>(dst) = make_uint4(r[0], r[1], r[2], r[3]);
-      *reinterpret_cast<uint4*>(dst + copy_stride) =
-          make_uint4(__byte_perm(r[0], r[1], 0x4321), __byte_perm(r[1], r[2], 0x4321),
-                     __byte_perm(r[2], r[3], 0x4321), __byte_perm(r[3], r[4], 0x4321));
-      *reinterpret_cast<uint4*>(dst + 2 * copy_stride) =
-          make_uint4(__byte_perm(r[0], r[1], 0x5432), __byte_perm(r[1], r[2], 0x5432),
-                     __byte_perm(r[2], r[3], 0x5432), __byte_perm(r[3], r[4], 0x5432));
-      *reinterpret_cast<uint4*>(dst + 3 * copy_stride) =
-          make_uint4(__byte_perm(r[0], r[1], 0x6543), __byte_perm(r[1], r[2], 0x6543),
-                     __byte_perm(r[2], r[3], 0x6543), __byte_perm(r[3], r[4], 0x6543));
-    }
-    // Offsets: trial r of the block reads channel cl at copy (rel & 3), byte (rel & ~3).
-    for (int e = tid; e < Di * cc; e += blockDim.x) {
-      const int r = e / cc, cl = e - r * cc;
-      const int i = min(i0 + r, a.n_dm - 1);
-      const int c = cb + cl;
-      const int d0 = drow0[c];
-      const int di = a.delays[(int64_t)i * a.channels + c];
-      const int start = (t0 + d0) & ~15;
-      const int rel = t0 + di - start;
-      tbl[r * cc_max + cl] = (uint32_t)((rel & 3) * copy_stride + cl * wb + (rel & ~3));
-    }
-    __syncthreads();
-
-    const uint32_t* trow = tbl + dm_sub * ND * cc_max;
-    int cl = 0;
-    for (; cl + 1 < cc; cl += 2) {
+    if (!mbar_wait(&bars[st], (ch >> 1) & 1, a.status)) aborted = 1;
+    if (!aborted) {
+      // 32-bit offsets into the shared window keep addressing in the shared space
+      const uint32_t base = (uint32_t)(st * stage_bytes) + toff;
+      const uint2* tb = reinterpret_cast<const uint2*>(smem + st * stage_bytes + 4 * copy_stride) + dm_sub * ND;
+      int cl = 0;
+      for (; cl + 1 < cc; cl += 2) {
+        const uint2* e = tb + (cl >> 1) * a.di_pad;
 #pragma unroll
-      for (int r = 0; r < ND; r++) {
-        const uint2 o = *reinterpret_cast<const uint2*>(trow + r * cc_max + cl);
-        const uint8_t* p1 = smem + o.x + toff;
-        const uint8_t* p2 = smem + o.y + toff;
+        for (int r = 0; r < ND; r++) {
+          const uint2 o = e[r];
+          const uint32_t a1 = base + o.x, a2 = base + o.y;
 #pragma unroll
-        for (int m = 0; m < NW; m++) {
-          const uint32_t w1 = *reinterpret_cast<const uint32_t*>(p1 + 128 * m);
-          const uint32_t w2 = *reinterpret_cast<const uint32_t*>(p2 + 128 * m);
-          lo[r][m] += (w1 & kEvenBytes) + (w2 & kEvenBytes);
-          hi[r][m] += odd_bytes(w1) + odd_bytes(w2);
+          for (int m = 0; m < NW; m++) {
+            const uint32_t w1 = *reinterpret_cast<const uint32_t*>(smem + (a1 + 128u * m));
+            const uint32_t w2 = *reinterpret_cast<const uint32_t*>(smem + (a2 + 128u * m));
+            lo[r][m] += (w1 & kEvenBytes) + (w2 & kEvenBytes);
+            hi[r][m] += odd_bytes(w1) + odd_bytes(w2);
+          }
         }
       }
-    }
-    if (cl < cc) {
+      if (cl < cc) {
+        const uint2* e = tb + (cl >> 1) * a.di_pad;
 #pragma unroll
-      for (int r = 0; r < ND; r++) {
-        const uint8_t* p1 = smem + trow[r * cc_max + cl] + toff;
+        for (int r = 0; r < ND; r++) {
+          const uint32_t a1 = base + e[r].x;
 #pragma unroll
-        for (int m = 0; m < NW; m++) {
-          const uint32_t w1 = *reinterpret_cast<const uint32_t*>(p1 + 128 * m);
-          lo[r][m] += w1 & kEvenBytes;
-          hi[r][m] += odd_bytes(w1);
+          for (int m = 0; m < NW; m++) {
+            const uint32_t w1 = *reinterpret_cast<const uint32_t*>(smem + (a1 + 128u * m));
+            lo[r][m] += w1 & kEvenBytes;
+            hi[r][m] += odd_bytes(w1);
+          }
         }
       }
     }
     pending += cc;
+    __syncthreads();
+    if (aborted) break;
+    if (ch + 2 < n_chunks) issue(ch + 2);
+  }
+  if (aborted) {
+    // let copies already in flight land before the block's shared memory goes away
+    if (tid == 0)
+      for (int k = ch; k < min(ch + 2, n_chunks); k++) mbar_wait(&bars[k & 1], (k >> 1) & 1, a.status);
+    return;
   }
   fold();
 
@@ -203,6 +223,49 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
   }
 }
 
+// Bytes [p, p + 20) of a channel row, zero at and beyond `len`.
+__device__ __forceinline__ void load_raw20(const uint8_t* row, int64_t p, int32_t len, uint32_t r[5]) {
+  if (p + 20 <= len) {
+    uint4 v = __ldg(reinterpret_cast<const uint4*>(row + p));
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+    r[4] = __ldg(reinterpret_cast<const uint32_t*>(row + p + 16));
+  } else {
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+      uint32_t w = 0;
+#pragma unroll
+      for (int b = 0; b < 4; b++) {
+        int64_t q = p + 4 * k + b;
+        uint32_t v = q < len ? (uint32_t)__ldg(row + q) : 0u;
+        w |= v << (8 * b);
+      }
+      r[k] = w;
+    }
+  }
+}
+
+// x4[j - 1][c][p] = x[c][p + j] for j = 1..3 (0 at and beyond in_len).
+__global__ void __launch_bounds__(256) expand_kernel(const uint8_t* x, int64_t pitch, int32_t in_len,
+                                                     int32_t channels, uint8_t* x4, int64_t pitch4) {
+  const int64_t spr = pitch4 >> 4;
+  const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (seg >= spr * channels) return;
+  const int64_t c = seg / spr, p = (seg - c * spr) << 4;
+  uint32_t r[5];
+  load_raw20(x + c * pitch, p, in_len, r);
+  const int64_t plane = (int64_t)channels * pitch4;
+  uint8_t* dst = x4 + c * pitch4 + p;
+  *reinterpret_cast<uint4*>(dst) =
+      make_uint4(__byte_perm(r[0], r[1], 0x4321), __byte_perm(r[1], r[2], 0x4321),
+                 __byte_perm(r[2], r[3], 0x4321), __byte_perm(r[3], r[4], 0x4321));
+  *reinterpret_cast<uint4*>(dst + plane) =
+      make_uint4(__byte_perm(r[0], r[1], 0x5432), __byte_perm(r[1], r[2], 0x5432),
+                 __byte_perm(r[2], r[3], 0x5432), __byte_perm(r[3], r[4], 0x5432));
+  *reinterpret_cast<uint4*>(dst + 2 * plane) =
+      make_uint4(__byte_perm(r[0], r[1], 0x6543), __byte_perm(r[1], r[2], 0x6543),
+                 __byte_perm(r[2], r[3], 0x6543), __byte_perm(r[3], r[4], 0x6543));
+}
+
 typedef void (*U8Kernel)(U8PassArgs, int, int, int);
 
 template <int ND, int NW>
@@ -222,12 +285,14 @@ U8Kernel find(int nd, int nw) {
   return nullptr;
 }
 
-int copy_bytes(const sps_dedisp_config& c, int32_t dmax_tile) {
+}  // namespace
+
+int u8_window_bytes(const sps_dedisp_config& c, int32_t dmax_tile) {
   const int Tt = c.warps_time * 32 * c.samples_per_thread;
   return (Tt + dmax_tile + 15 + 15) / 16 * 16;
 }
 
-}  // namespace
+int u8_di_pad(const sps_dedisp_config& c) { return (c.warps_dm * c.dms_per_thread + 1) / 2 * 2; }
 
 bool u8_config_supported(const sps_dedisp_config& c, std::string* why) {
   if (c.samples_per_thread % 4 || !find(c.dms_per_thread, c.samples_per_thread / 4)) {
@@ -239,16 +304,24 @@ bool u8_config_supported(const sps_dedisp_config& c, std::string* why) {
     *why = "warps_dm * warps_time must lie in [1, 16]";
     return false;
   }
-  if (c.chunk < 2 || c.chunk > 256 || (c.chunk & 1)) {
-    *why = "chunk must be even and in [2, 256]";
+  if (c.chunk < 2 || c.chunk > 64 || (c.chunk & 1)) {
+    *why = "chunk must be even and in [2, 64]";
     return false;
   }
   return true;
 }
 
-size_t u8_smem_bytes(const sps_dedisp_config& c, int32_t dmax_tile) {
-  const size_t Di = (size_t)c.warps_dm * c.dms_per_thread;
-  return 4 * (size_t)c.chunk * copy_bytes(c, dmax_tile) + Di * c.chunk * 4;
+size_t u8_smem_bytes(const sps_dedisp_config& c, int32_t dmax_tile, int32_t group_channels) {
+  const size_t stage = 4 * (size_t)c.chunk * u8_window_bytes(c, dmax_tile) + (size_t)c.chunk * u8_di_pad(c) * 4;
+  return 2 * stage + (((size_t)group_channels * 4 + 15) & ~(size_t)15) + 16;
+}
+
+sps_status launch_expand(const uint8_t* x, int64_t pitch, int32_t in_len, int32_t channels, uint8_t* x4,
+                         int64_t pitch4, cudaStream_t st) {
+  const int64_t segs = (pitch4 >> 4) * channels;
+  expand_kernel<<<(unsigned)((segs + 255) / 256), 256, 0, st>>>(x, pitch, in_len, channels, x4, pitch4);
+  SPS_CUDA(cudaGetLastError());
+  return SPS_OK;
 }
 
 sps_status launch_u8_pass(const U8PassArgs& a, const sps_dedisp_config& c, cudaStream_t st) {
@@ -257,11 +330,11 @@ sps_status launch_u8_pass(const U8PassArgs& a, const sps_dedisp_config& c, cudaS
   U8Kernel fn = find(c.dms_per_thread, c.samples_per_thread / 4);
   const int Di = c.warps_dm * c.dms_per_thread;
   const int Tt = c.warps_time * 32 * c.samples_per_thread;
-  const size_t smem = u8_smem_bytes(c, a.dmax_tile);
-  dim3 grid((a.n_out + Tt - 1) / Tt, (a.n_dm + Di - 1) / Di, a.n_groups);
-  if (grid.y > 65535 || grid.z > 65535) return fail(SPS_ERR_UNSUPPORTED, "too many DM tiles or groups");
+  const size_t smem = u8_smem_bytes(c, a.dmax_tile, a.group_channels);
+  dim3 grid((a.n_dm + Di - 1) / Di, (a.n_out + Tt - 1) / Tt, a.n_groups);
+  if (grid.y > 65535 || grid.z > 65535) return fail(SPS_ERR_UNSUPPORTED, "too many time tiles or groups");
   SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  fn<<<grid, 32 * c.warps_dm * c.warps_time, smem, st>>>(a, c.warps_dm, c.chunk, copy_bytes(c, a.dmax_tile));
+  fn<<<grid, 32 * c.warps_dm * c.warps_time, smem, st>>>(a, c.warps_dm, c.chunk, u8_window_bytes(c, a.dmax_tile));
   SPS_CUDA(cudaGetLastError());
   return SPS_OK;
 }

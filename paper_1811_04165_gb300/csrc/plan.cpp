@@ -57,6 +57,39 @@ int32_t tile_spread(const std::vector<int32_t>& t, int32_t rows, int32_t cols, i
   return best;
 }
 
+// Staged-window tables of the uint8 pass for one configuration (see
+// dedisperse_u8.cu): per DM tile and channel the first trial's delay rounded
+// down to 16 (where the window starts), and per (tile, channel, trial) the
+// byte offset of that trial's first sample inside the staged stage: copy
+// (e & 3), channel row (c mod chunk), byte (e & ~3), e = d(i, c) - start.
+// Tiles start at multiples of 128 samples, so none of this depends on time.
+void build_u8_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per,
+                     const sps_dedisp_config& cfg, int32_t dmax, std::vector<int32_t>* b0,
+                     std::vector<uint32_t>* offs) {
+  const int32_t Di = cfg.warps_dm * cfg.dms_per_thread;
+  const int32_t di_pad = sps::u8_di_pad(cfg);
+  const int32_t wb = sps::u8_window_bytes(cfg, dmax);
+  const int32_t copy_stride = cfg.chunk * wb;
+  const int32_t n_tiles = (rows + Di - 1) / Di;
+  const int32_t G = C / per, pairs = (per + 1) / 2;
+  b0->assign((size_t)n_tiles * C, 0);
+  offs->assign((size_t)n_tiles * G * pairs * di_pad * 2, 0u);
+  for (int32_t tile = 0; tile < n_tiles; tile++) {
+    const int32_t i0 = tile * Di;
+    for (int32_t c = 0; c < C; c++) {
+      const int32_t d0 = d[(size_t)i0 * C + c];
+      (*b0)[(size_t)tile * C + c] = d0 & ~15;
+      const int32_t g = c / per, cw = c % per, cl = cw % cfg.chunk;
+      for (int32_t r = 0; r < di_pad; r++) {
+        const int32_t i = std::min(i0 + std::min(r, Di - 1), rows - 1);
+        const int32_t e = (d0 & 15) + d[(size_t)i * C + c] - d0;
+        const uint32_t off = (uint32_t)((e & 3) * copy_stride + cl * wb + (e & ~3));
+        (*offs)[((((size_t)tile * G + g) * pairs + cw / 2) * di_pad + r) * 2 + (cw & 1)] = off;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 int64_t sps_plan::max_delay_brute() const {
@@ -111,13 +144,34 @@ sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg) {
   }
   int dev_max_smem = 0;
   SPS_CUDA(cudaDeviceGetAttribute(&dev_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
-  if (p->mode == SPS_MODE_BRUTE && u8_smem_bytes(cfg.brute, dmax_b) > (size_t)dev_max_smem)
+  if (p->mode == SPS_MODE_BRUTE && u8_smem_bytes(cfg.brute, dmax_b, p->channels) > (size_t)dev_max_smem)
     return fail(SPS_ERR_INVALID_ARG, "brute config needs more shared memory than a block may use");
   if (p->mode == SPS_MODE_SUBBAND) {
-    if (u8_smem_bytes(cfg.step1, dmax_1) > (size_t)dev_max_smem)
+    if (u8_smem_bytes(cfg.step1, dmax_1, p->channels / p->n_subbands) > (size_t)dev_max_smem)
       return fail(SPS_ERR_INVALID_ARG, "step1 config needs more shared memory than a block may use");
     if (step2_smem_bytes(cfg.step2, dmax_2) > (size_t)dev_max_smem)
       return fail(SPS_ERR_INVALID_ARG, "step2 config needs more shared memory than a block may use");
+  }
+  {
+    std::vector<int32_t> b0;
+    std::vector<uint32_t> offs;
+    if (p->mode == SPS_MODE_BRUTE)
+      build_u8_tables(p->delays, n_dms, p->channels, p->channels, cfg.brute, dmax_b, &b0, &offs);
+    else
+      build_u8_tables(p->d1, (int32_t)p->coarse_dms.size(), p->channels, p->channels / p->n_subbands, cfg.step1,
+                      dmax_1, &b0, &offs);
+    int32_t* db0 = nullptr;
+    uint32_t* doffs = nullptr;
+    sps_status st = upload(b0, &db0);
+    if (st == SPS_OK) st = upload(offs, &doffs);
+    if (st != SPS_OK) {
+      cudaFree(db0);
+      return st;
+    }
+    cudaFree(p->d_b0);
+    cudaFree(p->d_offs);
+    p->d_b0 = db0;
+    p->d_offs = doffs;
   }
   if (p->mode == SPS_MODE_SUBBAND) {
     int32_t* dt = nullptr;
@@ -240,11 +294,16 @@ sps_status plan_create(const sps_plan_desc* d, sps_plan** out) {
     p->step2_flush = std::max<int32_t>(1, 65535 / (255 * per));
   }
   p->n_in = p->n_t + max_total;
+  p->pitch4 = (p->n_in + 15) / 16 * 16;
   if (p->n_in > INT32_MAX / 2) { delete p; return fail(SPS_ERR_UNSUPPORTED, "input rows too long"); }
   int64_t max_sum = (int64_t)255 * C * p->widths.back();
   if (max_sum > INT32_MAX) { delete p; return fail(SPS_ERR_UNSUPPORTED, "boxcar sums could exceed int32"); }
 
   sps_status st = upload(p->widths, &p->d_widths);
+  if (st == SPS_OK) {
+    std::vector<uint32_t> zero(1, 0u);
+    st = upload(zero, &p->d_status);
+  }
   if (st == SPS_OK) st = upload(p->delays, &p->d_delays);
   if (st == SPS_OK) st = upload(p->d1, &p->d_d1);
   if (st == SPS_OK) st = upload(p->d2, &p->d_d2);

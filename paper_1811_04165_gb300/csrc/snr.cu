@@ -1,23 +1,27 @@
 // Boxcar integration and S/N with peak extraction (Sec. 2: smoothing of the
 // de-dispersed series, then S/N; the sliding-boxcar reading of "smoothing").
 //
-// For each DM row the block forms the prefix sums P[t] = sum_{u<t} D[u] once in
-// shared memory (32-bit wrap-around arithmetic: every boxcar
-// B_w[t] = P[t + w] - P[t] is below 2^31, so the wrapped difference is exact),
-// then for every width accumulates, over the N = N_t - w + 1 valid samples,
-// the exact integer moments S1 = sum B (64-bit), S2 = sum B^2 (128-bit), the
-// maximum and its first position.  One FP64 expression gives
+// One block per DM row.  The row arrives in shared memory by one bulk copy
+// (TMA) and is turned in place into prefix sums P[t] = sum_{u<t} D[u] (32-bit
+// wrap-around arithmetic: every boxcar B_w[t] = P[t + w] - P[t] is below 2^31,
+// so the wrapped difference is exact).  A single pass over t then serves all
+// widths of the pass at once, accumulating per width the exact integer moments
+// S1 = sum B, S2 = sum B^2 (128-bit at block level), the maximum and its first
+// position over the N = N_t - w + 1 valid samples.  One FP64 expression gives
 //   snr = (N P - S1) / sqrt(N S2 - S1^2),
 // i.e. (peak - mean) / population sigma, since N S2 - S1^2 = N^2 sigma^2.
 // Nothing is materialised; the integrate kernel writes B for checking.
 #include <algorithm>
 
 #include "sps_internal.h"
+#include "tma.cuh"
 
 namespace sps {
 namespace {
 
-constexpr int kMaxThreads = 1024;
+constexpr int kMaxThreads = 512;
+constexpr int kWidthsPerPass = 8;
+constexpr int kPad = 4;  // P[k] lives at buf[kPad - 1 + k]; the row lands at buf[kPad]
 
 // Block-wide exclusive prefix sum (uint32, wrap-around) of one value per thread.
 __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* scratch) {
@@ -45,20 +49,43 @@ __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* scratch) {
   return base + x - v;
 }
 
-// Fill P[0..n_t] with the prefix sums of one row (P[0] = 0).
-__device__ void row_prefix(const int32_t* row, int n_t, uint32_t* P, uint32_t* scratch) {
-  const int per = (n_t + blockDim.x - 1) / blockDim.x;
+// Load row i into buf[kPad .. kPad + n_t) and turn it into prefix sums in place:
+// afterwards buf[kPad - 1 + k] = sum_{u<k} D[u] for k = 0..n_t.
+__device__ bool load_prefix(const int32_t* row, int n_t, uint32_t* buf, uint32_t* scratch, uint64_t* bar,
+                            bool use_tma, uint32_t* status) {
+  bool ok = true;
+  if (use_tma) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+      mbar_arrive_expect_tx(bar, (uint32_t)n_t * 4u);
+      bulk_g2s(buf + kPad, row, (uint32_t)n_t * 4u, bar);
+    }
+    __syncthreads();
+    ok = mbar_wait(bar, 0, status);
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      // a copy that did not land in time may still be in flight: give it one
+      // more bounded wait before the block's shared memory is released
+      if (threadIdx.x == 0) mbar_wait(bar, 0, status);
+      return false;
+    }
+  } else {
+    for (int t = threadIdx.x; t < n_t; t += blockDim.x) buf[kPad + t] = (uint32_t)__ldg(row + t);
+  }
+  if (threadIdx.x == 0) buf[kPad - 1] = 0u;
+  __syncthreads();
+  // odd segment lengths keep the strided shared accesses free of bank conflicts
+  const int per = ((n_t + blockDim.x - 1) / blockDim.x) | 1;
   const int b = min(n_t, (int)threadIdx.x * per), e = min(n_t, b + per);
   uint32_t s = 0;
-  for (int t = b; t < e; t++) s += (uint32_t)__ldg(row + t);
+  for (int t = b; t < e; t++) s += buf[kPad + t];
   uint32_t run = block_exclusive_scan(s, scratch);
   for (int t = b; t < e; t++) {
-    P[t] = run;
-    run += (uint32_t)__ldg(row + t);
+    run += buf[kPad + t];
+    buf[kPad + t] = run;
   }
-  if (threadIdx.x == blockDim.x - 1) P[n_t] = run;
-  if (n_t == 0 && threadIdx.x == 0) P[0] = 0;
   __syncthreads();
+  return ok;
 }
 
 struct Moments {
@@ -68,20 +95,21 @@ struct Moments {
   int32_t best_t;
 };
 
-__device__ __forceinline__ void add128(unsigned long long& lo, unsigned long long& hi,
-                                       unsigned long long vlo, unsigned long long vhi) {
-  unsigned long long nlo = lo + vlo;
-  hi += vhi + (nlo < lo ? 1ull : 0ull);
-  lo = nlo;
+__device__ __forceinline__ void add128(unsigned long long& lo, unsigned long long& hi, unsigned long long v) {
+  const unsigned long long n = lo + v;
+  hi += n < lo ? 1ull : 0ull;
+  lo = n;
 }
 
 __device__ __forceinline__ void merge(Moments& a, const Moments& b) {
   a.s1 += b.s1;
-  add128(a.s2lo, a.s2hi, b.s2lo, b.s2hi);
+  const unsigned long long n = a.s2lo + b.s2lo;
+  a.s2hi += b.s2hi + (n < a.s2lo ? 1ull : 0ull);
+  a.s2lo = n;
   if (b.best > a.best || (b.best == a.best && b.best_t < a.best_t)) { a.best = b.best; a.best_t = b.best_t; }
 }
 
-__device__ Moments shfl_moments(const Moments& m, int o) {
+__device__ Moments shfl_down(const Moments& m, int o) {
   Moments r;
   r.s1 = __shfl_down_sync(0xffffffffu, m.s1, o);
   r.s2lo = __shfl_down_sync(0xffffffffu, m.s2lo, o);
@@ -93,62 +121,125 @@ __device__ Moments shfl_moments(const Moments& m, int o) {
 
 // (N P - S1) / sqrt(N S2 - S1^2) from exact moments; 0 for a constant series.
 __device__ double snr_from_moments(int64_t N, const Moments& m) {
-  const unsigned long long s1 = m.s1;
-  // var_num = N*S2 - S1^2 in 128 bits (non-negative by Cauchy-Schwarz)
   const unsigned __int128 s2 = ((unsigned __int128)m.s2hi << 64) | m.s2lo;
-  const unsigned __int128 var_num = (unsigned __int128)N * s2 - (unsigned __int128)s1 * s1;
+  const unsigned __int128 var_num = (unsigned __int128)N * s2 - (unsigned __int128)m.s1 * m.s1;
   if (var_num == 0) return 0.0;
-  const int64_t num = N * (int64_t)m.best - (int64_t)s1;
+  const int64_t num = N * (int64_t)m.best - (int64_t)m.s1;
   const double v = __dadd_rn(__dmul_rn((double)(unsigned long long)(var_num >> 64), 18446744073709551616.0),
                              (double)(unsigned long long)var_num);
   return __ddiv_rn((double)num, __dsqrt_rn(v));
 }
 
-__global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a) {
-  extern __shared__ __align__(16) uint32_t P[];
+// One pass over widths [w_begin, w_begin + NWP) (ascending).  `flush`: samples a
+// thread may add into its 32-bit S1 and 64-bit S2 partials before they could
+// overflow (from the largest possible boxcar value).  The pass tracks only the
+// maximum; the first position of the block's maximum is found afterwards by the
+// few threads whose own maximum equals it.
+template <int NWP>
+__global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_begin, int flush, int use_tma) {
+  extern __shared__ __align__(16) uint32_t buf[];
   __shared__ uint32_t scratch[32];
-  __shared__ Moments part[32];
+  __shared__ uint64_t bar;
+  __shared__ Moments part[32][NWP];
+  __shared__ int gmax[NWP], first[NWP];
   const int i = blockIdx.x;
   const int n_t = a.n_t;
-  row_prefix(a.D + (int64_t)i * n_t, n_t, P, scratch);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (!load_prefix(a.D + (int64_t)i * n_t, n_t, buf, scratch, &bar, use_tma != 0, a.status)) return;
+  const uint32_t* P = buf + kPad - 1;
 
-  for (int wi = 0; wi < a.n_widths; wi++) {
-    const int w = __ldg(a.widths + wi);
-    const int N = n_t - w + 1;
-    Moments m{0ull, 0ull, 0ull, -1, 0x7fffffff};
-    for (int t = threadIdx.x; t < N; t += blockDim.x) {
-      const int32_t B = (int32_t)(P[t + w] - P[t]);
-      m.s1 += (unsigned long long)(uint32_t)B;
-      const unsigned long long sq = (unsigned long long)(uint32_t)B * (uint32_t)B;
-      add128(m.s2lo, m.s2hi, sq, 0ull);
-      if (B > m.best) { m.best = B; m.best_t = t; }
+  int W[NWP];
+  uint32_t s1p[NWP], mx[NWP];
+  unsigned long long s2p[NWP], s1t[NWP], s2lo[NWP], s2hi[NWP];
+#pragma unroll
+  for (int k = 0; k < NWP; k++) {
+    W[k] = __ldg(a.widths + w_begin + k);
+    s1p[k] = 0u; mx[k] = 0u; s2p[k] = 0ull; s1t[k] = 0ull; s2lo[k] = 0ull; s2hi[k] = 0ull;
+  }
+  if (threadIdx.x < NWP) first[threadIdx.x] = 0x7fffffff;
+  auto flush_partials = [&]() {
+#pragma unroll
+    for (int k = 0; k < NWP; k++) {
+      s1t[k] += s1p[k];
+      add128(s2lo[k], s2hi[k], s2p[k]);
+      s1p[k] = 0u;
+      s2p[k] = 0ull;
     }
+  };
+  const int n_all = n_t - W[NWP - 1] + 1;  // every width of the pass is valid below this
+  const int n_any = n_t - W[0] + 1;
+  int count = 0;
+  int t = threadIdx.x;
+  for (; t < n_all; t += blockDim.x) {
+    const uint32_t p0 = P[t];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) merge(m, shfl_moments(m, o));
-    if (lane == 0) part[warp] = m;
-    __syncthreads();
-    if (warp == 0) {
-      Moments r = lane < nw ? part[lane] : Moments{0ull, 0ull, 0ull, -1, 0x7fffffff};
+    for (int k = 0; k < NWP; k++) {
+      const uint32_t B = P[t + W[k]] - p0;
+      s1p[k] += B;
+      s2p[k] += (unsigned long long)B * B;
+      mx[k] = max(mx[k], B);
+    }
+    if (++count == flush) { flush_partials(); count = 0; }
+  }
+  for (; t < n_any; t += blockDim.x) {
+    const uint32_t p0 = P[t];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) merge(r, shfl_moments(r, o));
-      if (lane == 0) {
-        const int64_t o = (int64_t)wi * a.n_dms + i;
-        a.snr[o] = snr_from_moments(N, r);
-        a.peak_t[o] = r.best_t;
-        a.peak_val[o] = r.best;
+    for (int k = 0; k < NWP; k++) {
+      if (t + W[k] <= n_t) {
+        const uint32_t B = P[t + W[k]] - p0;
+        s1p[k] += B;
+        s2p[k] += (unsigned long long)B * B;
+        mx[k] = max(mx[k], B);
       }
     }
-    __syncthreads();
+    if (++count == flush) { flush_partials(); count = 0; }
+  }
+  flush_partials();
+#pragma unroll
+  for (int k = 0; k < NWP; k++) {
+    Moments m{s1t[k], s2lo[k], s2hi[k], (int32_t)mx[k], 0};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) merge(m, shfl_down(m, o));
+    if (lane == 0) part[warp][k] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x < NWP) {
+    const int k = threadIdx.x;
+    int best = part[0][k].best;
+    for (int q = 1; q < nw; q++) best = max(best, part[q][k].best);
+    gmax[k] = best;
+  }
+  __syncthreads();
+  // first position of the maximum: only threads holding it scan their samples again
+#pragma unroll
+  for (int k = 0; k < NWP; k++) {
+    if ((int32_t)mx[k] == gmax[k]) {
+      const int N = n_t - W[k] + 1;
+      for (int u = threadIdx.x; u < N; u += blockDim.x)
+        if ((int32_t)(P[u + W[k]] - P[u]) == gmax[k]) { atomicMin(&first[k], u); break; }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NWP) {
+    const int k = threadIdx.x;
+    Moments r = part[0][k];
+    for (int q = 1; q < nw; q++) merge(r, part[q][k]);
+    const int64_t o = (int64_t)(w_begin + k) * a.n_dms + i;
+    a.snr[o] = snr_from_moments(n_t - W[k] + 1, r);
+    a.peak_t[o] = first[k];
+    a.peak_val[o] = gmax[k];
   }
 }
 
 __global__ void __launch_bounds__(kMaxThreads, 1)
-integrate_kernel(const int32_t* D, int n_dms, int n_t, const int32_t* widths, int n_widths, int32_t* B) {
-  extern __shared__ __align__(16) uint32_t P[];
+integrate_kernel(const int32_t* D, int n_dms, int n_t, const int32_t* widths, int n_widths, int32_t* B,
+                 int use_tma, uint32_t* status) {
+  extern __shared__ __align__(16) uint32_t buf[];
   __shared__ uint32_t scratch[32];
+  __shared__ uint64_t bar;
   const int i = blockIdx.x;
-  row_prefix(D + (int64_t)i * n_t, n_t, P, scratch);
+  if (!load_prefix(D + (int64_t)i * n_t, n_t, buf, scratch, &bar, use_tma != 0, status)) return;
+  const uint32_t* P = buf + kPad - 1;
   for (int wi = 0; wi < n_widths; wi++) {
     const int w = __ldg(widths + wi);
     const int N = n_t - w + 1;
@@ -206,38 +297,69 @@ detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
   }
 }
 
-size_t prefix_smem(int n_t) { return ((size_t)n_t + 1) * sizeof(uint32_t); }
+size_t prefix_smem(int n_t) { return ((size_t)n_t + kPad + 3) / 4 * 4 * sizeof(uint32_t); }
+
+bool tma_ok(const int32_t* D, int n_t) { return ((uintptr_t)D & 15) == 0 && (n_t & 3) == 0; }
+
+sps_status check_row_fits(int n_t, size_t extra) {
+  int dev = 0, max_smem = 0;
+  SPS_CUDA(cudaGetDevice(&dev));
+  SPS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (prefix_smem(n_t) + extra > (size_t)max_smem)
+    return fail(SPS_ERR_UNSUPPORTED, "rows too long for the shared-memory prefix");
+  return SPS_OK;
+}
 
 }  // namespace
 
 bool snr_config_supported(const sps_snr_config& c, std::string* why) {
   if (c.threads < 32 || c.threads > kMaxThreads || (c.threads & 31)) {
-    *why = "threads must be a multiple of 32 in [32, 1024]";
+    *why = "threads must be a multiple of 32 in [32, 512]";
     return false;
   }
   return true;
 }
 
+typedef void (*SnrKernel)(SnrArgs, int, int, int);
+
+SnrKernel snr_variant(int nwp) {
+  switch (nwp) {
+    case 1: return snr_kernel<1>;
+    case 2: return snr_kernel<2>;
+    case 3: return snr_kernel<3>;
+    case 4: return snr_kernel<4>;
+    case 5: return snr_kernel<5>;
+    case 6: return snr_kernel<6>;
+    case 7: return snr_kernel<7>;
+    default: return snr_kernel<8>;
+  }
+}
+
 sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st) {
   std::string why;
   if (!snr_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
+  if (sps_status s = check_row_fits(a.n_t, sizeof(Moments) * 32 * kWidthsPerPass + 512)) return s;
+  // largest boxcar value: 255 * channels * widest width (< 2^31, checked by the plan)
+  const unsigned long long bmax = std::max<unsigned long long>(1ull, (unsigned long long)a.max_boxcar);
+  const unsigned long long f1 = 0xFFFFFFFFull / bmax;
+  const unsigned long long f2 = 0xFFFFFFFFFFFFFFFFull / (bmax * bmax);
+  const int flush = (int)std::max<unsigned long long>(1ull, std::min<unsigned long long>({f1, f2, 1ull << 30}));
   const size_t smem = prefix_smem(a.n_t);
-  int dev = 0, max_smem = 0;
-  SPS_CUDA(cudaGetDevice(&dev));
-  SPS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (smem + 32 * sizeof(Moments) + 128 > (size_t)max_smem)
-    return fail(SPS_ERR_UNSUPPORTED, "rows too long for the shared-memory prefix");
-  SPS_CUDA(cudaFuncSetAttribute(snr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  snr_kernel<<<a.n_dms, c.threads, smem, st>>>(a);
-  SPS_CUDA(cudaGetLastError());
+  for (int w0 = 0; w0 < a.n_widths; w0 += kWidthsPerPass) {
+    SnrKernel fn = snr_variant(std::min(kWidthsPerPass, a.n_widths - w0));
+    SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fn<<<a.n_dms, c.threads, smem, st>>>(a, w0, flush, tma_ok(a.D, a.n_t) ? 1 : 0);
+    SPS_CUDA(cudaGetLastError());
+  }
   return SPS_OK;
 }
 
 sps_status launch_integrate(const int32_t* D, int32_t n_dms, int32_t n_t, const int32_t* widths,
-                            int32_t n_widths, int32_t* B, cudaStream_t st) {
+                            int32_t n_widths, int32_t* B, uint32_t* status, cudaStream_t st) {
+  if (sps_status s = check_row_fits(n_t, 256)) return s;
   const size_t smem = prefix_smem(n_t);
   SPS_CUDA(cudaFuncSetAttribute(integrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  integrate_kernel<<<n_dms, 256, smem, st>>>(D, n_dms, n_t, widths, n_widths, B);
+  integrate_kernel<<<n_dms, 256, smem, st>>>(D, n_dms, n_t, widths, n_widths, B, tma_ok(D, n_t) ? 1 : 0, status);
   SPS_CUDA(cudaGetLastError());
   return SPS_OK;
 }

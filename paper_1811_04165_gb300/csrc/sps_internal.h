@@ -26,12 +26,16 @@ void clear_error();
 // Kernel-side description of one de-dispersion pass over uint8 channels
 // (brute force, or subband step one with one output row per (coarse, subband)).
 struct U8PassArgs {
-  const uint8_t* x;        // [channels][pitch]
+  const uint8_t* x;        // [channels][pitch]: copy 0 of every window
   int64_t pitch;           // bytes per channel row
-  int32_t in_len;          // valid samples per row (bytes beyond read as 0)
-  const int32_t* delays;   // [n_dm][channels]
+  const uint8_t* x4;       // [3][channels][pitch4]: rows shifted by 1, 2, 3 bytes
+  int64_t pitch4;          // bytes per shifted row (N_in rounded up to 16)
+  int32_t win_limit;       // no staged window reads at or beyond this byte of a row
+  const int32_t* b0;       // [n_tiles][channels]: first-trial delay rounded down to 16
+  const uint32_t* offs;    // [n_tiles][n_groups][pairs][di_pad][2]: staged offsets
+  int32_t di_pad;          // trials per tile rounded up to even
   int32_t n_dm;            // delay-table rows
-  int32_t channels;        // total channels (delay-table row length)
+  int32_t channels;        // total channels
   int32_t group_channels;  // channels summed into one output row
   int32_t n_groups;        // output rows per DM (1 for brute force)
   int32_t n_out;           // output samples per row
@@ -39,6 +43,7 @@ struct U8PassArgs {
   int32_t dmax_tile;       // largest delay spread inside one DM tile of this config
   void* out;               // int32 rows (brute) or uint16 rows (step one)
   int32_t out_u16;         // 1: write uint16 sums (step one)
+  uint32_t* status;        // device status word (bounded-wait timeouts)
 };
 
 // Step two over uint16 subband series.
@@ -58,6 +63,7 @@ struct Step2Args {
 
 struct SnrArgs {
   const int32_t* D;        // [n_dms][n_t]
+  int64_t max_boxcar;      // 255 * channels * widest width
   int32_t n_dms;
   int32_t n_t;
   const int32_t* widths;   // device [n_widths]
@@ -65,6 +71,7 @@ struct SnrArgs {
   double* snr;             // [n_widths][n_dms]
   int32_t* peak_t;
   int32_t* peak_val;
+  uint32_t* status;
 };
 
 // Kernel launchers (dedisperse.cu, snr.cu).  They validate the configuration
@@ -73,13 +80,17 @@ sps_status launch_u8_pass(const U8PassArgs& a, const sps_dedisp_config& cfg, cud
 sps_status launch_step2(const Step2Args& a, const sps_dedisp_config& cfg, cudaStream_t st);
 sps_status launch_snr(const SnrArgs& a, const sps_snr_config& cfg, cudaStream_t st);
 sps_status launch_integrate(const int32_t* D, int32_t n_dms, int32_t n_t, const int32_t* widths,
-                            int32_t n_widths, int32_t* B, cudaStream_t st);
+                            int32_t n_widths, int32_t* B, uint32_t* status, cudaStream_t st);
+sps_status launch_expand(const uint8_t* x, int64_t pitch, int32_t in_len, int32_t channels, uint8_t* x4,
+                         int64_t pitch4, cudaStream_t st);
 sps_status launch_detect(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
                          int32_t n_dms, int32_t n_widths, int32_t* best, cudaStream_t st);
 bool u8_config_supported(const sps_dedisp_config& cfg, std::string* why);
 bool step2_config_supported(const sps_dedisp_config& cfg, std::string* why);
 bool snr_config_supported(const sps_snr_config& cfg, std::string* why);
-size_t u8_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
+size_t u8_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile, int32_t group_channels);
+int u8_window_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
+int u8_di_pad(const sps_dedisp_config& cfg);
 size_t step2_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
 
 }  // namespace sps
@@ -113,6 +124,12 @@ struct sps_plan {
   int32_t* d_widths = nullptr;
   int32_t* d_step2_tiles = nullptr;
   int32_t n_step2_tiles = 0;
+  uint32_t* d_status = nullptr;  // kernels' status word (bounded-wait timeouts)
+
+  // staged-window tables of the uint8 pass (brute force, or step one)
+  int32_t* d_b0 = nullptr;
+  uint32_t* d_offs = nullptr;
+  int64_t pitch4 = 0;            // bytes per row of the shifted copies
 
   sps_kernel_config cfg{};
   // delay spread of one DM tile for the current configuration

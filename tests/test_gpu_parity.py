@@ -78,12 +78,13 @@ def test_tiny_brute_whole_path(lib):
     _check_snr(_to_np(out["snr"]), _to_np(out["peak_t"]), _to_np(out["peak_val"]), s, pt, pv)
     assert _to_np(out["best"]).tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])]
     assert (bi, int(wl.widths[bw])) == (25, 4)
+    assert p.status() == 0
 
 
 CONFIGS = [  # (dms_per_thread, samples_per_thread, warps_dm, warps_time, chunk)
     (1, 4, 1, 1, 2), (1, 8, 2, 2, 6), (2, 4, 4, 2, 16), (2, 16, 2, 1, 32), (4, 4, 2, 2, 10),
-    (4, 8, 4, 2, 16), (4, 16, 8, 1, 16), (8, 4, 2, 4, 8), (8, 8, 1, 8, 16), (1, 32, 16, 1, 4),
-    (2, 32, 4, 1, 24),
+    (4, 8, 4, 2, 16), (4, 16, 8, 1, 16), (8, 4, 2, 4, 8), (8, 8, 1, 8, 6), (1, 32, 16, 1, 4),
+    (2, 32, 4, 1, 8),
 ]
 
 
@@ -248,8 +249,9 @@ def test_integrate_and_snr_exact(lib):
     rng = np.random.Generator(np.random.PCG64(3))
     n_dms, n_t = 37, 2003
     widths = [1, 2, 3, 16, 64, 2003]
-    p = lib.Plan(8, 1250.0, 1550.0, 81.92e-6, n_t, synth.dm_grid(n_dms, 1.0), widths)
-    D = rng.integers(0, 255 * 1536, (n_dms, n_t)).astype(np.int32)
+    # D within the plan's range: sums of 1536 uint8 channels
+    p = lib.Plan(1536, 1250.0, 1550.0, 81.92e-6, n_t, synth.dm_grid(n_dms, 1.0), widths)
+    D = rng.integers(0, 255 * 1536 + 1, (n_dms, n_t)).astype(np.int32)
     D[3] = 7  # constant row: S/N 0
     D[4] = 0
     D[4, 1000] = 123456  # single spike: closed form
@@ -272,17 +274,18 @@ def test_integrate_and_snr_exact(lib):
     assert np.all(_to_np(out["snr"])[:, 3] == 0.0)
 
 
-@pytest.mark.parametrize("threads", [32, 96, 256, 1024])
+@pytest.mark.parametrize("threads", [32, 96, 256, 512])
 def test_snr_thread_counts(lib, threads):
     torch = _torch()
     rng = np.random.Generator(np.random.PCG64(threads))
     n_dms, n_t = 9, 12500
-    p = lib.Plan(8, 1250.0, 1550.0, 81.92e-6, n_t, synth.dm_grid(n_dms, 1.0), [1, 2, 4, 8, 16, 32, 64])
+    p = lib.Plan(1536, 1250.0, 1550.0, 81.92e-6, n_t, synth.dm_grid(n_dms, 1.0), [1, 2, 4, 8, 16, 32, 64])
     c = p.config
     c.snr = lib.SnrConfig(threads)
     p.config = c
     D = rng.integers(150000, 250000, (n_dms, n_t)).astype(np.int32)
     D[:, 5000:5008] += 40000  # a burst so that maxima are distinct
+    D[0, :] = 255 * 1536      # the largest value the plan allows: exercises the partial-sum flushes
     out = p.alloc_outputs()
     lib.sps_snr(p, torch.from_numpy(D).cuda(), out["snr"], out["peak_t"], out["peak_val"], out["best"])
     torch.cuda.synchronize()
@@ -329,8 +332,17 @@ def test_argument_errors(lib):
     c.brute = lib.DedispConfig(3, 4, 1, 1, 2)  # no compiled variant
     with pytest.raises(lib.SpsError):
         p.config = c
-    ws = synth.apertif_beam(subband=True)
-    ps = lib.Plan.from_workload(ws)
-    with pytest.raises(lib.SpsError):  # subband mode needs its workspace
-        lib.sps_dedisperse(ps, torch.zeros((ws.channels, ps.pitch), dtype=torch.uint8, device="cuda"),
-                           torch.empty((2048, ws.n_t), dtype=torch.int32, device="cuda"))
+    # both modes need their workspace (shifted copies, and Y in subband mode)
+    L = lib.lib()
+    for wl in (synth.tiny_brute(), synth.apertif_beam(subband=True)):
+        ps = lib.Plan.from_workload(wl)
+        xs = torch.zeros((wl.channels, ps.pitch), dtype=torch.uint8, device="cuda")
+        Ds = torch.empty((wl.dms.size, wl.n_t), dtype=torch.int32, device="cuda")
+        small = torch.empty(ps.workspace_bytes - 16, dtype=torch.uint8, device="cuda")
+        import ctypes
+        assert L.sps_dedisperse(ps.handle, ctypes.c_void_p(xs.data_ptr()), ps.pitch,
+                                ctypes.c_void_p(Ds.data_ptr()), None, 0, None) == 1
+        assert L.sps_dedisperse(ps.handle, ctypes.c_void_p(xs.data_ptr()), ps.pitch,
+                                ctypes.c_void_p(Ds.data_ptr()), ctypes.c_void_p(small.data_ptr()),
+                                small.numel(), None) == 1
+    assert p.status() == 0  # no kernel's bounded wait ran out
