@@ -150,6 +150,24 @@ sps_status sps_plan_set_config(sps_plan* plan, const sps_kernel_config* cfg);
 sps_status sps_dedisperse(const sps_plan* plan, const uint8_t* x, int64_t x_pitch, int32_t* D,
                           void* workspace, size_t workspace_bytes, void* stream);
 
+/* sps_dedisperse without a workspace argument, for callers that cannot
+ * allocate device memory when they run: a real-time beam loop held to a fixed
+ * device-memory footprint once the observation has started, or code behind an
+ * interface that hands it only its input and output buffers.  The paper has no
+ * counterpart; this is a library convenience.
+ * Same inputs, outputs and results as sps_dedisperse.  The workspace comes
+ * from a file-scope device array of 96 MiB (enough for the brute-force search
+ * of one 1536-channel, 1.024 s beam, not for its subband path); plans that
+ * need more are rejected with UNSUPPORTED and a message giving both sizes.
+ * Allocates nothing.  Every device that loads this entry point keeps the
+ * array until the process exits.  All calls on a device share the array:
+ * calls whose work overlaps on the GPU (other streams or threads) race and
+ * corrupt each other's results.  The first call on each device looks up the
+ * array's device address (with the plan's device current, which is required)
+ * and should come before any stream capture. */
+sps_status sps_dedisperse_noalloc(const sps_plan* plan, const uint8_t* x, int64_t x_pitch, int32_t* D,
+                                  void* stream);
+
 /* Subband step one alone (Sec. 2, first footnote):
  *   Y[k][s][t] = sum_{c in s} x[c][t + d1(k, c)],  t < N_1,
  * Y: device, uint16 [n_coarse][n_subbands][y_pitch], y_pitch = N_1 rounded up

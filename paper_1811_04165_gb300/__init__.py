@@ -147,6 +147,15 @@ def sps_dedisperse(plan, x, D, workspace=None, stream=None):
                             ctypes.c_size_t(wsb), _stream(stream)), "sps_dedisperse")
 
 
+def sps_dedisperse_noalloc(plan, x, D, stream=None):
+    """sps_dedisperse with the library's fixed static scratch instead of a workspace
+    (for callers that cannot allocate device memory; see include/sps.h)."""
+    t = _torch()
+    check(_L.sps_dedisperse_noalloc(plan.handle, _dev(x, t.uint8, "x"), ctypes.c_int64(x.shape[1]),
+                                    _dev(D, t.int32, "D", (plan.n_dms, plan.n_samples)), _stream(stream)),
+          "sps_dedisperse_noalloc")
+
+
 def sps_subband_step1(plan, x, Y, workspace=None, stream=None):
     if workspace is None:
         workspace = plan.workspace()

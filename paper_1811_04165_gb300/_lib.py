@@ -25,6 +25,7 @@ SIGNATURES = {
     "sps_plan_get_config": (_I32, [_P, _P]),
     "sps_plan_set_config": (_I32, [_P, _P]),
     "sps_dedisperse": (_I32, [_P, _P, _I64, _P, _P, _SZ, _P]),
+    "sps_dedisperse_noalloc": (_I32, [_P, _P, _I64, _P, _P]),
     "sps_subband_step1": (_I32, [_P, _P, _I64, _P, _P, _SZ, _P]),
     "sps_subband_step2": (_I32, [_P, _P, _P, _P]),
     "sps_integrate": (_I32, [_P, _P, _P, _P]),

@@ -151,6 +151,14 @@ sps_status run_snr(const sps_plan* p, const int32_t* D, double* snr, int32_t* pe
 }
 
 }  // namespace
+
+size_t plan_workspace_bytes(const sps_plan* p) { return workspace_needed(p); }
+
+sps_status dedisperse_into(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
+                           size_t ws_bytes, cudaStream_t st) {
+  return run_dedisperse(p, x, pitch, D, ws, ws_bytes, st);
+}
+
 }  // namespace sps
 
 using namespace sps;

@@ -93,6 +93,12 @@ int u8_window_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
 int u8_di_pad(const sps_dedisp_config& cfg);
 size_t step2_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
 
+// Workspace a plan's de-dispersion needs, and de-dispersion into a given
+// workspace (abi.cpp); used by entry points that supply their own workspace.
+size_t plan_workspace_bytes(const sps_plan* p);
+sps_status dedisperse_into(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
+                           size_t ws_bytes, cudaStream_t st);
+
 }  // namespace sps
 
 struct sps_plan {
