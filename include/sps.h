@@ -211,6 +211,86 @@ sps_status sps_search_host(const sps_plan* plan, const uint8_t* x_host, int64_t 
                            int32_t* best_dev, double* snr_host, int32_t* peak_t_host,
                            int32_t* peak_val_host, int32_t* best_host, void* stream);
 
+/* ---------------------------------------------------------------- tuning */
+
+/* Auto-tuning (Sec. 3.2 and Sec. 4): the genetic algorithm that tunes every
+ * kernel's genes together, pure random search and exhaustive search, over a
+ * discrete space.  An individual is one value index per gene; genes are
+ * grouped by kernel (kernel_of non-decreasing).  Fitness is lower-is-better;
+ * +inf marks a failed configuration (the penalty of Sec. 4).
+ * Random numbers come from SplitMix64 seeded with `seed`; a run is
+ * reproducible draw for draw (the order of draws is fixed in tune.cpp).
+ * GA: N_pop individuals (even), tournament pools of max(2, round(pool_fraction
+ * * N_pop)) distinct individuals, N_pop tournaments, pairing without identical
+ * partners, per-kernel crossover with p_cross (uniform coin-toss or one-point,
+ * undone when it breaks validity), per-kernel mutation with p_mut to a
+ * different valid value, next population = fitter half of parents + fitter
+ * half of offspring.  The evaluation budget counts distinct individuals;
+ * repeats are served from a cache. */
+enum { SPS_TUNE_GA = 0, SPS_TUNE_RANDOM = 1, SPS_TUNE_EXHAUSTIVE = 2 };
+enum { SPS_CROSS_UNIFORM = 0, SPS_CROSS_ONE_POINT = 1 };
+enum { SPS_SPACE_FULL = 0, SPS_SPACE_REDUCED = 1 };
+#define SPS_TUNE_MAX_VALUES 8
+
+typedef struct {
+  int32_t n_genes;
+  const int32_t* n_values;   /* host, values per gene (>= 1)                       */
+  const int32_t* kernel_of;  /* host, kernel index per gene, non-decreasing        */
+} sps_space;
+
+typedef struct {
+  int32_t algorithm;         /* SPS_TUNE_*                                         */
+  int32_t crossover;         /* SPS_CROSS_* (GA)                                   */
+  int32_t population;        /* N_pop (GA)                                         */
+  int32_t max_generations;   /* GA stop                                            */
+  double p_cross;            /* per-kernel crossover probability (GA)              */
+  double p_mut;              /* per-kernel mutation probability (GA)               */
+  double pool_fraction;      /* tournament pool as a fraction of N_pop (GA)        */
+  int64_t max_evaluations;   /* budget of distinct evaluations (GA, random)        */
+  uint64_t seed;
+} sps_search_desc;
+
+typedef struct {
+  double best_fitness;
+  int64_t evaluations;       /* distinct individuals evaluated                     */
+  int32_t generations;
+  int32_t reserved;
+} sps_search_result;
+
+typedef int32_t (*sps_valid_fn)(const int32_t* point, void* user);          /* 1 = valid */
+typedef double (*sps_fitness_fn)(const int32_t* point, void* user);
+typedef void (*sps_trace_fn)(int64_t index, const int32_t* point, double fitness, void* user);
+
+/* Host-only search over a caller-defined space with caller callbacks (no GPU
+ * needed).  valid may be NULL (every point valid); trace (may be NULL) is
+ * called once per distinct evaluation, in order.  best_point: host int32
+ * [n_genes].  INVALID_ARG for a bad space or descriptor, or when no finite
+ * fitness was seen. */
+sps_status sps_optimize(const sps_space* space, const sps_search_desc* desc, sps_valid_fn valid,
+                        sps_fitness_fn fitness, sps_trace_fn trace, void* user, int32_t* best_point,
+                        sps_search_result* result);
+
+/* The plan's tuning space: the genes of every kernel its search path launches
+ * (brute: de-dispersion then S/N; subband: step one, step two, S/N), each a
+ * list of powers of two (Sec. 3.2).  SPS_SPACE_REDUCED keeps six genes of the
+ * subband path (5000 points) or five of the brute path.  Call with n_values
+ * NULL to get n_genes; values is [n_genes][SPS_TUNE_MAX_VALUES]. */
+sps_status sps_tune_space(const sps_plan* plan, int32_t which, int32_t max_genes, int32_t* n_genes,
+                          int32_t* n_values, int32_t* kernel_of, int32_t* values);
+/* The kernel configuration of a point (the plan's current one for genes the
+ * space does not hold); INVALID_ARG when the point breaks a boundary condition
+ * (no compiled variant, too many threads or too much shared memory). */
+sps_status sps_tune_config(const sps_plan* plan, int32_t which, const int32_t* point, sps_kernel_config* out);
+/* Live tuning on the GPU: fitness = median over three trials of the mean time
+ * (ms) of `reps` back-to-back sps_search calls on the given buffers (as for
+ * sps_search), +inf when a configuration is rejected or slower than limit_ms
+ * (0 = no limit).  Leaves the plan on the best configuration found.
+ * Synchronises `stream`. */
+sps_status sps_tune(sps_plan* plan, int32_t which, const sps_search_desc* desc, const uint8_t* x,
+                    int64_t x_pitch, int32_t* D, void* workspace, size_t workspace_bytes, double* snr,
+                    int32_t* peak_t, int32_t* peak_val, int32_t reps, double limit_ms, sps_trace_fn trace,
+                    void* user, int32_t* best_point, sps_search_result* result, void* stream);
+
 /* ---------------------------------------------------------------- misc */
 
 /* Reads (synchronously) the plan's device status word, which kernels set when

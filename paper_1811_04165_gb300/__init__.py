@@ -351,3 +351,123 @@ def upload_filterbank(x_np: np.ndarray, pitch: int | None = None):
     t = torch.zeros((C, pitch), dtype=torch.uint8)
     t[:, :n] = torch.from_numpy(np.ascontiguousarray(x_np))
     return t.to("cuda")
+
+
+# ----------------------------------------------------------------------------- tuning
+TUNE_GA, TUNE_RANDOM, TUNE_EXHAUSTIVE = 0, 1, 2
+CROSS_UNIFORM, CROSS_ONE_POINT = 0, 1
+SPACE_FULL, SPACE_REDUCED = 0, 1
+TUNE_MAX_VALUES = 8
+
+_VALID_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p)
+_FITNESS_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p)
+_TRACE_FN = ctypes.CFUNCTYPE(None, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.c_double, ctypes.c_void_p)
+
+
+class SpaceDesc(ctypes.Structure):
+    _fields_ = [("n_genes", ctypes.c_int32), ("n_values", ctypes.c_void_p), ("kernel_of", ctypes.c_void_p)]
+
+
+class SearchDesc(ctypes.Structure):
+    _fields_ = [("algorithm", ctypes.c_int32), ("crossover", ctypes.c_int32), ("population", ctypes.c_int32),
+                ("max_generations", ctypes.c_int32), ("p_cross", ctypes.c_double), ("p_mut", ctypes.c_double),
+                ("pool_fraction", ctypes.c_double), ("max_evaluations", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+
+
+class SearchResult(ctypes.Structure):
+    _fields_ = [("best_fitness", ctypes.c_double), ("evaluations", ctypes.c_int64), ("generations", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+def search_desc(algorithm=TUNE_GA, population=32, p_cross=0.8, p_mut=0.1, pool_fraction=0.2,
+                crossover=CROSS_UNIFORM, max_evaluations=500, max_generations=1000, seed=1) -> SearchDesc:
+    return SearchDesc(int(algorithm), int(crossover), int(population), int(max_generations), float(p_cross),
+                      float(p_mut), float(pool_fraction), int(max_evaluations), int(seed) & ((1 << 64) - 1))
+
+
+def sps_optimize(n_values, kernel_of, fitness, valid=None, desc: SearchDesc | None = None):
+    """Host-only GA / random / exhaustive search with Python callbacks.
+    Returns (best_point, SearchResult, trace) where trace lists (point, fitness)
+    per distinct evaluation, in order."""
+    nv = np.ascontiguousarray(n_values, np.int32)
+    ko = np.ascontiguousarray(kernel_of, np.int32)
+    sp = SpaceDesc(nv.size, nv.ctypes.data, ko.ctypes.data)
+    desc = desc or search_desc()
+    n = nv.size
+    trace, errors = [], []
+
+    def _pt(ptr):
+        return tuple(ptr[g] for g in range(n))
+
+    def _fit(ptr, _):
+        try:
+            return float(fitness(_pt(ptr)))
+        except Exception as e:  # keep exceptions from crossing the C boundary
+            errors.append(e)
+            return float("inf")
+
+    def _val(ptr, _):
+        try:
+            return 1 if valid(_pt(ptr)) else 0
+        except Exception as e:
+            errors.append(e)
+            return 0
+
+    def _tr(i, ptr, f, _):
+        trace.append((_pt(ptr), f))
+
+    cf, cv, ct = _FITNESS_FN(_fit), _VALID_FN(_val) if valid else None, _TRACE_FN(_tr)
+    best = np.zeros(n, np.int32)
+    res = SearchResult()
+    st = _L.sps_optimize(ctypes.byref(sp), ctypes.byref(desc), cv, cf, ct, None, best.ctypes.data, ctypes.byref(res))
+    if errors:
+        raise errors[0]
+    check(st, "sps_optimize")
+    return tuple(int(v) for v in best), res, trace
+
+
+def sps_tune_space(plan, which=SPACE_FULL):
+    """(n_values, kernel_of, values) of the plan's tuning space."""
+    n = ctypes.c_int32()
+    check(_L.sps_tune_space(plan.handle, int(which), 0, ctypes.byref(n), None, None, None), "sps_tune_space")
+    nv = np.zeros(n.value, np.int32)
+    ko = np.zeros(n.value, np.int32)
+    vals = np.zeros((n.value, TUNE_MAX_VALUES), np.int32)
+    check(_L.sps_tune_space(plan.handle, int(which), n.value, ctypes.byref(n), nv.ctypes.data, ko.ctypes.data,
+                            vals.ctypes.data), "sps_tune_space")
+    return nv, ko, [list(vals[g, :nv[g]]) for g in range(n.value)]
+
+
+def sps_tune_config(plan, which, point) -> KernelConfig:
+    pt = np.ascontiguousarray(point, np.int32)
+    c = KernelConfig()
+    check(_L.sps_tune_config(plan.handle, int(which), pt.ctypes.data, ctypes.byref(c)), "sps_tune_config")
+    return c
+
+
+def sps_tune(plan, x, which=SPACE_FULL, desc: SearchDesc | None = None, reps=3, limit_ms=0.0, out=None,
+             workspace=None, stream=None):
+    """Live tuning of the plan's kernels on input x; leaves the plan on the best
+    configuration.  Returns (best_point, SearchResult, trace)."""
+    t = _torch()
+    out = out or plan.alloc_outputs()
+    if workspace is None:
+        workspace = plan.workspace()
+    n = int(sps_tune_space(plan, which)[0].size)
+    trace = []
+
+    def _tr(i, ptr, f, _):
+        trace.append((tuple(ptr[g] for g in range(n)), f))
+
+    ct = _TRACE_FN(_tr)
+    best = np.zeros(n, np.int32)
+    res = SearchResult()
+    shp = (plan.n_widths, plan.n_dms)
+    check(_L.sps_tune(plan.handle, int(which), ctypes.byref(desc or search_desc()), _dev(x, t.uint8, "x"),
+                      ctypes.c_int64(x.shape[1]), _dev(out["D"], t.int32, "D", (plan.n_dms, plan.n_samples)),
+                      _dev(workspace, workspace.dtype, "workspace"),
+                      ctypes.c_size_t(workspace.numel() * workspace.element_size()),
+                      _dev(out["snr"], t.float64, "snr", shp), _dev(out["peak_t"], t.int32, "peak_t", shp),
+                      _dev(out["peak_val"], t.int32, "peak_val", shp), int(reps), float(limit_ms), ct, None,
+                      best.ctypes.data, ctypes.byref(res), _stream(stream)), "sps_tune")
+    return tuple(int(v) for v in best), res, trace

@@ -33,6 +33,11 @@ SIGNATURES = {
     "sps_search": (_I32, [_P, _P, _I64, _P, _P, _SZ, _P, _P, _P, _P, _P]),
     "sps_search_host": (_I32, [_P, _P, _I64, _P, _P, _P, _SZ, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "sps_plan_status": (_I32, [_P, _P, _I32]),
+    "sps_optimize": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "sps_tune_space": (_I32, [_P, _I32, _I32, _P, _P, _P, _P]),
+    "sps_tune_config": (_I32, [_P, _I32, _P, _P]),
+    "sps_tune": (_I32, [_P, _I32, _P, _P, _I64, _P, _P, _SZ, _P, _P, _P, _I32, ctypes.c_double, _P, _P, _P,
+                        _P, _P]),
     "sps_status_string": (ctypes.c_char_p, [_I32]),
     "sps_last_error": (ctypes.c_char_p, []),
     "sps_abi_version": (_I32, []),

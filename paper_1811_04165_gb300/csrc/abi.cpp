@@ -23,7 +23,6 @@ sps_status cuda_fail(cudaError_t e, const char* what) {
 void clear_error() { g_last_error.clear(); }
 
 sps_status plan_create(const sps_plan_desc* d, sps_plan** out);
-sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg);
 
 namespace {
 
@@ -153,6 +152,13 @@ sps_status run_snr(const sps_plan* p, const int32_t* D, double* snr, int32_t* pe
 }  // namespace
 
 size_t plan_workspace_bytes(const sps_plan* p) { return workspace_needed(p); }
+
+sps_status run_search(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws, size_t ws_bytes,
+                      double* snr, int32_t* peak_t, int32_t* peak_val, int32_t* best, cudaStream_t st) {
+  sps_status s = run_dedisperse(p, x, pitch, D, ws, ws_bytes, st);
+  if (s) return s;
+  return run_snr(p, D, snr, peak_t, peak_val, best, st);
+}
 
 sps_status dedisperse_into(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
                            size_t ws_bytes, cudaStream_t st) {

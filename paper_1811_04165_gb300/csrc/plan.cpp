@@ -109,8 +109,20 @@ sps_kernel_config default_config() {
   return c;
 }
 
-// Recompute everything that depends on the kernel configuration.
-sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg) {
+// Largest delay spread of the plan's table for tiles of `tile` rows (cached).
+int32_t cached_spread(const sps_plan* p, int which, int32_t tile) {
+  const int64_t key = (int64_t)which << 32 | (uint32_t)tile;
+  auto it = p->spread_cache.find(key);
+  if (it != p->spread_cache.end()) return it->second;
+  int32_t v = which == 0 ? tile_spread(p->delays, (int32_t)p->dms.size(), p->channels, tile)
+                         : tile_spread(p->d1, (int32_t)p->coarse_dms.size(), p->channels, tile);
+  p->spread_cache[key] = v;
+  return v;
+}
+
+// Validate a configuration against the compiled variants and the device's
+// shared memory, without changing the plan; fills the per-config sizes.
+sps_status check_config(const sps_plan* p, const sps_kernel_config& cfg, ConfigCheck* out) {
   std::string why;
   if (p->mode == SPS_MODE_BRUTE && !u8_config_supported(cfg.brute, &why))
     return fail(SPS_ERR_INVALID_ARG, "brute config: " + why);
@@ -120,38 +132,44 @@ sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg) {
   }
   if (!snr_config_supported(cfg.snr, &why)) return fail(SPS_ERR_INVALID_ARG, "snr config: " + why);
 
-  int32_t n_dms = (int32_t)p->dms.size();
-  int32_t dmax_b = 0, dmax_1 = 0, dmax_2 = 0;
-  std::vector<int32_t> tiles;
+  const int32_t n_dms = (int32_t)p->dms.size();
+  ConfigCheck c;
   if (p->mode == SPS_MODE_BRUTE) {
-    dmax_b = tile_spread(p->delays, n_dms, p->channels, cfg.brute.warps_dm * cfg.brute.dms_per_thread);
+    c.dmax_b = cached_spread(p, 0, cfg.brute.warps_dm * cfg.brute.dms_per_thread);
+    if (u8_smem_bytes(cfg.brute, c.dmax_b, p->channels) > (size_t)p->max_smem)
+      return fail(SPS_ERR_INVALID_ARG, "brute config needs more shared memory than a block may use");
   } else {
-    int32_t n_coarse = (int32_t)p->coarse_dms.size();
-    dmax_1 = tile_spread(p->d1, n_coarse, p->channels, cfg.step1.warps_dm * cfg.step1.dms_per_thread);
+    c.dmax_1 = cached_spread(p, 1, cfg.step1.warps_dm * cfg.step1.dms_per_thread);
     // step-two tiles: runs of trials sharing one coarse DM, at most Di long
-    int32_t di = cfg.step2.warps_dm * cfg.step2.dms_per_thread;
-    int32_t S = p->n_subbands;
+    const int32_t di = cfg.step2.warps_dm * cfg.step2.dms_per_thread;
+    const int32_t S = p->n_subbands;
     for (int32_t i = 0; i < n_dms;) {
-      int32_t k = p->coarse_of[i], j = i;
+      const int32_t k = p->coarse_of[i];
+      int32_t j = i;
       while (j < n_dms && p->coarse_of[j] == k && j - i < di) j++;
-      tiles.push_back(k);
-      tiles.push_back(i);
-      tiles.push_back(j - i);
+      c.tiles.push_back(k);
+      c.tiles.push_back(i);
+      c.tiles.push_back(j - i);
       for (int32_t s = 0; s < S; s++)
-        dmax_2 = std::max(dmax_2, p->d2[(size_t)(j - 1) * S + s] - p->d2[(size_t)i * S + s]);
+        c.dmax_2 = std::max(c.dmax_2, p->d2[(size_t)(j - 1) * S + s] - p->d2[(size_t)i * S + s]);
       i = j;
     }
-  }
-  int dev_max_smem = 0;
-  SPS_CUDA(cudaDeviceGetAttribute(&dev_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
-  if (p->mode == SPS_MODE_BRUTE && u8_smem_bytes(cfg.brute, dmax_b, p->channels) > (size_t)dev_max_smem)
-    return fail(SPS_ERR_INVALID_ARG, "brute config needs more shared memory than a block may use");
-  if (p->mode == SPS_MODE_SUBBAND) {
-    if (u8_smem_bytes(cfg.step1, dmax_1, p->channels / p->n_subbands) > (size_t)dev_max_smem)
+    if (u8_smem_bytes(cfg.step1, c.dmax_1, p->channels / S) > (size_t)p->max_smem)
       return fail(SPS_ERR_INVALID_ARG, "step1 config needs more shared memory than a block may use");
-    if (step2_smem_bytes(cfg.step2, dmax_2) > (size_t)dev_max_smem)
+    if (step2_smem_bytes(cfg.step2, c.dmax_2) > (size_t)p->max_smem)
       return fail(SPS_ERR_INVALID_ARG, "step2 config needs more shared memory than a block may use");
   }
+  if (out) *out = std::move(c);
+  return SPS_OK;
+}
+
+// Recompute everything that depends on the kernel configuration.
+sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg) {
+  ConfigCheck chk;
+  if (sps_status s = check_config(p, cfg, &chk)) return s;
+  const int32_t n_dms = (int32_t)p->dms.size();
+  const int32_t dmax_b = chk.dmax_b, dmax_1 = chk.dmax_1, dmax_2 = chk.dmax_2;
+  const std::vector<int32_t>& tiles = chk.tiles;
   {
     std::vector<int32_t> b0;
     std::vector<uint32_t> offs;
@@ -295,6 +313,10 @@ sps_status plan_create(const sps_plan_desc* d, sps_plan** out) {
   }
   p->n_in = p->n_t + max_total;
   p->pitch4 = (p->n_in + 15) / 16 * 16;
+  if (cudaDeviceGetAttribute(&p->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device) != cudaSuccess) {
+    delete p;
+    return fail(SPS_ERR_CUDA, "cudaDeviceGetAttribute(max shared memory)");
+  }
   if (p->n_in > INT32_MAX / 2) { delete p; return fail(SPS_ERR_UNSUPPORTED, "input rows too long"); }
   int64_t max_sum = (int64_t)255 * C * p->widths.back();
   if (max_sum > INT32_MAX) { delete p; return fail(SPS_ERR_UNSUPPORTED, "boxcar sums could exceed int32"); }

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -96,6 +97,16 @@ size_t step2_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
 // Workspace a plan's de-dispersion needs, and de-dispersion into a given
 // workspace (abi.cpp); used by entry points that supply their own workspace.
 size_t plan_workspace_bytes(const sps_plan* p);
+
+// Per-configuration sizes of a plan (plan.cpp).
+struct ConfigCheck {
+  int32_t dmax_b = 0, dmax_1 = 0, dmax_2 = 0;
+  std::vector<int32_t> tiles;  // step-two tiles
+};
+sps_status check_config(const sps_plan* p, const sps_kernel_config& cfg, ConfigCheck* out);
+sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg);
+sps_status run_search(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws, size_t ws_bytes,
+                      double* snr, int32_t* peak_t, int32_t* peak_val, int32_t* best, cudaStream_t st);
 sps_status dedisperse_into(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
                            size_t ws_bytes, cudaStream_t st);
 
@@ -136,6 +147,9 @@ struct sps_plan {
   int32_t* d_b0 = nullptr;
   uint32_t* d_offs = nullptr;
   int64_t pitch4 = 0;            // bytes per row of the shifted copies
+
+  int max_smem = 0;              // opt-in shared memory per block of the device
+  mutable std::map<int64_t, int32_t> spread_cache;  // tile delay spread by (table, rows)
 
   sps_kernel_config cfg{};
   // delay spread of one DM tile for the current configuration

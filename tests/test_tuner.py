@@ -1,0 +1,184 @@
+"""The auto-tuner: oracle pins, properties the paper states, and draw-for-draw
+parity of the library's C++ engine (sps_optimize) with the oracle (oracle/ga.py).
+Everything here is host code; no GPU is needed."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ga
+
+
+def _table_fitness(n_values, seed, ties=False):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = tuple(n_values)
+    t = rng.random(shape)
+    if ties:
+        t = np.round(t * 8) / 8  # many equal fitness values
+    return lambda p: float(t[tuple(p)]), t
+
+
+def _validity(n_values, seed, frac=0.7):
+    rng = np.random.Generator(np.random.PCG64(seed + 1000))
+    mask = rng.random(tuple(n_values)) < frac
+    mask[(0,) * len(n_values)] = True
+    return lambda p: bool(mask[tuple(p)]), mask
+
+
+# ----------------------------------------------------------------------------- oracle pins
+def test_splitmix64_published_outputs():
+    # Outputs of the SplitMix64 reference generator for seed 0 (Steele, Lea &
+    # Flood 2014; the constants of Vigna's public-domain splitmix64.c).
+    r = ga.SplitMix64(0)
+    assert [r.next_u64() for _ in range(4)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                                0x06C45D188009454F, 0xF88BB8A8724C81EC]
+
+
+def test_below_and_unit_are_uniform():
+    r = ga.SplitMix64(5)
+    counts = np.bincount([r.below(7) for _ in range(70000)], minlength=7)
+    assert counts.min() > 9500 and counts.max() < 10500
+    u = [r.unit() for _ in range(20000)]
+    assert 0.0 <= min(u) and max(u) < 1.0 and abs(np.mean(u) - 0.5) < 0.01
+
+
+def test_tournament_pool_is_twenty_percent():
+    # Sec. 4: the tournament pool is 20 % of N_pop (N_pop = 20 -> 4)
+    assert ga.tournament_pool_size(20, 0.2) == 4
+    assert ga.tournament_pool_size(32, 0.2) == 6
+    assert ga.tournament_pool_size(4, 0.2) == 2
+
+
+def test_exhaustive_finds_the_table_minimum_once_per_valid_point():
+    nv = [3, 4, 2, 5]
+    fit, t = _table_fitness(nv, 1)
+    valid, mask = _validity(nv, 1)
+    r = ga.exhaustive(ga.Space(nv, [0, 0, 1, 1], valid), fit)
+    pts = [p for p, _ in r.trace]
+    assert len(pts) == len(set(pts)) == int(mask.sum())
+    assert all(mask[p] for p in pts)
+    masked = np.where(mask, t, np.inf)
+    assert r.best_point == tuple(int(i) for i in np.unravel_index(np.argmin(masked), t.shape))
+    assert pts == sorted(pts)  # lexicographic order
+
+
+def test_random_search_never_repeats_and_respects_budget():
+    nv = [4, 4, 4]
+    fit, _ = _table_fitness(nv, 2)
+    valid, mask = _validity(nv, 2)
+    r = ga.random_search(ga.Space(nv, [0, 1, 2], valid), fit, max_evaluations=20, seed=9)
+    pts = [p for p, _ in r.trace]
+    assert len(pts) == 20 == len(set(pts)) and all(mask[p] for p in pts)
+
+
+@pytest.mark.parametrize("crossover", ["uniform", "one-point"])
+def test_ga_properties(crossover):
+    nv = [4, 3, 5, 2, 6, 3]
+    kernels = [0, 0, 0, 1, 1, 2]
+    fit, _ = _table_fitness(nv, 3)
+    valid, mask = _validity(nv, 3)
+    r = ga.genetic(ga.Space(nv, kernels, valid), fit, n_pop=10, crossover=crossover, max_evaluations=150, seed=4)
+    assert r.evaluations <= 150
+    assert all(mask[p] for p, _ in r.trace)  # boundary conditions always hold
+    best = [h[2] for h in r.history]
+    assert all(b2 <= b1 for b1, b2 in zip(best, best[1:]))  # the fittest parents survive
+    assert r.best_fitness == min(f for _, f in r.trace)
+
+
+def test_ga_without_operators_keeps_the_best_individual():
+    # pool = N_pop: every tournament picks the fittest; no crossover or mutation:
+    # offspring are copies of it, so nothing new is ever evaluated
+    nv = [5, 5, 5]
+    fit, _ = _table_fitness(nv, 5)
+    r = ga.genetic(ga.Space(nv, [0, 1, 2]), fit, n_pop=8, p_cross=0.0, p_mut=0.0, pool_fraction=1.0,
+                   max_evaluations=100, max_generations=5, seed=6)
+    assert r.evaluations == len({p for p, _ in r.trace}) <= 8
+    assert r.generations == 5
+
+
+def test_mutation_always_moves_a_gene_when_forced():
+    nv = [3, 3]
+    seen = []
+
+    def fit(p):
+        seen.append(p)
+        return float(p[0] + p[1])
+
+    ga.genetic(ga.Space(nv, [0, 1]), fit, n_pop=2, p_cross=0.0, p_mut=1.0, pool_fraction=1.0,
+               max_evaluations=9, max_generations=50, seed=7)
+    assert len(set(seen)) > 2  # forced mutation keeps producing new points
+
+
+def test_ga_beats_random_search_on_average():
+    # Sec. 5: on average the GA finds better configurations than pure random
+    # search with the same budget (separable landscape with a narrow optimum)
+    nv = [8, 8, 8, 8, 8]
+    rng = np.random.Generator(np.random.PCG64(11))
+    costs = [rng.random(8) for _ in nv]
+
+    def fit(p):
+        return float(sum(c[v] for c, v in zip(costs, p)))
+
+    sp = ga.Space(nv, [0, 0, 1, 1, 2])
+    g = [ga.genetic(sp, fit, n_pop=20, max_evaluations=300, seed=s).best_fitness for s in range(20)]
+    r = [ga.random_search(sp, fit, max_evaluations=300, seed=s).best_fitness for s in range(20)]
+    assert np.mean(g) < np.mean(r)
+
+
+# ----------------------------------------------------------------------------- parity with the library
+CASES = list(itertools.product(
+    [1, 2, 3],                     # seed
+    ["uniform", "one-point"],     # crossover
+    [(0.8, 0.1), (1.0, 1.0), (0.3, 0.5)],  # (p_cross, p_mut)
+    [False, True],                # validity constraints
+))
+
+
+@pytest.mark.parametrize("seed,crossover,rates,constrained", CASES)
+def test_library_ga_matches_oracle_draw_for_draw(lib, seed, crossover, rates, constrained):
+    nv = [4, 3, 5, 2, 6, 3, 4]
+    kernels = [0, 0, 0, 1, 1, 2, 2]
+    fit, _ = _table_fitness(nv, seed, ties=(seed == 2))
+    valid = _validity(nv, seed)[0] if constrained else None
+    kw = dict(n_pop=12, p_cross=rates[0], p_mut=rates[1], pool_fraction=0.2, max_evaluations=120,
+              max_generations=60, seed=seed)
+    want = ga.genetic(ga.Space(nv, kernels, valid), fit, crossover=crossover, **kw)
+    desc = lib.search_desc(algorithm=lib.TUNE_GA, population=12, p_cross=rates[0], p_mut=rates[1],
+                           pool_fraction=0.2, crossover=lib.CROSS_UNIFORM if crossover == "uniform" else
+                           lib.CROSS_ONE_POINT, max_evaluations=120, max_generations=60, seed=seed)
+    best, res, trace = lib.sps_optimize(nv, kernels, fit, valid, desc)
+    assert trace == [(tuple(p), f) for p, f in want.trace]
+    assert best == want.best_point and res.best_fitness == want.best_fitness
+    assert (res.evaluations, res.generations) == (want.evaluations, want.generations)
+
+
+@pytest.mark.parametrize("seed", [1, 8, 99])
+def test_library_random_and_exhaustive_match_oracle(lib, seed):
+    nv = [5, 4, 3, 4]
+    kernels = [0, 1, 1, 2]
+    fit, _ = _table_fitness(nv, seed)
+    valid = _validity(nv, seed)[0]
+    want = ga.random_search(ga.Space(nv, kernels, valid), fit, max_evaluations=40, seed=seed)
+    best, res, trace = lib.sps_optimize(nv, kernels, fit, valid,
+                                        lib.search_desc(algorithm=lib.TUNE_RANDOM, max_evaluations=40, seed=seed))
+    assert trace == [(tuple(p), f) for p, f in want.trace] and best == want.best_point
+    want = ga.exhaustive(ga.Space(nv, kernels, valid), fit)
+    best, res, trace = lib.sps_optimize(nv, kernels, fit, valid, lib.search_desc(algorithm=lib.TUNE_EXHAUSTIVE))
+    assert trace == [(tuple(p), f) for p, f in want.trace] and best == want.best_point
+
+
+def test_library_optimize_penalties_and_errors(lib):
+    # +inf (a failed configuration) never wins; a bad space or population is rejected
+    def fit(p):
+        return math.inf if p[0] == 0 else float(p[0] + p[1])
+
+    best, res, _ = lib.sps_optimize([4, 4], [0, 1], fit, None,
+                                    lib.search_desc(algorithm=lib.TUNE_EXHAUSTIVE))
+    assert best == (1, 0) and res.best_fitness == 1.0
+    with pytest.raises(lib.SpsError):
+        lib.sps_optimize([4, 4], [1, 0], fit)  # kernel_of not non-decreasing
+    with pytest.raises(lib.SpsError):
+        lib.sps_optimize([4, 4], [0, 1], fit, None, lib.search_desc(population=7))
+    with pytest.raises(lib.SpsError):
+        lib.sps_optimize([2], [0], lambda p: math.inf, None, lib.search_desc(algorithm=lib.TUNE_EXHAUSTIVE))
