@@ -62,6 +62,7 @@ U8PassArgs u8_args(const sps_plan* p, const uint8_t* x, int64_t pitch, const uin
   a.offs = p->d_offs;
   a.channels = p->channels;
   a.status = p->d_status;
+  a.one = 1u;
   return a;
 }
 

@@ -20,9 +20,12 @@
 //     chunk's shared-memory offset table arrive by bulk asynchronous copies
 //     (TMA) into a two-stage ring guarded by mbarriers, so the warps only add.
 //   * SWAR: a word of 4 samples is split into even and odd bytes in 16-bit
-//     lanes (one AND, one byte permute) and two channels are added per 3-input
-//     add.  16-bit lanes stay exact for 257 channels of 255; partial sums are
-//     folded into int32 registers every <= 256 channels.
+//     lanes (one AND, one byte permute: the integer ALU pipe, 64 lanes per SM)
+//     and the lanes are accumulated with integer multiply-adds by 1 on the FMA
+//     pipe, which the ALU work would otherwise saturate.  16-bit lanes stay
+//     exact for 257 channels of 255; partial sums are folded into int32
+//     registers every <= 256 channels.
+//   * Shared loads use 32-bit shared-window addresses with immediate offsets.
 //   * The offset of (trial, channel) inside the staged windows does not depend
 //     on the time tile (tiles start at multiples of 128), so the plan
 //     precomputes it once per configuration.
@@ -38,6 +41,23 @@ constexpr uint32_t kEvenBytes = 0x00FF00FFu;
 constexpr int kMaxThreads = 512;
 
 __device__ __forceinline__ uint32_t odd_bytes(uint32_t w) { return __byte_perm(w, 0u, 0x4341); }
+
+// c + a * one with one == 1 known only at run time: an integer multiply-add on
+// the FMA pipe instead of an add on the integer ALU pipe.
+__device__ __forceinline__ uint32_t madd(uint32_t a, uint32_t one, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(one), "r"(c));
+  return d;
+}
+
+// NW words at shared address addr + 128 * m, m < NW (immediate offsets).
+template <int NW, int M = 0>
+__device__ __forceinline__ void lds_row(uint32_t addr, uint32_t (&w)[NW]) {
+  if constexpr (M < NW) {
+    asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(w[M]) : "r"(addr), "n"(M * 128));
+    lds_row<NW, M + 1>(addr, w);
+  }
+}
 
 template <int ND, int NW>
 __global__ void __launch_bounds__(kMaxThreads, 1)
@@ -63,6 +83,7 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
   const int n_chunks = (G + cc_max - 1) / cc_max;
   const int pairs = (G + 1) >> 1;
   const uint32_t toff = (uint32_t)(t_sub * 128 * NW + lane * 4);
+  const uint32_t one = a.one;
 
   for (int c = tid; c < G; c += blockDim.x) b0s[c] = a.b0[(int64_t)tile * a.channels + c_lo + c];
   if (tid == 0) {
@@ -144,8 +165,7 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
     if (pending + cc > 256) { fold(); pending = 0; }
     if (!mbar_wait(&bars[st], (ch >> 1) & 1, a.status)) aborted = 1;
     if (!aborted) {
-      // 32-bit offsets into the shared window keep addressing in the shared space
-      const uint32_t base = (uint32_t)(st * stage_bytes) + toff;
+      const uint32_t base = smem_u32(smem) + (uint32_t)(st * stage_bytes) + toff;
       const uint2* tb = reinterpret_cast<const uint2*>(smem + st * stage_bytes + 4 * copy_stride) + dm_sub * ND;
       int cl = 0;
       for (; cl + 1 < cc; cl += 2) {
@@ -153,13 +173,13 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
 #pragma unroll
         for (int r = 0; r < ND; r++) {
           const uint2 o = e[r];
-          const uint32_t a1 = base + o.x, a2 = base + o.y;
+          uint32_t W1[NW], W2[NW];
+          lds_row<NW>(base + o.x, W1);
+          lds_row<NW>(base + o.y, W2);
 #pragma unroll
           for (int m = 0; m < NW; m++) {
-            const uint32_t w1 = *reinterpret_cast<const uint32_t*>(smem + (a1 + 128u * m));
-            const uint32_t w2 = *reinterpret_cast<const uint32_t*>(smem + (a2 + 128u * m));
-            lo[r][m] += (w1 & kEvenBytes) + (w2 & kEvenBytes);
-            hi[r][m] += odd_bytes(w1) + odd_bytes(w2);
+            lo[r][m] = madd(W2[m] & kEvenBytes, one, madd(W1[m] & kEvenBytes, one, lo[r][m]));
+            hi[r][m] = madd(odd_bytes(W2[m]), one, madd(odd_bytes(W1[m]), one, hi[r][m]));
           }
         }
       }
@@ -167,12 +187,12 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
         const uint2* e = tb + (cl >> 1) * a.di_pad;
 #pragma unroll
         for (int r = 0; r < ND; r++) {
-          const uint32_t a1 = base + e[r].x;
+          uint32_t W1[NW];
+          lds_row<NW>(base + e[r].x, W1);
 #pragma unroll
           for (int m = 0; m < NW; m++) {
-            const uint32_t w1 = *reinterpret_cast<const uint32_t*>(smem + (a1 + 128u * m));
-            lo[r][m] += w1 & kEvenBytes;
-            hi[r][m] += odd_bytes(w1);
+            lo[r][m] = madd(W1[m] & kEvenBytes, one, lo[r][m]);
+            hi[r][m] = madd(odd_bytes(W1[m]), one, hi[r][m]);
           }
         }
       }

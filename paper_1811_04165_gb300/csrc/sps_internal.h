@@ -45,6 +45,7 @@ struct U8PassArgs {
   void* out;               // int32 rows (brute) or uint16 rows (step one)
   int32_t out_u16;         // 1: write uint16 sums (step one)
   uint32_t* status;        // device status word (bounded-wait timeouts)
+  uint32_t one;            // 1, passed at run time (see madd in dedisperse_u8.cu)
 };
 
 // Step two over uint16 subband series.
