@@ -73,6 +73,11 @@ class Space:
     kernel_of: list           # kernel index per gene (non-decreasing)
     valid: object = None      # callable(point tuple) -> bool; None = all valid
 
+    def __post_init__(self):
+        # plain Python integers: the generator's arithmetic is exact big-integer math
+        self.n_values = [int(v) for v in self.n_values]
+        self.kernel_of = [int(k) for k in self.kernel_of]
+
     def kernels(self):
         out = {}
         for g, k in enumerate(self.kernel_of):

@@ -1,0 +1,99 @@
+"""Live auto-tuning on the GPU through the C ABI: the plan's gene space, the
+mapping of points to kernel configurations, and GA / random / exhaustive
+search with measured kernel time as fitness (Sec. 3.2, Sec. 4).  Every tuned
+configuration must give the same (exact) results."""
+import numpy as np
+import pytest
+
+from oracle import ga
+from paper_1811_04165_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def tiny_subband():
+    """The tiny 64-channel search run through the paper's two-step pipeline:
+    8 subbands, 4 coarse DMs (0, 16, 32, 48) for the 32 trials."""
+    wl = synth.tiny_brute()
+    wl.n_subbands = 8
+    wl.coarse_dms = wl.dms[::8].copy()
+    wl.name = "tiny-64ch-4096s-32dm-subband8"
+    return wl
+
+
+def _setup(lib, wl):
+    import torch
+    p = lib.Plan.from_workload(wl)
+    x = synth.filterbank(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, p.input_samples, wl.seed, wl.pulses,
+                         pitch=p.pitch)
+    return p, torch.from_numpy(x).cuda()
+
+
+def test_reduced_space_has_5000_valid_points(lib):
+    p, _ = _setup(lib, tiny_subband())
+    nv, ko, vals = lib.sps_tune_space(p, lib.SPACE_REDUCED)
+    assert int(np.prod(nv)) == 5000 and list(ko) == sorted(ko)
+    valid = 0
+    for pt in np.ndindex(*nv):
+        try:
+            lib.sps_tune_config(p, lib.SPACE_REDUCED, pt)
+            valid += 1
+        except lib.SpsError:
+            pass
+    assert valid == 5000
+
+
+def test_full_space_configs_map_and_validate(lib):
+    p, _ = _setup(lib, synth.apertif_beam())
+    nv, ko, vals = lib.sps_tune_space(p, lib.SPACE_FULL)
+    assert len(nv) == 6 and list(ko) == [0, 0, 0, 0, 0, 1]
+    c = lib.sps_tune_config(p, lib.SPACE_FULL, [2, 2, 3, 0, 3, 3])
+    assert c.brute.as_tuple() == (4, 16, 8, 1, 16) and c.snr.threads == 256
+    with pytest.raises(lib.SpsError):  # 16 x 16 warps: too many threads
+        lib.sps_tune_config(p, lib.SPACE_FULL, [0, 0, 4, 4, 0, 0])
+
+
+def test_live_ga_tuning_keeps_results_exact(lib):
+    import torch
+    wl = tiny_subband()
+    p, x = _setup(lib, wl)
+    want = p.search(x)
+    torch.cuda.synchronize()
+    ref = {k: v.clone() for k, v in want.items()}
+    desc = lib.search_desc(algorithm=lib.TUNE_GA, population=8, max_evaluations=24, seed=3)
+    best, res, trace = lib.sps_tune(p, x, which=lib.SPACE_FULL, desc=desc, reps=2)
+    assert res.evaluations == len(trace) <= 24 and np.isfinite(res.best_fitness)
+    assert res.best_fitness == min(f for _, f in trace)
+    # the plan now runs the best configuration; results are unchanged
+    cfg = lib.sps_tune_config(p, lib.SPACE_FULL, best)
+    assert p.config.as_dict() == cfg.as_dict()
+    got = p.search(x)
+    torch.cuda.synchronize()
+    for k in ("D", "peak_t", "peak_val", "best"):
+        assert torch.equal(got[k], ref[k]), k
+    assert torch.allclose(got["snr"], ref["snr"], rtol=1e-12, atol=0)
+
+
+def test_exhaustive_reduced_space_and_ga_on_its_table(lib):
+    """Config 3 in miniature: exhaustive search of the reduced 5000-point joint
+    space with live timings, then GA and pure random search replayed on the
+    measured table with equal budgets (10 % of the evaluations)."""
+    wl = tiny_subband()
+    p, x = _setup(lib, wl)
+    desc = lib.search_desc(algorithm=lib.TUNE_EXHAUSTIVE)
+    best, res, trace = lib.sps_tune(p, x, which=lib.SPACE_REDUCED, desc=desc, reps=2)
+    assert res.evaluations == 5000 == len(trace)
+    table = {pt: f for pt, f in trace}
+    opt = min(table.values())
+    assert res.best_fitness == opt and np.isfinite(opt)
+    nv, ko, _ = lib.sps_tune_space(p, lib.SPACE_REDUCED)
+    space = ga.Space(list(nv), list(ko))
+    ga_best = [ga.genetic(space, table.__getitem__, n_pop=32, max_evaluations=500, seed=s).best_fitness
+               for s in range(10)]
+    rnd_best = [ga.random_search(space, table.__getitem__, max_evaluations=500, seed=s).best_fitness
+                for s in range(10)]
+    assert min(ga_best) >= opt and min(rnd_best) >= opt
+    # the library's engine on the same table agrees with the oracle
+    b, r, _ = lib.sps_optimize(nv, ko, table.__getitem__, None,
+                               lib.search_desc(population=32, max_evaluations=500, seed=0))
+    assert r.best_fitness == ga_best[0]
