@@ -136,6 +136,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(loaded)}
 
 
+def profiled_traffic(kernel_src: str, summary: str):
+    """DRAM bytes per launch recorded in a profile summary, or None when the
+    kernel's source has changed since the counters were taken."""
+    import hashlib
+    import re
+    try:
+        data = open(os.path.join(ROOT, kernel_src), "rb").read()
+        text = open(os.path.join(ROOT, summary)).read()
+    except OSError:
+        return None
+    blob = hashlib.sha1(b"blob %d\0" % len(data) + data).hexdigest()
+    t = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+    b = re.search(r"traffic_source_blob: ([0-9a-f]+)", text)
+    return int(t.group(1)) if t and b and b.group(1) == blob else None
+
+
 def cpu_oracle_rate(wl, x, target_s=12.0, max_rows=None):
     """DM-trial samples/s of the oracle (dedispersion + S/N) on a bounded row sample."""
     import oracle
@@ -259,8 +275,11 @@ def main():
     dd_ms = statistics.mean(dedisp_ms)
     peak_tadd = N_SM * INT32_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     achieved = adds / (dd_ms * 1e-3) / 1e12
+    traffic = profiled_traffic("paper_1811_04165_gb300/csrc/dedisperse_u8.cu",
+                               "profiles/u8_pass_brute_apertif_2048dm.md") if args.dms == 2048 else None
     roofline = {"bound": "alu", "kernel": "u8_pass_kernel (brute force)", "achieved": achieved, "peak": peak_tadd,
-                "unit": "Tadd/s", "frac": achieved / peak_tadd, "traffic": None,
+                "unit": "Tadd/s", "frac": achieved / peak_tadd, "traffic": traffic,
+                "algorithmic_bytes_per_launch": wl.channels * pitch + 4 * wl.dm_trial_samples,
                 "algorithmic_adds_per_launch": adds, "ms_per_launch": dd_ms,
                 "peak_derivation": "152 SMs x 128 INT32 lanes/clk x 2070 MHz"}
 
