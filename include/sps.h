@@ -84,13 +84,16 @@ typedef struct {
 /* Launch and tiling parameters of one de-dispersion kernel (the Table 3 genes,
  * re-cast for sm_103a).  Block tile = (warps_dm * dms_per_thread) DMs by
  * (warps_time * 32 * samples_per_thread) samples; channels (or subbands) are
- * staged through shared memory `chunk` at a time. */
+ * staged through shared memory `chunk` at a time.  `pairs` (brute force and
+ * step one; binary like the paper's localMem gene) selects the kernel that sums
+ * pre-added adjacent-channel pairs instead of single channels; both are exact. */
 typedef struct {
   int32_t dms_per_thread;     /* register tile along DM                            */
   int32_t samples_per_thread; /* register tile along time (4*k for the uint8 path)  */
   int32_t warps_dm;           /* warps of a block along DM                          */
   int32_t warps_time;         /* warps of a block along time                        */
   int32_t chunk;              /* channels (subbands) staged per shared-memory pass  */
+  int32_t pairs;              /* 1: pre-summed channel pairs; 0: single channels    */
 } sps_dedisp_config;
 
 /* Launch parameters of the fused boxcar + S/N kernel. */
@@ -128,9 +131,12 @@ sps_status sps_plan_delay_table(const sps_plan* plan, int32_t* host_out);
 /* SUBBAND mode: host copies of d1 [n_coarse][channels] and d2 [n_dms][n_subbands]. */
 sps_status sps_plan_subband_tables(const sps_plan* plan, int32_t* host_d1, int32_t* host_d2);
 
-/* Bytes of device workspace sps_dedisperse / sps_search need: three copies of
- * the batch shifted by 1, 2 and 3 samples (3 * channels * N_in rounded up to
- * 16), plus, in SUBBAND mode, the step-one output Y. */
+/* Bytes of device workspace that sps_dedisperse / sps_search need under any
+ * kernel configuration: the staged form of the batch (three copies shifted by
+ * 1, 2 and 3 samples for the single-channel kernel, or the pre-summed pair
+ * series for the pair kernel, whichever is larger), plus, in SUBBAND mode, the
+ * step-one output Y.  The calls themselves accept any workspace at least as
+ * large as the current configuration uses. */
 sps_status sps_plan_workspace_bytes(const sps_plan* plan, size_t* bytes);
 
 sps_status sps_plan_get_config(const sps_plan* plan, sps_kernel_config* out);
@@ -157,8 +163,10 @@ sps_status sps_dedisperse(const sps_plan* plan, const uint8_t* x, int64_t x_pitc
  * counterpart; this is a library convenience.
  * Same inputs, outputs and results as sps_dedisperse.  The workspace comes
  * from a file-scope device array of 96 MiB (enough for the brute-force search
- * of one 1536-channel, 1.024 s beam, not for its subband path); plans that
- * need more are rejected with UNSUPPORTED and a message giving both sizes.
+ * of one 1536-channel, 1.024 s beam with the single-channel kernel, pairs = 0:
+ * 79 MB; not for the pair kernel's series, 236 MB, nor for the subband path);
+ * plans whose current configuration needs more are rejected with UNSUPPORTED
+ * and a message giving both sizes.
  * Allocates nothing.  Every device that loads this entry point keeps the
  * array until the process exits.  All calls on a device share the array:
  * calls whose work overlaps on the GPU (other streams or threads) race and

@@ -1,4 +1,5 @@
 // extern "C" entry points of libsps.so: argument checks, then kernel launches.
+#include <algorithm>
 #include <cstring>
 #include <string>
 
@@ -40,15 +41,28 @@ sps_status check_x(const sps_plan* p, const uint8_t* x, int64_t pitch) {
   return SPS_OK;
 }
 
-// Workspace layout: the three shifted copies of the batch (both modes), then,
-// in SUBBAND mode, the step-one output Y.
+// Workspace layout: the staged form of the batch -- three shifted copies of x
+// (single-channel kernel) or the pair-sum series (pair kernel) -- then, in
+// SUBBAND mode, the step-one output Y.  workspace_needed is what the current
+// configuration uses; sps_plan_workspace_bytes reports the larger of the two
+// forms so that a buffer of that size fits any configuration.
 size_t x4_bytes(const sps_plan* p) { return (size_t)3 * p->channels * p->pitch4; }
 
-size_t y_offset(const sps_plan* p) { return (x4_bytes(p) + 255) / 256 * 256; }
+size_t q_bytes(const sps_plan* p) { return (size_t)p->max_pair_series * 2 * p->q_pitch * sizeof(uint16_t); }
 
-size_t workspace_needed(const sps_plan* p) {
-  if (p->mode != SPS_MODE_SUBBAND) return x4_bytes(p);
-  return y_offset(p) + (size_t)p->coarse_dms.size() * p->n_subbands * p->y_pitch * sizeof(uint16_t);
+size_t y_bytes(const sps_plan* p) {
+  return p->mode == SPS_MODE_SUBBAND ? (size_t)p->coarse_dms.size() * p->n_subbands * p->y_pitch * sizeof(uint16_t)
+                                     : 0;
+}
+
+bool uses_pairs(const sps_plan* p) { return p->mode == SPS_MODE_BRUTE ? p->cfg.brute.pairs : p->cfg.step1.pairs; }
+
+size_t y_offset(const sps_plan* p) { return ((uses_pairs(p) ? q_bytes(p) : x4_bytes(p)) + 255) / 256 * 256; }
+
+size_t workspace_needed(const sps_plan* p) { return y_offset(p) + y_bytes(p); }
+
+size_t workspace_any_config(const sps_plan* p) {
+  return (std::max(x4_bytes(p), q_bytes(p)) + 255) / 256 * 256 + y_bytes(p);
 }
 
 U8PassArgs u8_args(const sps_plan* p, const uint8_t* x, int64_t pitch, const uint8_t* x4) {
@@ -66,21 +80,52 @@ U8PassArgs u8_args(const sps_plan* p, const uint8_t* x, int64_t pitch, const uin
   return a;
 }
 
-sps_status run_step1(const sps_plan* p, const uint8_t* x, int64_t pitch, uint8_t* x4, uint16_t* Y,
-                     cudaStream_t st) {
-  sps_status s = launch_expand(x, pitch, (int32_t)p->n_in, p->channels, x4, p->pitch4, st);
+// One uint8 pass (brute force or step one) with the configured kernel.
+sps_status run_u8_pass(const sps_plan* p, const sps_dedisp_config& cfg, const uint8_t* x, int64_t pitch,
+                       uint8_t* ws, int32_t rows, int32_t per, int32_t n_out, int64_t out_pitch, int32_t dmax,
+                       void* out, int32_t out_u16, cudaStream_t st) {
+  if (cfg.pairs) {
+    uint16_t* q = reinterpret_cast<uint16_t*>(ws);
+    sps_status s = launch_pair_series(x, pitch, (int32_t)p->n_in, p->d_pair_series, p->n_pair_series, q,
+                                      p->q_pitch, st);
+    if (s) return s;
+    PairPassArgs a{};
+    a.q = q;
+    a.q_pitch = p->q_pitch;
+    a.slots = p->d_pair_slots;
+    a.slots_max = p->pair_slots_max;
+    a.offs = p->d_pair_offs;
+    a.di_pad = pair_di_pad(cfg);
+    a.n_dm = rows;
+    a.n_groups = p->channels / per;
+    a.group_pairs = (per + 1) / 2;
+    a.n_out = n_out;
+    a.out_pitch = out_pitch;
+    a.dmax_tile = dmax;
+    a.out = out;
+    a.out_u16 = out_u16;
+    a.status = p->d_status;
+    return launch_pair_pass(a, cfg, st);
+  }
+  sps_status s = launch_expand(x, pitch, (int32_t)p->n_in, p->channels, ws, p->pitch4, st);
   if (s) return s;
-  U8PassArgs a = u8_args(p, x, pitch, x4);
-  a.di_pad = u8_di_pad(p->cfg.step1);
-  a.n_dm = (int32_t)p->coarse_dms.size();
-  a.group_channels = p->channels / p->n_subbands;
-  a.n_groups = p->n_subbands;
-  a.n_out = (int32_t)p->n_1;
-  a.out_pitch = p->y_pitch;
-  a.dmax_tile = p->dmax_step1;
-  a.out = Y;
-  a.out_u16 = 1;
-  return launch_u8_pass(a, p->cfg.step1, st);
+  U8PassArgs a = u8_args(p, x, pitch, ws);
+  a.di_pad = u8_di_pad(cfg);
+  a.n_dm = rows;
+  a.group_channels = per;
+  a.n_groups = p->channels / per;
+  a.n_out = n_out;
+  a.out_pitch = out_pitch;
+  a.dmax_tile = dmax;
+  a.out = out;
+  a.out_u16 = out_u16;
+  return launch_u8_pass(a, cfg, st);
+}
+
+sps_status run_step1(const sps_plan* p, const uint8_t* x, int64_t pitch, uint8_t* ws, uint16_t* Y,
+                     cudaStream_t st) {
+  return run_u8_pass(p, p->cfg.step1, x, pitch, ws, (int32_t)p->coarse_dms.size(), p->channels / p->n_subbands,
+                     (int32_t)p->n_1, p->y_pitch, p->dmax_step1, Y, 1, st);
 }
 
 sps_status run_step2(const sps_plan* p, const uint16_t* Y, int32_t* D, cudaStream_t st) {
@@ -112,20 +157,9 @@ sps_status run_dedisperse(const sps_plan* p, const uint8_t* x, int64_t pitch, in
   if (!D || !aligned16(D)) return fail(SPS_ERR_INVALID_ARG, "D must be non-null and 16-byte aligned");
   if ((s = check_workspace(p, ws, ws_bytes))) return s;
   uint8_t* x4 = static_cast<uint8_t*>(ws);
-  if (p->mode == SPS_MODE_BRUTE) {
-    if ((s = launch_expand(x, pitch, (int32_t)p->n_in, p->channels, x4, p->pitch4, st))) return s;
-    U8PassArgs a = u8_args(p, x, pitch, x4);
-    a.di_pad = u8_di_pad(p->cfg.brute);
-    a.n_dm = (int32_t)p->dms.size();
-    a.group_channels = p->channels;
-    a.n_groups = 1;
-    a.n_out = p->n_t;
-    a.out_pitch = p->n_t;
-    a.dmax_tile = p->dmax_brute;
-    a.out = D;
-    a.out_u16 = 0;
-    return launch_u8_pass(a, p->cfg.brute, st);
-  }
+  if (p->mode == SPS_MODE_BRUTE)
+    return run_u8_pass(p, p->cfg.brute, x, pitch, x4, (int32_t)p->dms.size(), p->channels, p->n_t, p->n_t,
+                       p->dmax_brute, D, 0, st);
   uint16_t* Y = reinterpret_cast<uint16_t*>(x4 + y_offset(p));
   if ((s = run_step1(p, x, pitch, x4, Y, st))) return s;
   return run_step2(p, Y, D, st);
@@ -190,6 +224,9 @@ sps_status sps_plan_destroy(sps_plan* p) {
   cudaFree(p->d_status);
   cudaFree(p->d_b0);
   cudaFree(p->d_offs);
+  cudaFree(p->d_pair_series);
+  cudaFree(p->d_pair_slots);
+  cudaFree(p->d_pair_offs);
   if (swap) cudaSetDevice(cur);
   delete p;
   return SPS_OK;
@@ -229,7 +266,7 @@ sps_status sps_plan_workspace_bytes(const sps_plan* p, size_t* bytes) {
   clear_error();
   if (sps_status s = check_plan(p)) return s;
   if (!bytes) return fail(SPS_ERR_INVALID_ARG, "null output");
-  *bytes = workspace_needed(p);
+  *bytes = workspace_any_config(p);
   return SPS_OK;
 }
 

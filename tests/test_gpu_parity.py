@@ -88,11 +88,19 @@ CONFIGS = [  # (dms_per_thread, samples_per_thread, warps_dm, warps_time, chunk)
 ]
 
 
-@pytest.mark.parametrize("cfg", CONFIGS)
+PAIR_CONFIGS = [  # (dms_per_thread, samples_per_thread, warps_dm, warps_time, chunk, pairs=1)
+    (1, 4, 1, 1, 2, 1), (1, 8, 2, 2, 6, 1), (2, 4, 4, 2, 16, 1), (2, 32, 2, 1, 8, 1), (4, 8, 2, 2, 10, 1),
+    (4, 16, 8, 1, 8, 1), (8, 4, 2, 4, 8, 1), (8, 8, 4, 2, 4, 1), (1, 32, 16, 1, 4, 1), (4, 8, 4, 4, 6, 1),
+]
+
+
+@pytest.mark.parametrize("cfg", CONFIGS + PAIR_CONFIGS)
 def test_brute_configs_ragged(lib, cfg):
-    # 37 channels (odd, not a multiple of any chunk), 29 DMs, 1003 samples: ragged everywhere
+    # 37 channels (odd, not a multiple of any chunk), 29 DMs, 1003 samples: ragged everywhere.
+    # The pair kernel gets a finer DM grid: with 5.4 MHz channels a coarse grid
+    # spreads the pair delay differences too far for one tile's staging.
     torch = _torch()
-    dms = synth.dm_grid(29, 3.1)
+    dms = synth.dm_grid(29, 0.31 if len(cfg) > 5 and cfg[5] else 3.1)
     p = lib.Plan(37, 1300.0, 1500.0, 65.536e-6, 1003, dms, [1, 3, 8, 50])
     c = p.config
     c.brute = lib.DedispConfig(*cfg)
@@ -117,6 +125,13 @@ def test_brute_saturated_and_edges(lib):
     lib.sps_dedisperse(p, torch.from_numpy(x).cuda(), D)
     torch.cuda.synchronize()
     assert np.all(_to_np(D) == 255 * C)
+    c = p.config
+    c.brute = lib.DedispConfig(4, 16, 8, 1, 4, 1)  # pair sums at their limit: 128 pairs of 510 per 16-bit lane
+    p.config = c
+    D.fill_(0)
+    lib.sps_dedisperse(p, torch.from_numpy(x).cuda(), D)
+    torch.cuda.synchronize()
+    assert np.all(_to_np(D) == 255 * C)
     # a single channel, single DM, single sample
     p1 = lib.Plan(1, 1250.0, 1550.0, 81.92e-6, 1, [0.0], [1])
     x1 = np.zeros((1, 16), np.uint8)
@@ -127,11 +142,15 @@ def test_brute_saturated_and_edges(lib):
     assert _to_np(D1).tolist() == [[201]]
 
 
-def test_apertif_brute_sampled_rows(lib):
-    """Full Apertif-shaped beam in the launch configuration the benchmark times."""
+@pytest.mark.parametrize("pairs", [0, 1])
+def test_apertif_brute_sampled_rows(lib, pairs):
+    """Full Apertif-shaped beam in the launch configurations the benchmark times."""
     torch = _torch()
     wl = synth.apertif_beam()
     p = lib.Plan.from_workload(wl)
+    c = p.config
+    c.brute.pairs = pairs
+    p.config = c
     x = _x_for(p, wl)
     out = p.search(torch.from_numpy(x).cuda())
     torch.cuda.synchronize()
@@ -194,6 +213,10 @@ def test_subband_small_exact(lib, S):
 
 
 @pytest.mark.parametrize("cfg1,cfg2", [
+    # pair kernel on 4.7 MHz channels: delta ranges are wide, so one pair per chunk
+    ((1, 4, 1, 1, 2, 1), (1, 4, 1, 1, 1)),
+    ((4, 16, 8, 1, 2, 1), (4, 16, 8, 1, 8)),
+    ((2, 8, 2, 2, 2, 1), (8, 4, 4, 2, 5)),
     ((1, 4, 1, 1, 2), (1, 4, 1, 1, 1)),
     ((2, 8, 2, 2, 6), (2, 8, 2, 2, 3)),
     ((4, 16, 8, 1, 16), (8, 4, 4, 2, 5)),
@@ -219,10 +242,14 @@ def test_subband_configs(lib, cfg1, cfg2):
     assert np.array_equal(_to_np(D), Do)
 
 
-def test_apertif_subband_sampled(lib):
+@pytest.mark.parametrize("pairs", [0, 1])
+def test_apertif_subband_sampled(lib, pairs):
     torch = _torch()
     wl = synth.apertif_beam(subband=True)
     p = lib.Plan.from_workload(wl)
+    c = p.config
+    c.step1.pairs = pairs
+    p.config = c
     x = _x_for(p, wl)
     xd = torch.from_numpy(x).cuda()
     Y = torch.empty(p.y_shape, dtype=torch.uint16, device="cuda")
@@ -338,7 +365,7 @@ def test_argument_errors(lib):
         ps = lib.Plan.from_workload(wl)
         xs = torch.zeros((wl.channels, ps.pitch), dtype=torch.uint8, device="cuda")
         Ds = torch.empty((wl.dms.size, wl.n_t), dtype=torch.int32, device="cuda")
-        small = torch.empty(ps.workspace_bytes - 16, dtype=torch.uint8, device="cuda")
+        small = torch.empty(1024, dtype=torch.uint8, device="cuda")  # far below what the plan needs
         import ctypes
         assert L.sps_dedisperse(ps.handle, ctypes.c_void_p(xs.data_ptr()), ps.pitch,
                                 ctypes.c_void_p(Ds.data_ptr()), None, 0, None) == 1

@@ -46,11 +46,11 @@ def test_reduced_space_has_5000_valid_points(lib):
 def test_full_space_configs_map_and_validate(lib):
     p, _ = _setup(lib, synth.apertif_beam())
     nv, ko, vals = lib.sps_tune_space(p, lib.SPACE_FULL)
-    assert len(nv) == 6 and list(ko) == [0, 0, 0, 0, 0, 1]
-    c = lib.sps_tune_config(p, lib.SPACE_FULL, [2, 2, 3, 0, 3, 3])
-    assert c.brute.as_tuple() == (4, 16, 8, 1, 16) and c.snr.threads == 256
+    assert len(nv) == 7 and list(ko) == [0, 0, 0, 0, 0, 0, 1]
+    c = lib.sps_tune_config(p, lib.SPACE_FULL, [2, 2, 3, 0, 3, 1, 3])
+    assert c.brute.as_tuple() == (4, 16, 8, 1, 16, 1) and c.snr.threads == 256
     with pytest.raises(lib.SpsError):  # 16 x 16 warps: too many threads
-        lib.sps_tune_config(p, lib.SPACE_FULL, [0, 0, 4, 4, 0, 0])
+        lib.sps_tune_config(p, lib.SPACE_FULL, [0, 0, 4, 4, 0, 0, 0])
 
 
 def test_live_ga_tuning_keeps_results_exact(lib):
