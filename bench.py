@@ -275,9 +275,13 @@ def main():
     dd_ms = statistics.mean(dedisp_ms)
     peak_tadd = N_SM * INT32_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     achieved = adds / (dd_ms * 1e-3) / 1e12
-    traffic = profiled_traffic("paper_1811_04165_gb300/csrc/dedisperse_u8.cu",
-                               "profiles/u8_pass_brute_apertif_2048dm.md") if args.dms == 2048 else None
-    roofline = {"bound": "alu", "kernel": "u8_pass_kernel (brute force)", "achieved": achieved, "peak": peak_tadd,
+    pairs = bool(plan.config.brute.pairs)
+    kernel = "pair_pass_kernel" if pairs else "u8_pass_kernel"
+    src = "dedisperse_pair.cu" if pairs else "dedisperse_u8.cu"
+    traffic = profiled_traffic("paper_1811_04165_gb300/csrc/" + src,
+                               f"profiles/{kernel.split('_kernel')[0]}_brute_apertif_2048dm.md") if args.dms == 2048 else None
+    roofline = {"bound": "alu", "kernel": kernel + " (brute force, incl. its pre-pass)", "achieved": achieved,
+                "peak": peak_tadd,
                 "unit": "Tadd/s", "frac": achieved / peak_tadd, "traffic": traffic,
                 "algorithmic_bytes_per_launch": wl.channels * pitch + 4 * wl.dm_trial_samples,
                 "algorithmic_adds_per_launch": adds, "ms_per_launch": dd_ms,
@@ -288,7 +292,8 @@ def main():
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": workload_config(wl, "brute"),
             "kernels_ms": {"dedisperse": dd_ms, "snr_detect": statistics.mean(snr_ms)},
-            "real_time_beams": 1024.0 / ms_per_step, "gpu_launches": 3 * args.steps,
+            "kernel_config": plan.config.as_dict(),
+            "real_time_beams": 1024.0 / ms_per_step, "gpu_launches": 4 * args.steps,
             "roofline": roofline, "clocks": clk.summary()}
 
     # ---- the two-step subband path on the same batch
