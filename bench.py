@@ -275,11 +275,12 @@ def main():
     dd_ms = statistics.mean(dedisp_ms)
     peak_tadd = N_SM * INT32_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     achieved = adds / (dd_ms * 1e-3) / 1e12
-    pairs = bool(plan.config.brute.pairs)
-    kernel = "pair_pass_kernel" if pairs else "u8_pass_kernel"
-    src = "dedisperse_pair.cu" if pairs else "dedisperse_u8.cu"
-    traffic = profiled_traffic("paper_1811_04165_gb300/csrc/" + src,
-                               f"profiles/{kernel.split('_kernel')[0]}_brute_apertif_2048dm.md") if args.dms == 2048 else None
+    presum = plan.config.brute.presum
+    kernel = "presum_pass_kernel" if presum else "u8_pass_kernel"
+    src = "dedisperse_presum.cu" if presum else "dedisperse_u8.cu"
+    summary = f"profiles/presum{1 << presum}_pass_brute_apertif_2048dm.md" if presum else \
+        "profiles/u8_pass_brute_apertif_2048dm.md"
+    traffic = profiled_traffic("paper_1811_04165_gb300/csrc/" + src, summary) if args.dms == 2048 else None
     roofline = {"bound": "alu", "kernel": kernel + " (brute force, incl. its pre-pass)", "achieved": achieved,
                 "peak": peak_tadd,
                 "unit": "Tadd/s", "frac": achieved / peak_tadd, "traffic": traffic,

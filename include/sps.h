@@ -84,16 +84,17 @@ typedef struct {
 /* Launch and tiling parameters of one de-dispersion kernel (the Table 3 genes,
  * re-cast for sm_103a).  Block tile = (warps_dm * dms_per_thread) DMs by
  * (warps_time * 32 * samples_per_thread) samples; channels (or subbands) are
- * staged through shared memory `chunk` at a time.  `pairs` (brute force and
- * step one; binary like the paper's localMem gene) selects the kernel that sums
- * pre-added adjacent-channel pairs instead of single channels; both are exact. */
+ * staged through shared memory `chunk` at a time.  `presum` (brute force and
+ * step one) selects the kernel: 0 sums single channels; 1 and 2 sum series of
+ * 2^presum adjacent channels pre-added once per batch (pairs, quads), each
+ * series taken at the delay of its highest-frequency channel.  All are exact. */
 typedef struct {
   int32_t dms_per_thread;     /* register tile along DM                            */
   int32_t samples_per_thread; /* register tile along time (4*k for the uint8 path)  */
   int32_t warps_dm;           /* warps of a block along DM                          */
   int32_t warps_time;         /* warps of a block along time                        */
   int32_t chunk;              /* channels (subbands) staged per shared-memory pass  */
-  int32_t pairs;              /* 1: pre-summed channel pairs; 0: single channels    */
+  int32_t presum;             /* 0 single channels, 1 pairs, 2 quads (pre-summed)   */
 } sps_dedisp_config;
 
 /* Launch parameters of the fused boxcar + S/N kernel. */
@@ -163,8 +164,9 @@ sps_status sps_dedisperse(const sps_plan* plan, const uint8_t* x, int64_t x_pitc
  * counterpart; this is a library convenience.
  * Same inputs, outputs and results as sps_dedisperse.  The workspace comes
  * from a file-scope device array of 96 MiB (enough for the brute-force search
- * of one 1536-channel, 1.024 s beam with the single-channel kernel, pairs = 0:
- * 79 MB; not for the pair kernel's series, 236 MB, nor for the subband path);
+ * of one 1536-channel, 1.024 s beam with the single-channel kernel, presum = 0:
+ * 79 MB; not for the pre-summed series of presum 1 or 2, 236 and 614 MB, nor
+ * for the subband path);
  * plans whose current configuration needs more are rejected with UNSUPPORTED
  * and a message giving both sizes.
  * Allocates nothing.  Every device that loads this entry point keeps the

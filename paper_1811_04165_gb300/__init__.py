@@ -33,7 +33,7 @@ MODE_SUBBAND = 1
 class DedispConfig(ctypes.Structure):
     _fields_ = [("dms_per_thread", ctypes.c_int32), ("samples_per_thread", ctypes.c_int32),
                 ("warps_dm", ctypes.c_int32), ("warps_time", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("pairs", ctypes.c_int32)]
+                ("presum", ctypes.c_int32)]
 
     def as_tuple(self):
         return tuple(getattr(self, f) for f, _ in self._fields_)

@@ -42,27 +42,29 @@ sps_status check_x(const sps_plan* p, const uint8_t* x, int64_t pitch) {
 }
 
 // Workspace layout: the staged form of the batch -- three shifted copies of x
-// (single-channel kernel) or the pair-sum series (pair kernel) -- then, in
+// (single-channel kernel) or the pre-summed series (pairs or quads) -- then, in
 // SUBBAND mode, the step-one output Y.  workspace_needed is what the current
-// configuration uses; sps_plan_workspace_bytes reports the larger of the two
+// configuration uses; sps_plan_workspace_bytes reports the largest of the
 // forms so that a buffer of that size fits any configuration.
 size_t x4_bytes(const sps_plan* p) { return (size_t)3 * p->channels * p->pitch4; }
 
-size_t q_bytes(const sps_plan* p) { return (size_t)p->max_pair_series * 2 * p->q_pitch * sizeof(uint16_t); }
+size_t q_bytes(const sps_plan* p, int64_t n_series) { return (size_t)n_series * 2 * p->q_pitch * sizeof(uint16_t); }
 
 size_t y_bytes(const sps_plan* p) {
   return p->mode == SPS_MODE_SUBBAND ? (size_t)p->coarse_dms.size() * p->n_subbands * p->y_pitch * sizeof(uint16_t)
                                      : 0;
 }
 
-bool uses_pairs(const sps_plan* p) { return p->mode == SPS_MODE_BRUTE ? p->cfg.brute.pairs : p->cfg.step1.pairs; }
+bool uses_presum(const sps_plan* p) { return p->mode == SPS_MODE_BRUTE ? p->cfg.brute.presum : p->cfg.step1.presum; }
 
-size_t y_offset(const sps_plan* p) { return ((uses_pairs(p) ? q_bytes(p) : x4_bytes(p)) + 255) / 256 * 256; }
+size_t y_offset(const sps_plan* p) {
+  return ((uses_presum(p) ? q_bytes(p, p->n_presum_series) : x4_bytes(p)) + 255) / 256 * 256;
+}
 
 size_t workspace_needed(const sps_plan* p) { return y_offset(p) + y_bytes(p); }
 
 size_t workspace_any_config(const sps_plan* p) {
-  return (std::max(x4_bytes(p), q_bytes(p)) + 255) / 256 * 256 + y_bytes(p);
+  return (std::max(x4_bytes(p), q_bytes(p, p->max_presum_series)) + 255) / 256 * 256 + y_bytes(p);
 }
 
 U8PassArgs u8_args(const sps_plan* p, const uint8_t* x, int64_t pitch, const uint8_t* x4) {
@@ -84,28 +86,30 @@ U8PassArgs u8_args(const sps_plan* p, const uint8_t* x, int64_t pitch, const uin
 sps_status run_u8_pass(const sps_plan* p, const sps_dedisp_config& cfg, const uint8_t* x, int64_t pitch,
                        uint8_t* ws, int32_t rows, int32_t per, int32_t n_out, int64_t out_pitch, int32_t dmax,
                        void* out, int32_t out_u16, cudaStream_t st) {
-  if (cfg.pairs) {
+  if (cfg.presum) {
     uint16_t* q = reinterpret_cast<uint16_t*>(ws);
-    sps_status s = launch_pair_series(x, pitch, (int32_t)p->n_in, p->d_pair_series, p->n_pair_series, q,
-                                      p->q_pitch, st);
+    sps_status s = launch_presum_series(x, pitch, (int32_t)p->n_in, p->d_presum_series, p->n_presum_series, q,
+                                        p->q_pitch, st);
     if (s) return s;
-    PairPassArgs a{};
+    const int32_t K = 1 << cfg.presum;
+    PresumPassArgs a{};
     a.q = q;
     a.q_pitch = p->q_pitch;
-    a.slots = p->d_pair_slots;
-    a.slots_max = p->pair_slots_max;
-    a.offs = p->d_pair_offs;
-    a.di_pad = pair_di_pad(cfg);
+    a.slots = p->d_presum_slots;
+    a.slots_max = p->presum_slots_max;
+    a.offs = p->d_presum_offs;
+    a.di_pad = presum_di_pad(cfg);
     a.n_dm = rows;
     a.n_groups = p->channels / per;
-    a.group_pairs = (per + 1) / 2;
+    a.group_units = (per + K - 1) / K;
+    a.fold_units = 65535 / (255 * K);
     a.n_out = n_out;
     a.out_pitch = out_pitch;
     a.dmax_tile = dmax;
     a.out = out;
     a.out_u16 = out_u16;
     a.status = p->d_status;
-    return launch_pair_pass(a, cfg, st);
+    return launch_presum_pass(a, cfg, st);
   }
   sps_status s = launch_expand(x, pitch, (int32_t)p->n_in, p->channels, ws, p->pitch4, st);
   if (s) return s;
@@ -224,9 +228,9 @@ sps_status sps_plan_destroy(sps_plan* p) {
   cudaFree(p->d_status);
   cudaFree(p->d_b0);
   cudaFree(p->d_offs);
-  cudaFree(p->d_pair_series);
-  cudaFree(p->d_pair_slots);
-  cudaFree(p->d_pair_offs);
+  cudaFree(p->d_presum_series);
+  cudaFree(p->d_presum_slots);
+  cudaFree(p->d_presum_offs);
   if (swap) cudaSetDevice(cur);
   delete p;
   return SPS_OK;
@@ -385,6 +389,6 @@ const char* sps_status_string(sps_status s) {
 
 const char* sps_last_error(void) { return g_last_error.c_str(); }
 
-int32_t sps_abi_version(void) { return 100; }
+int32_t sps_abi_version(void) { return 101; }
 
 }  // extern "C"

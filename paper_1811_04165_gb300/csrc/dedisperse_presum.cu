@@ -1,0 +1,417 @@
+// De-dispersion over pre-summed units of K = 2^presum adjacent channels
+// (K = 2 pairs, K = 4 quads; brute force, or subband step one), exactly:
+//
+//   out[i * G + g][t] = sum_{c in group g} x[c][t + d(i, c)]
+//                     = sum_{units (c0 .. e)} S_rel[t + d(i, e)],
+//   S_rel[u] = sum_j x[c0 + j][u + rel_j],   rel_j = d(i, c0 + j) - d(i, e) >= 0.
+//
+// (Sec. 1: shift and integrate channels; Sec. 2, first footnote: step one.)
+// Adjacent channels have nearly equal delays, so a tile of consecutive trials
+// needs only a few tuples rel per unit.  A pre-pass writes, for every unit and
+// every tuple its trials need, the series S_rel as uint16 (two copies, the
+// second shifted by one sample, so every 32-bit shared load is aligned); the
+// block then stages, per chunk of units, just the series its tile uses (a
+// host-built slot list) with bulk asynchronous copies (TMA) into a ring of
+// kStages mbarrier-tracked stages.  A 32-bit load holds two samples of a unit sum in 16-bit
+// lanes: one add accumulates 2 K channel-samples, with no unpacking.  Unit sums
+// are <= 255 K, so 16-bit lanes are exact for 65535 / (255 K) units (128 pairs,
+// 64 quads); partial sums fold into int32 registers that often.  A group whose
+// size is not a multiple of K ends in a shorter unit.
+#include <algorithm>
+
+#include "sps_internal.h"
+#include "tma.cuh"
+
+namespace sps {
+namespace {
+
+constexpr int kMaxThreads = 512;
+constexpr int kStages = 3;  // shared-memory ring depth
+
+// NW words at shared address addr + 128 * m (immediate offsets).
+template <int NW, int M = 0>
+__device__ __forceinline__ void lds_row(uint32_t addr, uint32_t (&w)[NW]) {
+  if constexpr (M < NW) {
+    asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(w[M]) : "r"(addr), "n"(M * 128));
+    lds_row<NW, M + 1>(addr, w);
+  }
+}
+
+// The staged offsets of one unit for a warp's ND trials (uint16 words, one
+// vector load), as byte offsets.
+template <int ND>
+__device__ __forceinline__ void load_offs(const uint16_t* p, uint32_t (&o)[ND]) {
+  if constexpr (ND == 1) {
+    o[0] = (uint32_t)*p << 2;
+  } else {
+    uint32_t w[ND / 2];
+    if constexpr (ND == 8) {
+      const uint4 v = *reinterpret_cast<const uint4*>(p);
+      w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    } else if constexpr (ND == 4) {
+      const uint2 v = *reinterpret_cast<const uint2*>(p);
+      w[0] = v.x; w[1] = v.y;
+    } else {
+      w[0] = *reinterpret_cast<const uint32_t*>(p);
+    }
+#pragma unroll
+    for (int k = 0; k < ND / 2; k++) {
+      o[2 * k] = (w[k] & 0xFFFFu) << 2;
+      o[2 * k + 1] = (w[k] >> 16) << 2;
+    }
+  }
+}
+
+template <int ND, int NW>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb, int slots_max) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int wt = (int)(blockDim.x >> 5) / wd;
+  const int Tt = wt * 64 * NW;
+  const int Di = wd * ND;
+  const int stage_bytes = slots_max * 2 * wb + cp_max * a.di_pad * 2;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * stage_bytes);
+  uint64_t* empty = full + kStages;
+  __shared__ volatile int aborted;
+  __shared__ volatile int issued_upto;  // chunks [0, issued_upto) have been issued
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = (int)(blockDim.x >> 5);
+  const int dm_sub = warp % wd, t_sub = warp / wd;
+  const int tile = blockIdx.x;
+  const int i0 = tile * Di;
+  const int t0 = blockIdx.y * Tt;
+  const int g = blockIdx.z;
+  const int P = a.group_units;
+  const int n_chunks = (P + cp_max - 1) / cp_max;
+  const uint32_t toff = (uint32_t)(t_sub * 128 * NW + lane * 4);  // bytes
+  const int64_t chunk_row = ((int64_t)tile * a.n_groups + g) * n_chunks;
+
+  if (tid == 0) {
+    aborted = 0;
+    issued_upto = 0;
+    for (int k = 0; k < kStages; k++) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], nwarps);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // One warp stages a whole chunk: the chunk's slot list names the series (and
+  // window start) of each slot; copy j of slot k lands at (2k + j) * wb, and
+  // lane 0 also copies the chunk's offset table and arrives on the stage's
+  // "full" barrier with the byte count.  The issuing warp fetches its first two
+  // list entries per lane (and the slot count) a chunk early (`fetch`).
+  struct Fetched { int n_slots; int2 e0, e1; };
+  auto fetch = [&](int ch) {
+    const int2* list = a.slots + (chunk_row + ch) * (slots_max + 1);
+    Fetched f;
+    f.n_slots = __ldg(&list[slots_max].x);
+    f.e0 = lane < 2 * slots_max ? __ldg(&list[lane >> 1]) : make_int2(0, 0);
+    f.e1 = lane + 32 < 2 * slots_max ? __ldg(&list[(lane + 32) >> 1]) : make_int2(0, 0);
+    return f;
+  };
+  auto issue = [&](int ch, const Fetched& f) {
+    const int st = ch % kStages;
+    uint8_t* sb = smem + st * stage_bytes;
+    const int pb = ch * cp_max, cp = min(cp_max, P - pb);
+    const int2* list = a.slots + (chunk_row + ch) * (slots_max + 1);
+    const int n2 = 2 * f.n_slots;
+    const uint32_t tbl_bytes = (uint32_t)(cp * a.di_pad * 2);
+    auto entry = [&](int q) { return q == lane ? f.e0 : (q == lane + 32 ? f.e1 : __ldg(&list[q >> 1])); };
+    uint32_t bytes_all = 0;
+    for (int q = lane; q < n2; q += 32) bytes_all += (uint32_t)min(wb, 2 * (a.q_pitch - (t0 + entry(q).y)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bytes_all += __shfl_xor_sync(0xffffffffu, bytes_all, o);
+    if (lane == 0) mbar_arrive_expect_tx(&full[st], bytes_all + tbl_bytes);
+    __syncwarp();
+    for (int q = lane; q < n2; q += 32) {
+      const int2 e = entry(q);
+      const int start = t0 + e.y;
+      const uint32_t bytes = (uint32_t)min(wb, 2 * (a.q_pitch - start));
+      const uint16_t* src = a.q + ((int64_t)e.x * 2 + (q & 1)) * a.q_pitch + start;
+      bulk_g2s(sb + q * wb, src, bytes, &full[st]);
+    }
+    if (lane == 0) {
+      const uint16_t* src = a.offs + (((int64_t)tile * a.n_groups + g) * P + pb) * a.di_pad;
+      bulk_g2s(sb + slots_max * 2 * wb, src, tbl_bytes, &full[st]);
+      issued_upto = ch + 1;
+    }
+  };
+
+  uint32_t lanes[ND][NW];
+  int32_t acc[ND][NW][2];
+#pragma unroll
+  for (int r = 0; r < ND; r++)
+#pragma unroll
+    for (int m = 0; m < NW; m++) { lanes[r][m] = 0u; acc[r][m][0] = 0; acc[r][m][1] = 0; }
+  auto fold = [&]() {
+#pragma unroll
+    for (int r = 0; r < ND; r++)
+#pragma unroll
+      for (int m = 0; m < NW; m++) {
+        acc[r][m][0] += (int32_t)(lanes[r][m] & 0xFFFFu);
+        acc[r][m][1] += (int32_t)(lanes[r][m] >> 16);
+        lanes[r][m] = 0u;
+      }
+  };
+
+  // Chunks 0 and 1 go out first; after computing chunk ch, warp (ch mod
+  // nwarps) stages chunk ch + 2 into the stage chunk ch - 1 used, once every
+  // warp has released that stage.  No block-wide barrier: a warp waits only for
+  // its data, and the issuer for warps one chunk behind.
+  if (warp == 0)
+    for (int k = 0; k < min(kStages - 1, n_chunks); k++) issue(k, fetch(k));
+
+  int pending = 0;
+  int ch = 0;
+  for (; ch < n_chunks; ch++) {
+    const int st = ch % kStages;
+    const int cp = min(cp_max, P - ch * cp_max);
+    const bool issuer = ch % nwarps == warp && ch + kStages - 1 < n_chunks;
+    if (pending + cp > a.fold_units) { fold(); pending = 0; }
+    Fetched next{};
+    if (issuer) next = fetch(ch + kStages - 1);
+    bool ok = !aborted;
+    if (ok && !mbar_wait(&full[st], (ch / kStages) & 1, a.status)) {
+      aborted = 1;
+      ok = false;
+    }
+    if (ok) {
+      const uint32_t base = smem_u32(smem) + (uint32_t)(st * stage_bytes) + toff;
+      const uint16_t* tb =
+          reinterpret_cast<const uint16_t*>(smem + st * stage_bytes + slots_max * 2 * wb) + dm_sub * ND;
+      int p = 0;
+      for (; p + 1 < cp; p += 2) {
+        uint32_t e0[ND], e1[ND];
+        load_offs<ND>(tb + p * a.di_pad, e0);
+        load_offs<ND>(tb + (p + 1) * a.di_pad, e1);
+#pragma unroll
+        for (int r = 0; r < ND; r++) {
+          uint32_t A[NW], B[NW];
+          lds_row<NW>(base + e0[r], A);
+          lds_row<NW>(base + e1[r], B);
+#pragma unroll
+          for (int m = 0; m < NW; m++) lanes[r][m] += A[m] + B[m];
+        }
+      }
+      if (p < cp) {
+        uint32_t e0[ND];
+        load_offs<ND>(tb + p * a.di_pad, e0);
+#pragma unroll
+        for (int r = 0; r < ND; r++) {
+          uint32_t A[NW];
+          lds_row<NW>(base + e0[r], A);
+#pragma unroll
+          for (int m = 0; m < NW; m++) lanes[r][m] += A[m];
+        }
+      }
+    }
+    pending += cp;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+    if (issuer && !aborted) {
+      const int prev = ch - 1;  // the stage chunk ch + 2 reuses
+      if (prev >= 0 && !mbar_wait(&empty[prev % kStages], (prev / kStages) & 1, a.status))
+        aborted = 1;
+      else
+        issue(ch + kStages - 1, next);
+    }
+  }
+  __syncthreads();  // every warp has left the loop
+  if (aborted) {
+    // let the copies still in flight (the last chunks issued) land before the
+    // block's shared memory goes away; each wait is bounded
+    if (tid == 0)
+      for (int k = max(0, issued_upto - kStages); k < issued_upto; k++)
+        mbar_wait(&full[k % kStages], (k / kStages) & 1, nullptr);
+    return;
+  }
+  fold();
+
+  // Each lane holds 2 consecutive samples per (trial, word).
+  const bool vec = (a.out_pitch & 1) == 0;
+#pragma unroll
+  for (int r = 0; r < ND; r++) {
+    const int i = i0 + dm_sub * ND + r;
+    if (i >= a.n_dm) continue;
+    const int64_t row = (int64_t)i * a.n_groups + g;
+#pragma unroll
+    for (int m = 0; m < NW; m++) {
+      const int t = t0 + (int)(toff >> 1) + 64 * m;
+      if (t >= a.n_out) continue;
+      if (a.out_u16) {
+        uint16_t* o = static_cast<uint16_t*>(a.out) + row * a.out_pitch + t;
+        if (t + 1 < a.n_out && vec) {
+          *reinterpret_cast<uint32_t*>(o) = (uint32_t)acc[r][m][0] | ((uint32_t)acc[r][m][1] << 16);
+        } else {
+          o[0] = (uint16_t)acc[r][m][0];
+          if (t + 1 < a.n_out) o[1] = (uint16_t)acc[r][m][1];
+        }
+      } else {
+        int32_t* o = static_cast<int32_t*>(a.out) + row * a.out_pitch + t;
+        if (t + 1 < a.n_out && vec) {
+          *reinterpret_cast<int2*>(o) = make_int2(acc[r][m][0], acc[r][m][1]);
+        } else {
+          o[0] = acc[r][m][0];
+          if (t + 1 < a.n_out) o[1] = acc[r][m][1];
+        }
+      }
+    }
+  }
+}
+
+// Adds bytes u + j .. u + j + 15 of a channel row, for j = 0 and 1, into
+// v[j] as eight words of 16-bit lanes (bytes at and beyond in_len read as 0).
+// `row` is 8-byte aligned.  Three aligned 8-byte loads cover both copies.
+__device__ __forceinline__ void add_bytes16x2(const uint8_t* row, int u, int in_len, uint32_t (&v)[2][8]) {
+  const int b = u & ~7;
+  uint32_t W[6];
+  if (u >= 0 && b + 24 <= in_len) {
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const uint2 t = __ldg(reinterpret_cast<const uint2*>(row + b + 8 * k));
+      W[2 * k] = t.x;
+      W[2 * k + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      uint32_t w = 0;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const int p = b + 4 * k + i;
+        if (p >= 0 && p < in_len) w |= (uint32_t)__ldg(row + p) << (8 * i);
+      }
+      W[k] = w;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    const int o = u - b + j;  // 0 .. 8: byte offset of the copy's first sample in W
+    const int wi = o >> 2, sh = (o & 3) * 8;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t lo = wi == 0 ? W[k] : (wi == 1 ? W[k + 1] : W[k + 2]);
+      const uint32_t hi = wi == 0 ? W[k + 1] : (wi == 1 ? W[k + 2] : (k + 3 < 6 ? W[k + 3] : 0u));
+      const uint32_t w = __funnelshift_r(lo, hi, sh);
+      v[j][2 * k] += __byte_perm(w, 0u, 0x4140);
+      v[j][2 * k + 1] += __byte_perm(w, 0u, 0x4342);
+    }
+  }
+}
+
+// Series s, both copies j: q[(2 s + j) * q_pitch + u] = sum_c x[c0 + c][u + j + rel_c]
+// (rel of the last channel 0).  One thread writes 16 samples of each copy.
+__global__ void __launch_bounds__(256) presum_series_kernel(const uint8_t* x, int64_t pitch, int32_t in_len,
+                                                            const PresumSeries* series, int32_t n_series,
+                                                            uint16_t* q, int32_t q_pitch) {
+  const int64_t per_row = q_pitch >> 4;
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= per_row * n_series) return;
+  const int s = (int)(id / per_row);
+  const int u0 = (int)(id - (int64_t)s * per_row) << 4;
+  const int4 h = __ldg(reinterpret_cast<const int4*>(series + s));  // {c0, n, rel0, rel1}
+  const int rel2 = __ldg(&series[s].rel[2]);
+  uint32_t v[2][8];
+#pragma unroll
+  for (int j = 0; j < 2; j++)
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[j][k] = 0u;
+  for (int c = 0; c < h.y; c++) {
+    const int rel = c + 1 == h.y ? 0 : (c == 0 ? h.z : (c == 1 ? h.w : rel2));
+    add_bytes16x2(x + (int64_t)(h.x + c) * pitch, u0 + rel, in_len, v);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    uint4* o = reinterpret_cast<uint4*>(q + ((int64_t)s * 2 + j) * q_pitch + u0);
+    o[0] = make_uint4(v[j][0], v[j][1], v[j][2], v[j][3]);
+    o[1] = make_uint4(v[j][4], v[j][5], v[j][6], v[j][7]);
+  }
+}
+
+typedef void (*PresumKernel)(PresumPassArgs, int, int, int, int);
+
+template <int ND, int NW>
+constexpr PresumKernel k() { return presum_pass_kernel<ND, NW>; }
+
+struct Variant { int nd, nw; PresumKernel fn; };
+const Variant kVariants[] = {
+    {1, 2, k<1, 2>()}, {1, 4, k<1, 4>()}, {1, 8, k<1, 8>()}, {1, 16, k<1, 16>()},
+    {2, 2, k<2, 2>()}, {2, 4, k<2, 4>()}, {2, 8, k<2, 8>()}, {2, 16, k<2, 16>()},
+    {4, 2, k<4, 2>()}, {4, 4, k<4, 4>()}, {4, 8, k<4, 8>()},
+    {8, 2, k<8, 2>()}, {8, 4, k<8, 4>()},
+};
+
+PresumKernel find(int nd, int nw) {
+  for (const Variant& v : kVariants)
+    if (v.nd == nd && v.nw == nw) return v.fn;
+  return nullptr;
+}
+
+}  // namespace
+
+int presum_window_bytes(const sps_dedisp_config& c, int32_t dmax_tile) {
+  const int Tt = c.warps_time * 32 * c.samples_per_thread;
+  return 2 * ((Tt + dmax_tile + 7 + 7) / 8 * 8);
+}
+
+int presum_di_pad(const sps_dedisp_config& c) { return (c.warps_dm * c.dms_per_thread + 7) / 8 * 8; }
+
+int presum_chunk(const sps_dedisp_config& c) { return std::max(1, c.chunk >> c.presum); }
+
+bool presum_config_supported(const sps_dedisp_config& c, std::string* why) {
+  if (c.presum < 1 || c.presum > 2) {
+    *why = "presum must be 1 (pairs) or 2 (quads) for this kernel";
+    return false;
+  }
+  if (c.samples_per_thread % 2 || !find(c.dms_per_thread, c.samples_per_thread / 2)) {
+    *why = "no compiled pre-summed variant for this (dms_per_thread, samples_per_thread)";
+    return false;
+  }
+  const int threads = 32 * c.warps_dm * c.warps_time;
+  if (c.warps_dm < 1 || c.warps_time < 1 || threads > kMaxThreads) {
+    *why = "warps_dm * warps_time must lie in [1, 16]";
+    return false;
+  }
+  if (c.chunk < 2 || c.chunk > 64 || (c.chunk & 1)) {
+    *why = "chunk must be even and in [2, 64]";
+    return false;
+  }
+  return true;
+}
+
+size_t presum_smem_bytes(const sps_dedisp_config& c, int32_t dmax_tile, int32_t slots_max) {
+  const size_t stage = (size_t)slots_max * 2 * presum_window_bytes(c, dmax_tile) +
+                       (size_t)presum_chunk(c) * presum_di_pad(c) * 2;
+  return kStages * stage + 16 * kStages;
+}
+
+sps_status launch_presum_series(const uint8_t* x, int64_t pitch, int32_t in_len, const PresumSeries* series,
+                                int32_t n_series, uint16_t* q, int32_t q_pitch, cudaStream_t st) {
+  const int64_t threads = (int64_t)(q_pitch >> 4) * n_series;
+  if (threads == 0) return SPS_OK;
+  presum_series_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(x, pitch, in_len, series, n_series, q,
+                                                                           q_pitch);
+  SPS_CUDA(cudaGetLastError());
+  return SPS_OK;
+}
+
+sps_status launch_presum_pass(const PresumPassArgs& a, const sps_dedisp_config& c, cudaStream_t st) {
+  std::string why;
+  if (!presum_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
+  PresumKernel fn = find(c.dms_per_thread, c.samples_per_thread / 2);
+  const int Di = c.warps_dm * c.dms_per_thread;
+  const int Tt = c.warps_time * 32 * c.samples_per_thread;
+  const size_t smem = presum_smem_bytes(c, a.dmax_tile, a.slots_max);
+  dim3 grid((a.n_dm + Di - 1) / Di, (a.n_out + Tt - 1) / Tt, a.n_groups);
+  if (grid.y > 65535 || grid.z > 65535) return fail(SPS_ERR_UNSUPPORTED, "too many time tiles or groups");
+  SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  fn<<<grid, 32 * c.warps_dm * c.warps_time, smem, st>>>(a, c.warps_dm, presum_chunk(c),
+                                                        presum_window_bytes(c, a.dmax_tile), a.slots_max);
+  SPS_CUDA(cudaGetLastError());
+  return SPS_OK;
+}
+
+}  // namespace sps

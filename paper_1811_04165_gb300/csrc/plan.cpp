@@ -100,15 +100,15 @@ int64_t sps_plan::max_delay_brute() const {
 
 namespace sps {
 
-// Default configurations, tried in order at plan creation: the pair kernel for
-// brute force (fastest on finely channelised bands), then the single-channel
+// Default configurations, tried in order at plan creation: the pre-summed
+// (quad) kernel for brute force (fastest on finely channelised bands), then the single-channel
 // kernel, then smaller chunks for plans whose DM tiles span long delays.
 std::vector<sps_kernel_config> default_configs() {
   std::vector<sps_kernel_config> out;
   const sps_dedisp_config u8[3] = {{4, 16, 8, 1, 16, 0}, {4, 16, 8, 1, 4, 0}, {1, 4, 1, 1, 2, 0}};
   const sps_dedisp_config s2[3] = {{4, 16, 8, 1, 8, 0}, {4, 16, 8, 1, 2, 0}, {1, 4, 1, 1, 1, 0}};
   sps_kernel_config c{};
-  c.brute = {8, 8, 8, 1, 16, 1};
+  c.brute = {4, 16, 8, 1, 12, 2};
   c.step1 = u8[0];
   c.step2 = s2[0];
   c.snr = {256};
@@ -122,62 +122,18 @@ std::vector<sps_kernel_config> default_configs() {
   return out;
 }
 
-// Pair-series count of a delay table (groups of `per` channels, adjacent pairs):
-// for each pair, every delta between its smallest and largest over all rows.
-int64_t count_pair_series(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per) {
-  int64_t n = 0;
-  for (int32_t g = 0; g < C / per; g++)
-    for (int32_t a = g * per; a < (g + 1) * per; a += 2) {
-      if (a + 1 >= (g + 1) * per) { n += 1; continue; }
-      int32_t lo = INT32_MAX, hi = INT32_MIN;
-      for (int32_t i = 0; i < rows; i++) {
-        const int32_t v = d[(size_t)i * C + a] - d[(size_t)i * C + a + 1];
-        lo = std::min(lo, v);
-        hi = std::max(hi, v);
-      }
-      n += hi - lo + 1;
-    }
-  return n;
-}
-
-// Most series slots any (tile, group, chunk) of the pair kernel stages.
-int32_t pair_slots(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t Di, int32_t cp) {
-  int32_t best = 0;
-  for (int32_t i0 = 0; i0 < rows; i0 += Di) {
-    const int32_t i1 = std::min(i0 + Di, rows) - 1;
-    for (int32_t g = 0; g < C / per; g++) {
-      int32_t in_chunk = 0, count = 0;
-      for (int32_t a = g * per; a < (g + 1) * per; a += 2) {
-        int32_t n = 1;
-        if (a + 1 < (g + 1) * per) {
-          int32_t lo = INT32_MAX, hi = INT32_MIN;
-          for (int32_t i = i0; i <= i1; i++) {
-            const int32_t v = d[(size_t)i * C + a] - d[(size_t)i * C + a + 1];
-            lo = std::min(lo, v);
-            hi = std::max(hi, v);
-          }
-          n = hi - lo + 1;
-        }
-        count += n;
-        if (++in_chunk == cp) {
-          best = std::max(best, count);
-          in_chunk = count = 0;
-        }
-      }
-      best = std::max(best, count);
-    }
-  }
-  return best;
-}
-
-int32_t cached_pair_slots(const sps_plan* p, int which, int32_t Di, int32_t cp) {
-  const int64_t key = ((int64_t)which << 40) | ((int64_t)Di << 20) | cp;
-  auto it = p->pair_slot_cache.find(key);
-  if (it != p->pair_slot_cache.end()) return it->second;
-  const int32_t v = which == 0 ? pair_slots(p->delays, (int32_t)p->dms.size(), p->channels, p->channels, Di, cp)
-                               : pair_slots(p->d1, (int32_t)p->coarse_dms.size(), p->channels,
-                                            p->channels / p->n_subbands, Di, cp);
-  p->pair_slot_cache[key] = v;
+// Most series slots any (tile, group, chunk) of the pre-summed kernel stages
+// for `presum` (cached).
+int32_t cached_presum_slots(const sps_plan* p, int which, int32_t presum, int32_t Di, int32_t cu) {
+  const int64_t key = ((int64_t)which << 48) | ((int64_t)presum << 40) | ((int64_t)Di << 20) | cu;
+  auto it = p->presum_slot_cache.find(key);
+  if (it != p->presum_slot_cache.end()) return it->second;
+  const int32_t K = 1 << presum;
+  const int32_t v = which == 0
+                        ? presum_slots(p->delays, (int32_t)p->dms.size(), p->channels, p->channels, K, Di, cu)
+                        : presum_slots(p->d1, (int32_t)p->coarse_dms.size(), p->channels,
+                                       p->channels / p->n_subbands, K, Di, cu);
+  p->presum_slot_cache[key] = v;
   return v;
 }
 
@@ -197,9 +153,10 @@ int32_t cached_spread(const sps_plan* p, int which, int32_t tile) {
 sps_status check_config(const sps_plan* p, const sps_kernel_config& cfg, ConfigCheck* out) {
   std::string why;
   auto pass_ok = [&](const sps_dedisp_config& c) {
-    return c.pairs ? pair_config_supported(c, &why) : u8_config_supported(c, &why);
+    return c.presum ? presum_config_supported(c, &why) : u8_config_supported(c, &why);
   };
-  if ((cfg.brute.pairs | cfg.step1.pairs) & ~1) return fail(SPS_ERR_INVALID_ARG, "pairs must be 0 or 1");
+  for (int32_t v : {cfg.brute.presum, cfg.step1.presum})
+    if (v < 0 || v > 2) return fail(SPS_ERR_INVALID_ARG, "presum must be 0, 1 or 2");
   if (p->mode == SPS_MODE_BRUTE && !pass_ok(cfg.brute))
     return fail(SPS_ERR_INVALID_ARG, "brute config: " + why);
   if (p->mode == SPS_MODE_SUBBAND) {
@@ -213,9 +170,11 @@ sps_status check_config(const sps_plan* p, const sps_kernel_config& cfg, ConfigC
   if (p->mode == SPS_MODE_BRUTE) {
     const int32_t di = cfg.brute.warps_dm * cfg.brute.dms_per_thread;
     c.dmax_b = cached_spread(p, 0, di);
-    const size_t need = cfg.brute.pairs
-                            ? pair_smem_bytes(cfg.brute, c.dmax_b, cached_pair_slots(p, 0, di, pair_chunk(cfg.brute)))
-                            : u8_smem_bytes(cfg.brute, c.dmax_b, p->channels);
+    const size_t need =
+        cfg.brute.presum
+            ? presum_smem_bytes(cfg.brute, c.dmax_b,
+                                cached_presum_slots(p, 0, cfg.brute.presum, di, presum_chunk(cfg.brute)))
+            : u8_smem_bytes(cfg.brute, c.dmax_b, p->channels);
     if (need > (size_t)p->max_smem)
       return fail(SPS_ERR_INVALID_ARG, "brute config needs more shared memory than a block may use");
   } else {
@@ -236,8 +195,10 @@ sps_status check_config(const sps_plan* p, const sps_kernel_config& cfg, ConfigC
     }
     const int32_t di1 = cfg.step1.warps_dm * cfg.step1.dms_per_thread;
     const size_t need1 =
-        cfg.step1.pairs ? pair_smem_bytes(cfg.step1, c.dmax_1, cached_pair_slots(p, 1, di1, pair_chunk(cfg.step1)))
-                        : u8_smem_bytes(cfg.step1, c.dmax_1, p->channels / S);
+        cfg.step1.presum
+            ? presum_smem_bytes(cfg.step1, c.dmax_1,
+                                cached_presum_slots(p, 1, cfg.step1.presum, di1, presum_chunk(cfg.step1)))
+            : u8_smem_bytes(cfg.step1, c.dmax_1, p->channels / S);
     if (need1 > (size_t)p->max_smem)
       return fail(SPS_ERR_INVALID_ARG, "step1 config needs more shared memory than a block may use");
     if (step2_smem_bytes(cfg.step2, c.dmax_2) > (size_t)p->max_smem)
@@ -255,16 +216,16 @@ sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg) {
   const int32_t dmax_b = chk.dmax_b, dmax_1 = chk.dmax_1, dmax_2 = chk.dmax_2;
   const std::vector<int32_t>& tiles = chk.tiles;
   const sps_dedisp_config& pass = p->mode == SPS_MODE_BRUTE ? cfg.brute : cfg.step1;
-  if (pass.pairs) {
-    PairTables pt;
+  if (pass.presum) {
+    PresumTables pt;
     sps_status s = p->mode == SPS_MODE_BRUTE
-                       ? build_pair_tables(p->delays, n_dms, p->channels, p->channels, pass, dmax_b, &pt)
-                       : build_pair_tables(p->d1, (int32_t)p->coarse_dms.size(), p->channels,
-                                           p->channels / p->n_subbands, pass, dmax_1, &pt);
+                       ? build_presum_tables(p->delays, n_dms, p->channels, p->channels, pass, dmax_b, &pt)
+                       : build_presum_tables(p->d1, (int32_t)p->coarse_dms.size(), p->channels,
+                                             p->channels / p->n_subbands, pass, dmax_1, &pt);
     if (s) return s;
-    int4* dser = nullptr;
+    PresumSeries* dser = nullptr;
     int2* dslot = nullptr;
-    uint32_t* doffs = nullptr;
+    uint16_t* doffs = nullptr;
     s = upload(pt.series, &dser);
     if (s == SPS_OK) s = upload(pt.slots, &dslot);
     if (s == SPS_OK) s = upload(pt.offs, &doffs);
@@ -273,14 +234,14 @@ sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg) {
       cudaFree(dslot);
       return s;
     }
-    cudaFree(p->d_pair_series);
-    cudaFree(p->d_pair_slots);
-    cudaFree(p->d_pair_offs);
-    p->d_pair_series = dser;
-    p->d_pair_slots = dslot;
-    p->d_pair_offs = doffs;
-    p->n_pair_series = (int32_t)pt.series.size();
-    p->pair_slots_max = pt.slots_max;
+    cudaFree(p->d_presum_series);
+    cudaFree(p->d_presum_slots);
+    cudaFree(p->d_presum_offs);
+    p->d_presum_series = dser;
+    p->d_presum_slots = dslot;
+    p->d_presum_offs = doffs;
+    p->n_presum_series = (int32_t)pt.series.size();
+    p->presum_slots_max = pt.slots_max;
   } else {
     std::vector<int32_t> b0;
     std::vector<uint32_t> offs;
@@ -424,10 +385,12 @@ sps_status plan_create(const sps_plan_desc* d, sps_plan** out) {
   }
   p->n_in = p->n_t + max_total;
   p->pitch4 = (p->n_in + 15) / 16 * 16;
-  p->q_pitch = (int32_t)((p->n_in + 7) / 8 * 8);
-  p->max_pair_series = d->mode == SPS_MODE_BRUTE
-                           ? count_pair_series(p->delays, n_dms, C, C)
-                           : count_pair_series(p->d1, d->n_coarse, C, C / d->n_subbands);
+  p->q_pitch = (int32_t)((p->n_in + 15) / 16 * 16);
+  for (int32_t K : {2, 4})
+    p->max_presum_series = std::max(p->max_presum_series,
+                                    d->mode == SPS_MODE_BRUTE
+                                        ? count_presum_series(p->delays, n_dms, C, C, K)
+                                        : count_presum_series(p->d1, d->n_coarse, C, C / d->n_subbands, K));
   if (cudaDeviceGetAttribute(&p->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device) != cudaSuccess) {
     delete p;
     return fail(SPS_ERR_CUDA, "cudaDeviceGetAttribute(max shared memory)");

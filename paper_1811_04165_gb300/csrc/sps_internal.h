@@ -33,7 +33,7 @@ struct U8PassArgs {
   int64_t pitch4;          // bytes per shifted row (N_in rounded up to 16)
   int32_t win_limit;       // no staged window reads at or beyond this byte of a row
   const int32_t* b0;       // [n_tiles][channels]: first-trial delay rounded down to 16
-  const uint32_t* offs;    // [n_tiles][n_groups][pairs][di_pad][2]: staged offsets
+  const uint32_t* offs;    // [n_tiles][n_groups][channel pairs][di_pad][2]: staged offsets
   int32_t di_pad;          // trials per tile rounded up to even
   int32_t n_dm;            // delay-table rows
   int32_t channels;        // total channels
@@ -48,17 +48,19 @@ struct U8PassArgs {
   uint32_t one;            // 1, passed at run time (see madd in dedisperse_u8.cu)
 };
 
-// De-dispersion over pre-summed channel pairs (dedisperse_pair.cu).
-struct PairPassArgs {
-  const uint16_t* q;       // [n_series][2][q_pitch]: pair-sum series, second copy shifted by one
-  int32_t q_pitch;         // samples per series row (N_in rounded up to 8)
+// De-dispersion over pre-summed units of K = 2^presum adjacent channels
+// (dedisperse_presum.cu, presum_tables.cpp).
+struct PresumPassArgs {
+  const uint16_t* q;       // [n_series][2][q_pitch]: unit-sum series, second copy shifted by one
+  int32_t q_pitch;         // samples per series row (N_in rounded up to 16)
   const int2* slots;       // [tiles][groups][chunks][slots_max + 1]: {series, window start}; last .x = count
   int32_t slots_max;
-  const uint32_t* offs;    // [tiles][groups][pairs][di_pad]: staged byte offsets
+  const uint16_t* offs;    // [tiles][groups][units][di_pad]: staged offsets in 4-byte words
   int32_t di_pad;
   int32_t n_dm;            // delay-table rows
   int32_t n_groups;
-  int32_t group_pairs;     // pairs per group
+  int32_t group_units;     // units per group
+  int32_t fold_units;      // units a 16-bit lane sums exactly: 65535 / (255 K)
   int32_t n_out;
   int64_t out_pitch;
   int32_t dmax_tile;
@@ -67,10 +69,16 @@ struct PairPassArgs {
   uint32_t* status;
 };
 
-struct PairTables {
-  std::vector<int4> series;    // {a, b (-1: none), delta, 0}
+// One pre-summed series: channels c0 .. c0 + n - 1, channel c0 + j (j < n - 1)
+// taken rel[j] samples later than the last one.
+struct PresumSeries {
+  int32_t c0, n, rel[3], pad[3];
+};
+
+struct PresumTables {
+  std::vector<PresumSeries> series;
   std::vector<int2> slots;
-  std::vector<uint32_t> offs;
+  std::vector<uint16_t> offs;
   int32_t slots_max = 0;
   int32_t wb = 0;
 };
@@ -114,16 +122,21 @@ sps_status launch_expand(const uint8_t* x, int64_t pitch, int32_t in_len, int32_
                          int64_t pitch4, cudaStream_t st);
 sps_status launch_detect(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
                          int32_t n_dms, int32_t n_widths, int32_t* best, cudaStream_t st);
-sps_status launch_pair_series(const uint8_t* x, int64_t pitch, int32_t in_len, const int4* series,
-                              int32_t n_series, uint16_t* q, int32_t q_pitch, cudaStream_t st);
-sps_status launch_pair_pass(const PairPassArgs& a, const sps_dedisp_config& cfg, cudaStream_t st);
-bool pair_config_supported(const sps_dedisp_config& cfg, std::string* why);
-size_t pair_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile, int32_t slots_max);
-int pair_window_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
-int pair_di_pad(const sps_dedisp_config& cfg);
-int pair_chunk(const sps_dedisp_config& cfg);
-sps_status build_pair_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per,
-                             const sps_dedisp_config& cfg, int32_t dmax_tile, PairTables* out);
+sps_status launch_presum_series(const uint8_t* x, int64_t pitch, int32_t in_len, const PresumSeries* series,
+                                int32_t n_series, uint16_t* q, int32_t q_pitch, cudaStream_t st);
+sps_status launch_presum_pass(const PresumPassArgs& a, const sps_dedisp_config& cfg, cudaStream_t st);
+bool presum_config_supported(const sps_dedisp_config& cfg, std::string* why);
+size_t presum_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile, int32_t slots_max);
+int presum_window_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
+int presum_di_pad(const sps_dedisp_config& cfg);
+int presum_chunk(const sps_dedisp_config& cfg);  // units staged per chunk
+// Host tables (presum_tables.cpp): series count over all rows, most slots of
+// any (tile, group, chunk), and the full tables of one configuration.
+int64_t count_presum_series(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t K);
+int32_t presum_slots(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t K, int32_t Di,
+                     int32_t units_per_chunk);
+sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per,
+                               const sps_dedisp_config& cfg, int32_t dmax_tile, PresumTables* out);
 bool u8_config_supported(const sps_dedisp_config& cfg, std::string* why);
 bool step2_config_supported(const sps_dedisp_config& cfg, std::string* why);
 bool snr_config_supported(const sps_snr_config& cfg, std::string* why);
@@ -186,18 +199,18 @@ struct sps_plan {
   uint32_t* d_offs = nullptr;
   int64_t pitch4 = 0;            // bytes per row of the shifted copies
 
-  // pre-summed-pair tables (when the uint8 pass uses pairs)
-  int4* d_pair_series = nullptr;
-  int2* d_pair_slots = nullptr;
-  uint32_t* d_pair_offs = nullptr;
-  int32_t n_pair_series = 0;     // of the current configuration's table
-  int32_t pair_slots_max = 0;
-  int32_t q_pitch = 0;           // samples per pair-series row
-  int64_t max_pair_series = 0;   // over both tables (sizes the workspace)
+  // pre-summed-series tables (when the uint8 pass has presum > 0)
+  sps::PresumSeries* d_presum_series = nullptr;
+  int2* d_presum_slots = nullptr;
+  uint16_t* d_presum_offs = nullptr;
+  int32_t n_presum_series = 0;   // of the current configuration's table
+  int32_t presum_slots_max = 0;
+  int32_t q_pitch = 0;           // samples per series row
+  int64_t max_presum_series = 0; // over presum 1 and 2 (sizes the workspace)
 
   int max_smem = 0;              // opt-in shared memory per block of the device
   mutable std::map<int64_t, int32_t> spread_cache;     // tile delay spread by (table, rows)
-  mutable std::map<int64_t, int32_t> pair_slot_cache;  // pair slots by (table, rows, chunk)
+  mutable std::map<int64_t, int32_t> presum_slot_cache;  // slots by (table, K, rows, units)
 
   sps_kernel_config cfg{};
   // delay spread of one DM tile for the current configuration

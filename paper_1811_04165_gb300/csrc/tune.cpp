@@ -295,15 +295,15 @@ sps_status space_problem(const sps_space* sp, Problem* pr) {
 // ------------------------------------------------------------------ plan space
 // Gene value arrays (powers of two, Sec. 3.2) of each kernel kind.
 const int32_t kU8Values[6][6] = {{1, 2, 4, 8}, {4, 8, 16, 32}, {1, 2, 4, 8, 16}, {1, 2, 4, 8, 16},
-                                 {2, 4, 8, 16, 32, 64}, {0, 1}};
-const int32_t kU8Counts[6] = {4, 4, 5, 5, 6, 2};
+                                 {2, 4, 8, 16, 32, 64}, {0, 1, 2}};
+const int32_t kU8Counts[6] = {4, 4, 5, 5, 6, 3};
 const int32_t kStep2Values[5][6] = {{1, 2, 4, 8}, {4, 8, 16}, {1, 2, 4, 8, 16}, {1, 2, 4, 8, 16}, {1, 2, 4, 8, 16, 32}};
 const int32_t kStep2Counts[5] = {4, 3, 5, 5, 6};
 const int32_t kSnrValues[5] = {32, 64, 128, 256, 512};
 
 struct PlanGene {
   int32_t kernel;            // 0 brute / step1, 1 step2 (subband), last: snr
-  int32_t field;             // 0..5 dedispersion fields (5: pairs), 6 snr threads
+  int32_t field;             // 0..5 dedispersion fields (5: presum), 6 snr threads
   std::vector<int32_t> values;
 };
 
@@ -320,7 +320,7 @@ std::vector<PlanGene> plan_genes(const sps_plan* p, int32_t which) {
         const std::vector<std::vector<int32_t>> r = {{4}, {16}, {1, 2, 4, 8, 16}, {1}, {2, 4, 8, 16, 32}, {0}};
         v = r[f];
       } else if (reduced_brute) {
-        const std::vector<std::vector<int32_t>> r = {{1, 2, 4, 8}, {4, 8, 16}, {1, 2, 4, 8, 16}, {1, 2}, {16}, {0, 1}};
+        const std::vector<std::vector<int32_t>> r = {{1, 2, 4, 8}, {4, 8, 16}, {1, 2, 4, 8, 16}, {1, 2}, {16}, {0, 1, 2}};
         v = r[f];
       }
       out.push_back({kernel, f, v});
@@ -354,7 +354,7 @@ sps_kernel_config point_config(const sps_plan* p, const std::vector<PlanGene>& g
     }
     sps_dedisp_config* k = p->mode == SPS_MODE_BRUTE ? &c.brute : (genes[g].kernel == 0 ? &c.step1 : &c.step2);
     int32_t* fields[6] = {&k->dms_per_thread, &k->samples_per_thread, &k->warps_dm, &k->warps_time, &k->chunk,
-                          &k->pairs};
+                          &k->presum};
     *fields[genes[g].field] = v;
   }
   return c;

@@ -88,17 +88,19 @@ CONFIGS = [  # (dms_per_thread, samples_per_thread, warps_dm, warps_time, chunk)
 ]
 
 
-PAIR_CONFIGS = [  # (dms_per_thread, samples_per_thread, warps_dm, warps_time, chunk, pairs=1)
+PRESUM_CONFIGS = [  # (dms_per_thread, samples_per_thread, warps_dm, warps_time, chunk, presum)
     (1, 4, 1, 1, 2, 1), (1, 8, 2, 2, 6, 1), (2, 4, 4, 2, 16, 1), (2, 32, 2, 1, 8, 1), (4, 8, 2, 2, 10, 1),
     (4, 16, 8, 1, 8, 1), (8, 4, 2, 4, 8, 1), (8, 8, 4, 2, 4, 1), (1, 32, 16, 1, 4, 1), (4, 8, 4, 4, 6, 1),
+    (1, 4, 1, 1, 2, 2), (1, 8, 2, 2, 8, 2), (2, 4, 4, 2, 16, 2), (2, 32, 2, 1, 8, 2), (4, 8, 2, 2, 12, 2),
+    (4, 16, 8, 1, 4, 2), (8, 4, 2, 4, 8, 2), (8, 8, 4, 2, 4, 2), (1, 32, 16, 1, 4, 2), (4, 8, 4, 4, 6, 2),
 ]
 
 
-@pytest.mark.parametrize("cfg", CONFIGS + PAIR_CONFIGS)
+@pytest.mark.parametrize("cfg", CONFIGS + PRESUM_CONFIGS)
 def test_brute_configs_ragged(lib, cfg):
     # 37 channels (odd, not a multiple of any chunk), 29 DMs, 1003 samples: ragged everywhere.
-    # The pair kernel gets a finer DM grid: with 5.4 MHz channels a coarse grid
-    # spreads the pair delay differences too far for one tile's staging.
+    # The pre-summed kernels get a finer DM grid: with 5.4 MHz channels a coarse
+    # grid spreads the relative delays too far for one tile's staging.
     torch = _torch()
     dms = synth.dm_grid(29, 0.31 if len(cfg) > 5 and cfg[5] else 3.1)
     p = lib.Plan(37, 1300.0, 1500.0, 65.536e-6, 1003, dms, [1, 3, 8, 50])
@@ -111,6 +113,24 @@ def test_brute_configs_ragged(lib, cfg):
     lib.sps_dedisperse(p, xd, D)
     torch.cuda.synchronize()
     want = oracle.dedisperse(x, oracle.delay_table(1300.0, 1500.0, 37, 65.536e-6, dms), 1003)
+    assert np.array_equal(_to_np(D), want)
+
+
+@pytest.mark.parametrize("C", [38, 39, 40])
+@pytest.mark.parametrize("cfg", [(1, 4, 1, 1, 2, 2), (4, 8, 2, 2, 12, 2)])
+def test_quads_short_last_unit(lib, C, cfg):
+    """Channel counts ending in a unit of 2, 3 or 4 channels."""
+    torch = _torch()
+    dms = synth.dm_grid(29, 0.31)
+    p = lib.Plan(C, 1300.0, 1500.0, 65.536e-6, 1003, dms, [1, 3])
+    c = p.config
+    c.brute = lib.DedispConfig(*cfg)
+    p.config = c
+    x = synth.filterbank(C, 1300.0, 1500.0, 65.536e-6, p.input_samples, 5 + C, pitch=p.pitch)
+    D = torch.full((29, 1003), -7, dtype=torch.int32, device="cuda")
+    lib.sps_dedisperse(p, torch.from_numpy(x).cuda(), D)
+    torch.cuda.synchronize()
+    want = oracle.dedisperse(x, oracle.delay_table(1300.0, 1500.0, C, 65.536e-6, dms), 1003)
     assert np.array_equal(_to_np(D), want)
 
 
@@ -132,6 +152,16 @@ def test_brute_saturated_and_edges(lib):
     lib.sps_dedisperse(p, torch.from_numpy(x).cuda(), D)
     torch.cuda.synchronize()
     assert np.all(_to_np(D) == 255 * C)
+    # quad sums at their limit: 64 quads of 1020 per 16-bit lane, 4 quads per chunk
+    # (a finer DM grid keeps one tile's quad tuples within shared memory)
+    pq = lib.Plan(C, 1250.0, 1550.0, 81.92e-6, 500, synth.dm_grid(16, 0.5), [1, 7])
+    c = pq.config
+    c.brute = lib.DedispConfig(4, 16, 8, 1, 16, 2)
+    pq.config = c
+    D.fill_(0)
+    lib.sps_dedisperse(pq, torch.from_numpy(x).cuda(), D)
+    torch.cuda.synchronize()
+    assert np.all(_to_np(D) == 255 * C)
     # a single channel, single DM, single sample
     p1 = lib.Plan(1, 1250.0, 1550.0, 81.92e-6, 1, [0.0], [1])
     x1 = np.zeros((1, 16), np.uint8)
@@ -142,14 +172,14 @@ def test_brute_saturated_and_edges(lib):
     assert _to_np(D1).tolist() == [[201]]
 
 
-@pytest.mark.parametrize("pairs", [0, 1])
-def test_apertif_brute_sampled_rows(lib, pairs):
+@pytest.mark.parametrize("presum", [0, 1, 2])
+def test_apertif_brute_sampled_rows(lib, presum):
     """Full Apertif-shaped beam in the launch configurations the benchmark times."""
     torch = _torch()
     wl = synth.apertif_beam()
     p = lib.Plan.from_workload(wl)
     c = p.config
-    c.brute.pairs = pairs
+    c.brute.presum = presum
     p.config = c
     x = _x_for(p, wl)
     out = p.search(torch.from_numpy(x).cuda())
@@ -213,10 +243,13 @@ def test_subband_small_exact(lib, S):
 
 
 @pytest.mark.parametrize("cfg1,cfg2", [
-    # pair kernel on 4.7 MHz channels: delta ranges are wide, so one pair per chunk
+    # pre-summed kernels on 4.7 MHz channels: relative delays vary widely, so small chunks
     ((1, 4, 1, 1, 2, 1), (1, 4, 1, 1, 1)),
     ((4, 16, 8, 1, 2, 1), (4, 16, 8, 1, 8)),
     ((2, 8, 2, 2, 2, 1), (8, 4, 4, 2, 5)),
+    ((1, 4, 1, 1, 4, 2), (1, 4, 1, 1, 1)),
+    ((4, 16, 8, 1, 4, 2), (4, 16, 8, 1, 8)),
+    ((2, 8, 2, 2, 8, 2), (8, 4, 4, 2, 5)),
     ((1, 4, 1, 1, 2), (1, 4, 1, 1, 1)),
     ((2, 8, 2, 2, 6), (2, 8, 2, 2, 3)),
     ((4, 16, 8, 1, 16), (8, 4, 4, 2, 5)),
@@ -242,13 +275,14 @@ def test_subband_configs(lib, cfg1, cfg2):
     assert np.array_equal(_to_np(D), Do)
 
 
-@pytest.mark.parametrize("pairs", [0, 1])
-def test_apertif_subband_sampled(lib, pairs):
+@pytest.mark.parametrize("presum", [0, 1, 2])
+def test_apertif_subband_sampled(lib, presum):
     torch = _torch()
     wl = synth.apertif_beam(subband=True)
     p = lib.Plan.from_workload(wl)
     c = p.config
-    c.step1.pairs = pairs
+    # quads on the widely spaced coarse trials: smaller DM tiles keep a chunk's tuples in shared memory
+    c.step1 = lib.DedispConfig(1, 16, 8, 1, 8, 2) if presum == 2 else lib.DedispConfig(4, 16, 8, 1, 16, presum)
     p.config = c
     x = _x_for(p, wl)
     xd = torch.from_numpy(x).cuda()

@@ -34,7 +34,7 @@ def test_noalloc_matches_the_workspace_entry_point_twice(lib, which):
     p = lib.Plan.from_workload(wl)
     if which == "apertif":  # the single-channel kernel's staging fits the static scratch
         c = p.config
-        c.brute.pairs = 0
+        c.brute.presum = 0
         p.config = c
     x = synth.filterbank(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, p.input_samples, wl.seed, wl.pulses,
                          pitch=p.pitch)
