@@ -88,10 +88,10 @@ sps_status run_u8_pass(const sps_plan* p, const sps_dedisp_config& cfg, const ui
                        void* out, int32_t out_u16, cudaStream_t st) {
   if (cfg.presum) {
     uint16_t* q = reinterpret_cast<uint16_t*>(ws);
-    sps_status s = launch_presum_series(x, pitch, (int32_t)p->n_in, p->d_presum_series, p->n_presum_series, q,
-                                        p->q_pitch, st);
-    if (s) return s;
     const int32_t K = 1 << cfg.presum;
+    sps_status s = launch_presum_series(x, pitch, (int32_t)p->n_in, p->d_presum_units, p->n_presum_units, K,
+                                        p->presum_max_rel, p->d_presum_series, p->n_presum_series, q, p->q_pitch, st);
+    if (s) return s;
     PresumPassArgs a{};
     a.q = q;
     a.q_pitch = p->q_pitch;
@@ -103,6 +103,7 @@ sps_status run_u8_pass(const sps_plan* p, const sps_dedisp_config& cfg, const ui
     a.n_groups = p->channels / per;
     a.group_units = (per + K - 1) / K;
     a.fold_units = 65535 / (255 * K);
+    a.max_start = (int32_t)(p->n_in - p->n_t);
     a.n_out = n_out;
     a.out_pitch = out_pitch;
     a.dmax_tile = dmax;
@@ -229,6 +230,7 @@ sps_status sps_plan_destroy(sps_plan* p) {
   cudaFree(p->d_b0);
   cudaFree(p->d_offs);
   cudaFree(p->d_presum_series);
+  cudaFree(p->d_presum_units);
   cudaFree(p->d_presum_slots);
   cudaFree(p->d_presum_offs);
   if (swap) cudaSetDevice(cur);

@@ -86,6 +86,7 @@ presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb, int slots_max) 
   const int n_chunks = (P + cp_max - 1) / cp_max;
   const uint32_t toff = (uint32_t)(t_sub * 128 * NW + lane * 4);  // bytes
   const int64_t chunk_row = ((int64_t)tile * a.n_groups + g) * n_chunks;
+  const bool clip = t0 + wb / 2 + a.max_start > a.q_pitch;  // windows may be cut at the row end
 
   if (tid == 0) {
     aborted = 0;
@@ -120,10 +121,14 @@ presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb, int slots_max) 
     const int n2 = 2 * f.n_slots;
     const uint32_t tbl_bytes = (uint32_t)(cp * a.di_pad * 2);
     auto entry = [&](int q) { return q == lane ? f.e0 : (q == lane + 32 ? f.e1 : __ldg(&list[q >> 1])); };
-    uint32_t bytes_all = 0;
-    for (int q = lane; q < n2; q += 32) bytes_all += (uint32_t)min(wb, 2 * (a.q_pitch - (t0 + entry(q).y)));
+    // every window is whole unless it may run past the end of a series row
+    uint32_t bytes_all = (uint32_t)(n2 * wb);
+    if (clip) {
+      bytes_all = 0;
+      for (int q = lane; q < n2; q += 32) bytes_all += (uint32_t)min(wb, 2 * (a.q_pitch - (t0 + entry(q).y)));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bytes_all += __shfl_xor_sync(0xffffffffu, bytes_all, o);
+      for (int o = 16; o > 0; o >>= 1) bytes_all += __shfl_xor_sync(0xffffffffu, bytes_all, o);
+    }
     if (lane == 0) mbar_arrive_expect_tx(&full[st], bytes_all + tbl_bytes);
     __syncwarp();
     for (int q = lane; q < n2; q += 32) {
@@ -164,21 +169,25 @@ presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb, int slots_max) 
   if (warp == 0)
     for (int k = 0; k < min(kStages - 1, n_chunks); k++) issue(k, fetch(k));
 
+  // A warp that sees a wait run out stops waiting for the rest of the block
+  // (`bad`) and records it for the block (`aborted`, read once at the end).
   int pending = 0;
   int ch = 0;
+  int turn = 0;  // ch mod nwarps
+  bool bad = false;
   for (; ch < n_chunks; ch++) {
     const int st = ch % kStages;
     const int cp = min(cp_max, P - ch * cp_max);
-    const bool issuer = ch % nwarps == warp && ch + kStages - 1 < n_chunks;
+    const bool issuer = turn == warp && ch + kStages - 1 < n_chunks;
+    if (++turn == nwarps) turn = 0;
     if (pending + cp > a.fold_units) { fold(); pending = 0; }
     Fetched next{};
     if (issuer) next = fetch(ch + kStages - 1);
-    bool ok = !aborted;
-    if (ok && !mbar_wait(&full[st], (ch / kStages) & 1, a.status)) {
+    if (!bad && !mbar_wait(&full[st], (ch / kStages) & 1, a.status)) {
+      bad = true;
       aborted = 1;
-      ok = false;
     }
-    if (ok) {
+    if (!bad) {
       const uint32_t base = smem_u32(smem) + (uint32_t)(st * stage_bytes) + toff;
       const uint16_t* tb =
           reinterpret_cast<const uint16_t*>(smem + st * stage_bytes + slots_max * 2 * wb) + dm_sub * ND;
@@ -211,12 +220,14 @@ presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb, int slots_max) 
     pending += cp;
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
-    if (issuer && !aborted) {
+    if (issuer && !bad) {
       const int prev = ch - 1;  // the stage chunk ch + 2 reuses
-      if (prev >= 0 && !mbar_wait(&empty[prev % kStages], (prev / kStages) & 1, a.status))
+      if (prev >= 0 && !mbar_wait(&empty[prev % kStages], (prev / kStages) & 1, a.status)) {
+        bad = true;
         aborted = 1;
-      else
+      } else {
         issue(ch + kStages - 1, next);
+      }
     }
   }
   __syncthreads();  // every warp has left the loop
@@ -262,35 +273,13 @@ presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb, int slots_max) 
   }
 }
 
-// Adds bytes u + j .. u + j + 15 of a channel row, for j = 0 and 1, into
-// v[j] as eight words of 16-bit lanes (bytes at and beyond in_len read as 0).
-// `row` is 8-byte aligned.  Three aligned 8-byte loads cover both copies.
-__device__ __forceinline__ void add_bytes16x2(const uint8_t* row, int u, int in_len, uint32_t (&v)[2][8]) {
-  const int b = u & ~7;
-  uint32_t W[6];
-  if (u >= 0 && b + 24 <= in_len) {
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-      const uint2 t = __ldg(reinterpret_cast<const uint2*>(row + b + 8 * k));
-      W[2 * k] = t.x;
-      W[2 * k + 1] = t.y;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-      uint32_t w = 0;
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        const int p = b + 4 * k + i;
-        if (p >= 0 && p < in_len) w |= (uint32_t)__ldg(row + p) << (8 * i);
-      }
-      W[k] = w;
-    }
-  }
+// Adds bytes o + j .. o + j + 15 of W (24 bytes, o in 0 .. 7), for j = 0 and
+// 1, into v[j] as eight words of 16-bit lanes.
+__device__ __forceinline__ void add_window16x2(const uint32_t (&W)[6], int o, uint32_t (&v)[2][8]) {
 #pragma unroll
   for (int j = 0; j < 2; j++) {
-    const int o = u - b + j;  // 0 .. 8: byte offset of the copy's first sample in W
-    const int wi = o >> 2, sh = (o & 3) * 8;
+    const int oj = o + j;  // 0 .. 8
+    const int wi = oj >> 2, sh = (oj & 3) * 8;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       const uint32_t lo = wi == 0 ? W[k] : (wi == 1 ? W[k + 1] : W[k + 2]);
@@ -302,17 +291,116 @@ __device__ __forceinline__ void add_bytes16x2(const uint8_t* row, int u, int in_
   }
 }
 
+// Bytes u .. u + 23 of a channel row (u & 7 == 0) as six words; bytes at and
+// beyond in_len read as 0.  `row` is 16-byte aligned.
+__device__ __forceinline__ void load_row24(const uint8_t* row, int u, int in_len, uint32_t (&W)[6]) {
+  if (u >= 0 && u + 24 <= in_len) {
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const uint2 t = __ldg(reinterpret_cast<const uint2*>(row + u + 8 * k));
+      W[2 * k] = t.x;
+      W[2 * k + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      uint32_t w = 0;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const int p = u + 4 * k + i;
+        if (p >= 0 && p < in_len) w |= (uint32_t)__ldg(row + p) << (8 * i);
+      }
+      W[k] = w;
+    }
+  }
+}
+
+constexpr int kSeriesThreads = 256;
+constexpr int kSeriesBlock = kSeriesThreads * 16;  // samples per block
+
+__device__ __forceinline__ void store_series(uint16_t* q, int64_t q_pitch, int s, int u0, const uint32_t (&v)[2][8]) {
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    uint4* o = reinterpret_cast<uint4*>(q + ((int64_t)s * 2 + j) * q_pitch + u0);
+    o[0] = make_uint4(v[j][0], v[j][1], v[j][2], v[j][3]);
+    o[1] = make_uint4(v[j][4], v[j][5], v[j][6], v[j][7]);
+  }
+}
+
 // Series s, both copies j: q[(2 s + j) * q_pitch + u] = sum_c x[c0 + c][u + j + rel_c]
-// (rel of the last channel 0).  One thread writes 16 samples of each copy.
-__global__ void __launch_bounds__(256) presum_series_kernel(const uint8_t* x, int64_t pitch, int32_t in_len,
-                                                            const PresumSeries* series, int32_t n_series,
-                                                            uint16_t* q, int32_t q_pitch) {
+// (rel of the last channel 0).  A block takes one unit and kSeriesBlock samples:
+// it stages the unit's channel rows once in shared memory (win_bytes per row,
+// covering the block plus the unit's largest relative delay), then every
+// thread writes 16 samples of both copies of each of the unit's series.
+__global__ void __launch_bounds__(kSeriesThreads) presum_series_kernel(const uint8_t* x, int64_t pitch,
+                                                                       int32_t in_len, const PresumUnit* units,
+                                                                       const PresumSeries* series, uint16_t* q,
+                                                                       int32_t q_pitch, int32_t win_bytes) {
+  extern __shared__ __align__(16) uint8_t win[];
+  const int4 uh = __ldg(reinterpret_cast<const int4*>(units + blockIdx.x));  // {c0, n, s_begin, s_end}
+  const int ub = blockIdx.y * kSeriesBlock;
+  for (int c = 0; c < uh.y; c++) {
+    const uint8_t* row = x + (int64_t)(uh.x + c) * pitch;
+    for (int k = threadIdx.x; k < win_bytes / 16; k += kSeriesThreads) {
+      const int p = ub + 16 * k;
+      uint4 v;
+      if (p + 16 <= in_len) {
+        v = __ldg(reinterpret_cast<const uint4*>(row + p));
+      } else {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          uint32_t t = 0;
+#pragma unroll
+          for (int b = 0; b < 4; b++)
+            if (p + 4 * i + b < in_len) t |= (uint32_t)__ldg(row + p + 4 * i + b) << (8 * b);
+          w[i] = t;
+        }
+        v = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      *reinterpret_cast<uint4*>(win + c * win_bytes + 16 * k) = v;
+    }
+  }
+  __syncthreads();
+  const int u0 = ub + 16 * (int)threadIdx.x;
+  if (u0 >= q_pitch) return;
+  for (int s = uh.z; s < uh.w; s++) {
+    const int4 h = __ldg(reinterpret_cast<const int4*>(series + s));  // {c0, n, rel0, rel1}
+    const int rel2 = __ldg(&series[s].rel[2]);
+    uint32_t v[2][8];
+#pragma unroll
+    for (int j = 0; j < 2; j++)
+#pragma unroll
+      for (int k = 0; k < 8; k++) v[j][k] = 0u;
+    for (int c = 0; c < h.y; c++) {
+      const int rel = c + 1 == h.y ? 0 : (c == 0 ? h.z : (c == 1 ? h.w : rel2));
+      const int off = 16 * (int)threadIdx.x + rel, b = off & ~7;
+      const uint2* src = reinterpret_cast<const uint2*>(win + c * win_bytes + b);
+      uint32_t W[6];
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const uint2 t = src[k];
+        W[2 * k] = t.x;
+        W[2 * k + 1] = t.y;
+      }
+      add_window16x2(W, off - b, v);
+    }
+    store_series(q, q_pitch, s, u0, v);
+  }
+}
+
+// The same series straight from global memory, one (series, 16 samples) per
+// thread: for units whose relative delays are too long to stage.
+__global__ void __launch_bounds__(256) presum_series_direct_kernel(const uint8_t* x, int64_t pitch,
+                                                                   int32_t in_len, const PresumSeries* series,
+                                                                   int32_t n_series, uint16_t* q,
+                                                                   int32_t q_pitch) {
   const int64_t per_row = q_pitch >> 4;
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= per_row * n_series) return;
   const int s = (int)(id / per_row);
   const int u0 = (int)(id - (int64_t)s * per_row) << 4;
-  const int4 h = __ldg(reinterpret_cast<const int4*>(series + s));  // {c0, n, rel0, rel1}
+  const int4 h = __ldg(reinterpret_cast<const int4*>(series + s));
   const int rel2 = __ldg(&series[s].rel[2]);
   uint32_t v[2][8];
 #pragma unroll
@@ -321,14 +409,12 @@ __global__ void __launch_bounds__(256) presum_series_kernel(const uint8_t* x, in
     for (int k = 0; k < 8; k++) v[j][k] = 0u;
   for (int c = 0; c < h.y; c++) {
     const int rel = c + 1 == h.y ? 0 : (c == 0 ? h.z : (c == 1 ? h.w : rel2));
-    add_bytes16x2(x + (int64_t)(h.x + c) * pitch, u0 + rel, in_len, v);
+    const int u = u0 + rel, b = u & ~7;
+    uint32_t W[6];
+    load_row24(x + (int64_t)(h.x + c) * pitch, b, in_len, W);
+    add_window16x2(W, u - b, v);
   }
-#pragma unroll
-  for (int j = 0; j < 2; j++) {
-    uint4* o = reinterpret_cast<uint4*>(q + ((int64_t)s * 2 + j) * q_pitch + u0);
-    o[0] = make_uint4(v[j][0], v[j][1], v[j][2], v[j][3]);
-    o[1] = make_uint4(v[j][4], v[j][5], v[j][6], v[j][7]);
-  }
+  store_series(q, q_pitch, s, u0, v);
 }
 
 typedef void (*PresumKernel)(PresumPassArgs, int, int, int, int);
@@ -388,12 +474,24 @@ size_t presum_smem_bytes(const sps_dedisp_config& c, int32_t dmax_tile, int32_t 
   return kStages * stage + 16 * kStages;
 }
 
-sps_status launch_presum_series(const uint8_t* x, int64_t pitch, int32_t in_len, const PresumSeries* series,
+sps_status launch_presum_series(const uint8_t* x, int64_t pitch, int32_t in_len, const PresumUnit* units,
+                                int32_t n_units, int32_t unit_channels, int32_t max_rel, const PresumSeries* series,
                                 int32_t n_series, uint16_t* q, int32_t q_pitch, cudaStream_t st) {
-  const int64_t threads = (int64_t)(q_pitch >> 4) * n_series;
-  if (threads == 0) return SPS_OK;
-  presum_series_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(x, pitch, in_len, series, n_series, q,
-                                                                           q_pitch);
+  if (n_series == 0) return SPS_OK;
+  // staged window per channel row: the block's samples, the largest relative
+  // delay, and the 24-byte reach of the last thread's loads
+  const int64_t win = ((int64_t)kSeriesBlock + max_rel + 32 + 15) / 16 * 16;
+  const int64_t smem = win * unit_channels;
+  if (smem <= 96 * 1024) {
+    SPS_CUDA(cudaFuncSetAttribute(presum_series_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)n_units, (unsigned)((q_pitch + kSeriesBlock - 1) / kSeriesBlock));
+    presum_series_kernel<<<grid, kSeriesThreads, (size_t)smem, st>>>(x, pitch, in_len, units, series, q, q_pitch,
+                                                                    (int32_t)win);
+  } else {
+    const int64_t threads = (int64_t)(q_pitch >> 4) * n_series;
+    presum_series_direct_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(x, pitch, in_len, series,
+                                                                                   n_series, q, q_pitch);
+  }
   SPS_CUDA(cudaGetLastError());
   return SPS_OK;
 }

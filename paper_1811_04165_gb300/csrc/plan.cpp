@@ -108,7 +108,7 @@ std::vector<sps_kernel_config> default_configs() {
   const sps_dedisp_config u8[3] = {{4, 16, 8, 1, 16, 0}, {4, 16, 8, 1, 4, 0}, {1, 4, 1, 1, 2, 0}};
   const sps_dedisp_config s2[3] = {{4, 16, 8, 1, 8, 0}, {4, 16, 8, 1, 2, 0}, {1, 4, 1, 1, 1, 0}};
   sps_kernel_config c{};
-  c.brute = {4, 16, 8, 1, 12, 2};
+  c.brute = {8, 8, 4, 2, 12, 2};
   c.step1 = u8[0];
   c.step2 = s2[0];
   c.snr = {256};
@@ -224,20 +224,27 @@ sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg) {
                                              p->channels / p->n_subbands, pass, dmax_1, &pt);
     if (s) return s;
     PresumSeries* dser = nullptr;
+    PresumUnit* dunit = nullptr;
     int2* dslot = nullptr;
     uint16_t* doffs = nullptr;
     s = upload(pt.series, &dser);
+    if (s == SPS_OK) s = upload(pt.units, &dunit);
     if (s == SPS_OK) s = upload(pt.slots, &dslot);
     if (s == SPS_OK) s = upload(pt.offs, &doffs);
     if (s != SPS_OK) {
       cudaFree(dser);
+      cudaFree(dunit);
       cudaFree(dslot);
       return s;
     }
     cudaFree(p->d_presum_series);
+    cudaFree(p->d_presum_units);
     cudaFree(p->d_presum_slots);
     cudaFree(p->d_presum_offs);
     p->d_presum_series = dser;
+    p->d_presum_units = dunit;
+    p->n_presum_units = (int32_t)pt.units.size();
+    p->presum_max_rel = pt.max_rel;
     p->d_presum_slots = dslot;
     p->d_presum_offs = doffs;
     p->n_presum_series = (int32_t)pt.series.size();

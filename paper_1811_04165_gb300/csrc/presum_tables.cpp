@@ -99,6 +99,8 @@ sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int3
   std::vector<int32_t> sbase((size_t)G * U);
   std::vector<std::vector<Rel>> all((size_t)G * U);
   out->series.clear();
+  out->units.clear();
+  out->max_rel = 0;
   for (int32_t g = 0; g < G; g++)
     for (int32_t u = 0; u < U; u++) {
       const Unit un = unit_of(g, u, per, K);
@@ -109,6 +111,9 @@ sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int3
           return fail(SPS_ERR_INVALID_ARG, "a lower channel arrives before a higher one");
       sbase[(size_t)g * U + u] = (int32_t)out->series.size();
       for (const Rel& r : v) out->series.push_back({un.c0, un.n, {r[0], r[1], r[2]}, {0, 0, 0}});
+      const int32_t max_rel = v.back()[0];  // tuples sorted: the last has the largest first delay
+      out->units.push_back({un.c0, un.n, sbase[(size_t)g * U + u], (int32_t)out->series.size(), max_rel, {0, 0, 0}});
+      out->max_rel = std::max(out->max_rel, max_rel);
     }
 
   // slot lists per (tile, group, chunk): each unit's tuples within the tile

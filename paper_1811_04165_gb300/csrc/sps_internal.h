@@ -61,6 +61,7 @@ struct PresumPassArgs {
   int32_t n_groups;
   int32_t group_units;     // units per group
   int32_t fold_units;      // units a 16-bit lane sums exactly: 65535 / (255 K)
+  int32_t max_start;       // bound on any staged window's start (the pass's largest delay)
   int32_t n_out;
   int64_t out_pitch;
   int32_t dmax_tile;
@@ -75,8 +76,16 @@ struct PresumSeries {
   int32_t c0, n, rel[3], pad[3];
 };
 
+// One unit of K adjacent channels and the range of its series in the table;
+// max_rel = the largest relative delay of any of its series (of its first channel).
+struct PresumUnit {
+  int32_t c0, n, s_begin, s_end, max_rel, pad[3];
+};
+
 struct PresumTables {
   std::vector<PresumSeries> series;
+  std::vector<PresumUnit> units;
+  int32_t max_rel = 0;
   std::vector<int2> slots;
   std::vector<uint16_t> offs;
   int32_t slots_max = 0;
@@ -122,7 +131,8 @@ sps_status launch_expand(const uint8_t* x, int64_t pitch, int32_t in_len, int32_
                          int64_t pitch4, cudaStream_t st);
 sps_status launch_detect(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
                          int32_t n_dms, int32_t n_widths, int32_t* best, cudaStream_t st);
-sps_status launch_presum_series(const uint8_t* x, int64_t pitch, int32_t in_len, const PresumSeries* series,
+sps_status launch_presum_series(const uint8_t* x, int64_t pitch, int32_t in_len, const PresumUnit* units,
+                                int32_t n_units, int32_t unit_channels, int32_t max_rel, const PresumSeries* series,
                                 int32_t n_series, uint16_t* q, int32_t q_pitch, cudaStream_t st);
 sps_status launch_presum_pass(const PresumPassArgs& a, const sps_dedisp_config& cfg, cudaStream_t st);
 bool presum_config_supported(const sps_dedisp_config& cfg, std::string* why);
@@ -201,6 +211,9 @@ struct sps_plan {
 
   // pre-summed-series tables (when the uint8 pass has presum > 0)
   sps::PresumSeries* d_presum_series = nullptr;
+  sps::PresumUnit* d_presum_units = nullptr;
+  int32_t n_presum_units = 0;
+  int32_t presum_max_rel = 0;
   int2* d_presum_slots = nullptr;
   uint16_t* d_presum_offs = nullptr;
   int32_t n_presum_series = 0;   // of the current configuration's table
