@@ -95,8 +95,9 @@ sps_status run_u8_pass(const sps_plan* p, const sps_dedisp_config& cfg, const ui
     PresumPassArgs a{};
     a.q = q;
     a.q_pitch = p->q_pitch;
-    a.slots = p->d_presum_slots;
-    a.slots_max = p->presum_slots_max;
+    a.copies = p->d_presum_copies;
+    a.copies_max = p->presum_copies_max;
+    a.data_bytes = p->presum_data_bytes;
     a.offs = p->d_presum_offs;
     a.di_pad = presum_di_pad(cfg);
     a.n_dm = rows;
@@ -231,7 +232,7 @@ sps_status sps_plan_destroy(sps_plan* p) {
   cudaFree(p->d_offs);
   cudaFree(p->d_presum_series);
   cudaFree(p->d_presum_units);
-  cudaFree(p->d_presum_slots);
+  cudaFree(p->d_presum_copies);
   cudaFree(p->d_presum_offs);
   if (swap) cudaSetDevice(cur);
   delete p;

@@ -10,8 +10,9 @@
 // needs only a few tuples rel per unit.  A pre-pass writes, for every unit and
 // every tuple its trials need, the series S_rel as uint16 (two copies, the
 // second shifted by one sample, so every 32-bit shared load is aligned); the
-// block then stages, per chunk of units, just the series its tile uses (a
-// host-built slot list) with bulk asynchronous copies (TMA) into a ring of
+// block then stages, per chunk of units, just the windows of the copies its
+// tile reads (a host-built list, packed) with bulk asynchronous copies (TMA)
+// into a ring of
 // kStages mbarrier-tracked stages.  A 32-bit load holds two samples of a unit sum in 16-bit
 // lanes: one add accumulates 2 K channel-samples, with no unpacking.  Unit sums
 // are <= 255 K, so 16-bit lanes are exact for 65535 / (255 K) units (128 pairs,
@@ -64,12 +65,13 @@ __device__ __forceinline__ void load_offs(const uint16_t* p, uint32_t (&o)[ND]) 
 
 template <int ND, int NW>
 __global__ void __launch_bounds__(kMaxThreads, 1)
-presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb, int slots_max) {
+presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int wt = (int)(blockDim.x >> 5) / wd;
   const int Tt = wt * 64 * NW;
   const int Di = wd * ND;
-  const int stage_bytes = slots_max * 2 * wb + cp_max * a.di_pad * 2;
+  const int copies_max = a.copies_max;
+  const int stage_bytes = a.data_bytes + cp_max * a.di_pad * 2;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * stage_bytes);
   uint64_t* empty = full + kStages;
   __shared__ volatile int aborted;
@@ -99,48 +101,60 @@ presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb, int slots_max) 
   }
   __syncthreads();
 
-  // One warp stages a whole chunk: the chunk's slot list names the series (and
-  // window start) of each slot; copy j of slot k lands at (2k + j) * wb, and
-  // lane 0 also copies the chunk's offset table and arrives on the stage's
-  // "full" barrier with the byte count.  The issuing warp fetches its first two
-  // list entries per lane (and the slot count) a chunk early (`fetch`).
-  struct Fetched { int n_slots; int2 e0, e1; };
+  // One warp stages a whole chunk: the chunk's copy list names, per window,
+  // the series copy (row), its first sample relative to the time tile, its
+  // byte in the stage and its length; lane 0 also copies the chunk's offset
+  // table and arrives on the stage's "full" barrier with the byte count (the
+  // list's last entry, unless a window may be cut at the end of a row).  The
+  // issuing warp fetches the count and its first list entry per lane a chunk
+  // early (`fetch`).
+  // A list entry is {row, start, (stage byte / 16) | (bytes / 16) << 16, 0};
+  // the last is {count, total bytes}.
+  struct Fetched { uint32_t nt; int row, start, at; };  // nt = count | total << 14
   auto fetch = [&](int ch) {
-    const int2* list = a.slots + (chunk_row + ch) * (slots_max + 1);
+    const int4* list = a.copies + (chunk_row + ch) * (copies_max + 1);
     Fetched f;
-    f.n_slots = __ldg(&list[slots_max].x);
-    f.e0 = lane < 2 * slots_max ? __ldg(&list[lane >> 1]) : make_int2(0, 0);
-    f.e1 = lane + 32 < 2 * slots_max ? __ldg(&list[(lane + 32) >> 1]) : make_int2(0, 0);
+    const int4 h = __ldg(&list[copies_max]);
+    f.nt = (uint32_t)h.x | ((uint32_t)h.y << 14);
+    const int4 e = lane < copies_max ? __ldg(&list[lane]) : make_int4(0, 0, 0, 0);
+    f.row = e.x;
+    f.start = e.y;
+    f.at = e.z;
     return f;
   };
   auto issue = [&](int ch, const Fetched& f) {
     const int st = ch % kStages;
     uint8_t* sb = smem + st * stage_bytes;
     const int pb = ch * cp_max, cp = min(cp_max, P - pb);
-    const int2* list = a.slots + (chunk_row + ch) * (slots_max + 1);
-    const int n2 = 2 * f.n_slots;
+    const int4* list = a.copies + (chunk_row + ch) * (copies_max + 1);
     const uint32_t tbl_bytes = (uint32_t)(cp * a.di_pad * 2);
-    auto entry = [&](int q) { return q == lane ? f.e0 : (q == lane + 32 ? f.e1 : __ldg(&list[q >> 1])); };
-    // every window is whole unless it may run past the end of a series row
-    uint32_t bytes_all = (uint32_t)(n2 * wb);
+    const int n = (int)(f.nt & 0x3FFFu);
+    auto entry = [&](int q) {
+      if (q == lane) return make_int3(f.row, f.start, f.at);
+      const int4 e = __ldg(&list[q]);
+      return make_int3(e.x, e.y, e.z);
+    };
+    auto length = [&](const int3& e) {
+      const int w = (int)((uint32_t)e.z >> 16) * 16;
+      return clip ? min(w, 2 * (a.q_pitch - (t0 + e.y))) : w;
+    };
+    uint32_t bytes_all = f.nt >> 14;
     if (clip) {
       bytes_all = 0;
-      for (int q = lane; q < n2; q += 32) bytes_all += (uint32_t)min(wb, 2 * (a.q_pitch - (t0 + entry(q).y)));
+      for (int q = lane; q < n; q += 32) bytes_all += (uint32_t)length(entry(q));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) bytes_all += __shfl_xor_sync(0xffffffffu, bytes_all, o);
     }
     if (lane == 0) mbar_arrive_expect_tx(&full[st], bytes_all + tbl_bytes);
     __syncwarp();
-    for (int q = lane; q < n2; q += 32) {
-      const int2 e = entry(q);
-      const int start = t0 + e.y;
-      const uint32_t bytes = (uint32_t)min(wb, 2 * (a.q_pitch - start));
-      const uint16_t* src = a.q + ((int64_t)e.x * 2 + (q & 1)) * a.q_pitch + start;
-      bulk_g2s(sb + q * wb, src, bytes, &full[st]);
+    for (int q = lane; q < n; q += 32) {
+      const int3 e = entry(q);
+      const uint16_t* src = a.q + (int64_t)e.x * a.q_pitch + t0 + e.y;
+      bulk_g2s(sb + ((uint32_t)e.z & 0xFFFFu) * 16, src, (uint32_t)length(e), &full[st]);
     }
     if (lane == 0) {
       const uint16_t* src = a.offs + (((int64_t)tile * a.n_groups + g) * P + pb) * a.di_pad;
-      bulk_g2s(sb + slots_max * 2 * wb, src, tbl_bytes, &full[st]);
+      bulk_g2s(sb + a.data_bytes, src, tbl_bytes, &full[st]);
       issued_upto = ch + 1;
     }
   };
@@ -190,7 +204,7 @@ presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb, int slots_max) 
     if (!bad) {
       const uint32_t base = smem_u32(smem) + (uint32_t)(st * stage_bytes) + toff;
       const uint16_t* tb =
-          reinterpret_cast<const uint16_t*>(smem + st * stage_bytes + slots_max * 2 * wb) + dm_sub * ND;
+          reinterpret_cast<const uint16_t*>(smem + st * stage_bytes + a.data_bytes) + dm_sub * ND;
       int p = 0;
       for (; p + 1 < cp; p += 2) {
         uint32_t e0[ND], e1[ND];
@@ -417,7 +431,7 @@ __global__ void __launch_bounds__(256) presum_series_direct_kernel(const uint8_t
   store_series(q, q_pitch, s, u0, v);
 }
 
-typedef void (*PresumKernel)(PresumPassArgs, int, int, int, int);
+typedef void (*PresumKernel)(PresumPassArgs, int, int, int);
 
 template <int ND, int NW>
 constexpr PresumKernel k() { return presum_pass_kernel<ND, NW>; }
@@ -468,9 +482,8 @@ bool presum_config_supported(const sps_dedisp_config& c, std::string* why) {
   return true;
 }
 
-size_t presum_smem_bytes(const sps_dedisp_config& c, int32_t dmax_tile, int32_t slots_max) {
-  const size_t stage = (size_t)slots_max * 2 * presum_window_bytes(c, dmax_tile) +
-                       (size_t)presum_chunk(c) * presum_di_pad(c) * 2;
+size_t presum_smem_bytes(const sps_dedisp_config& c, int32_t data_bytes) {
+  const size_t stage = (size_t)data_bytes + (size_t)presum_chunk(c) * presum_di_pad(c) * 2;
   return kStages * stage + 16 * kStages;
 }
 
@@ -502,12 +515,12 @@ sps_status launch_presum_pass(const PresumPassArgs& a, const sps_dedisp_config& 
   PresumKernel fn = find(c.dms_per_thread, c.samples_per_thread / 2);
   const int Di = c.warps_dm * c.dms_per_thread;
   const int Tt = c.warps_time * 32 * c.samples_per_thread;
-  const size_t smem = presum_smem_bytes(c, a.dmax_tile, a.slots_max);
+  const size_t smem = presum_smem_bytes(c, a.data_bytes);
   dim3 grid((a.n_dm + Di - 1) / Di, (a.n_out + Tt - 1) / Tt, a.n_groups);
   if (grid.y > 65535 || grid.z > 65535) return fail(SPS_ERR_UNSUPPORTED, "too many time tiles or groups");
   SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   fn<<<grid, 32 * c.warps_dm * c.warps_time, smem, st>>>(a, c.warps_dm, presum_chunk(c),
-                                                        presum_window_bytes(c, a.dmax_tile), a.slots_max);
+                                                        presum_window_bytes(c, a.dmax_tile));
   SPS_CUDA(cudaGetLastError());
   return SPS_OK;
 }

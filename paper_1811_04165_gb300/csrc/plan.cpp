@@ -108,7 +108,7 @@ std::vector<sps_kernel_config> default_configs() {
   const sps_dedisp_config u8[3] = {{4, 16, 8, 1, 16, 0}, {4, 16, 8, 1, 4, 0}, {1, 4, 1, 1, 2, 0}};
   const sps_dedisp_config s2[3] = {{4, 16, 8, 1, 8, 0}, {4, 16, 8, 1, 2, 0}, {1, 4, 1, 1, 1, 0}};
   sps_kernel_config c{};
-  c.brute = {8, 8, 4, 2, 12, 2};
+  c.brute = {4, 16, 8, 1, 16, 2};
   c.step1 = u8[0];
   c.step2 = s2[0];
   c.snr = {256};
@@ -122,18 +122,21 @@ std::vector<sps_kernel_config> default_configs() {
   return out;
 }
 
-// Most series slots any (tile, group, chunk) of the pre-summed kernel stages
-// for `presum` (cached).
-int32_t cached_presum_slots(const sps_plan* p, int which, int32_t presum, int32_t Di, int32_t cu) {
-  const int64_t key = ((int64_t)which << 48) | ((int64_t)presum << 40) | ((int64_t)Di << 20) | cu;
-  auto it = p->presum_slot_cache.find(key);
-  if (it != p->presum_slot_cache.end()) return it->second;
-  const int32_t K = 1 << presum;
+// Largest packed window data of any (tile, group, chunk) of the pre-summed
+// kernel for a configuration (cached).
+int32_t cached_presum_stage(const sps_plan* p, int which, const sps_dedisp_config& c) {
+  const int32_t Di = c.warps_dm * c.dms_per_thread, cu = presum_chunk(c);
+  const int32_t Tt = c.warps_time * 32 * c.samples_per_thread;
+  const int64_t key = ((int64_t)which << 62) | ((int64_t)c.presum << 58) | ((int64_t)Di << 42) |
+                      ((int64_t)cu << 26) | Tt;
+  auto it = p->presum_stage_cache.find(key);
+  if (it != p->presum_stage_cache.end()) return it->second;
+  const int32_t K = 1 << c.presum;
   const int32_t v = which == 0
-                        ? presum_slots(p->delays, (int32_t)p->dms.size(), p->channels, p->channels, K, Di, cu)
-                        : presum_slots(p->d1, (int32_t)p->coarse_dms.size(), p->channels,
-                                       p->channels / p->n_subbands, K, Di, cu);
-  p->presum_slot_cache[key] = v;
+                        ? presum_stage_data(p->delays, (int32_t)p->dms.size(), p->channels, p->channels, K, Di, cu, Tt)
+                        : presum_stage_data(p->d1, (int32_t)p->coarse_dms.size(), p->channels,
+                                            p->channels / p->n_subbands, K, Di, cu, Tt);
+  p->presum_stage_cache[key] = v;
   return v;
 }
 
@@ -172,8 +175,7 @@ sps_status check_config(const sps_plan* p, const sps_kernel_config& cfg, ConfigC
     c.dmax_b = cached_spread(p, 0, di);
     const size_t need =
         cfg.brute.presum
-            ? presum_smem_bytes(cfg.brute, c.dmax_b,
-                                cached_presum_slots(p, 0, cfg.brute.presum, di, presum_chunk(cfg.brute)))
+            ? presum_smem_bytes(cfg.brute, cached_presum_stage(p, 0, cfg.brute))
             : u8_smem_bytes(cfg.brute, c.dmax_b, p->channels);
     if (need > (size_t)p->max_smem)
       return fail(SPS_ERR_INVALID_ARG, "brute config needs more shared memory than a block may use");
@@ -196,8 +198,7 @@ sps_status check_config(const sps_plan* p, const sps_kernel_config& cfg, ConfigC
     const int32_t di1 = cfg.step1.warps_dm * cfg.step1.dms_per_thread;
     const size_t need1 =
         cfg.step1.presum
-            ? presum_smem_bytes(cfg.step1, c.dmax_1,
-                                cached_presum_slots(p, 1, cfg.step1.presum, di1, presum_chunk(cfg.step1)))
+            ? presum_smem_bytes(cfg.step1, cached_presum_stage(p, 1, cfg.step1))
             : u8_smem_bytes(cfg.step1, c.dmax_1, p->channels / S);
     if (need1 > (size_t)p->max_smem)
       return fail(SPS_ERR_INVALID_ARG, "step1 config needs more shared memory than a block may use");
@@ -219,17 +220,17 @@ sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg) {
   if (pass.presum) {
     PresumTables pt;
     sps_status s = p->mode == SPS_MODE_BRUTE
-                       ? build_presum_tables(p->delays, n_dms, p->channels, p->channels, pass, dmax_b, &pt)
+                       ? build_presum_tables(p->delays, n_dms, p->channels, p->channels, pass, &pt)
                        : build_presum_tables(p->d1, (int32_t)p->coarse_dms.size(), p->channels,
-                                             p->channels / p->n_subbands, pass, dmax_1, &pt);
+                                             p->channels / p->n_subbands, pass, &pt);
     if (s) return s;
     PresumSeries* dser = nullptr;
     PresumUnit* dunit = nullptr;
-    int2* dslot = nullptr;
+    int4* dslot = nullptr;
     uint16_t* doffs = nullptr;
     s = upload(pt.series, &dser);
     if (s == SPS_OK) s = upload(pt.units, &dunit);
-    if (s == SPS_OK) s = upload(pt.slots, &dslot);
+    if (s == SPS_OK) s = upload(pt.copies, &dslot);
     if (s == SPS_OK) s = upload(pt.offs, &doffs);
     if (s != SPS_OK) {
       cudaFree(dser);
@@ -239,16 +240,17 @@ sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg) {
     }
     cudaFree(p->d_presum_series);
     cudaFree(p->d_presum_units);
-    cudaFree(p->d_presum_slots);
+    cudaFree(p->d_presum_copies);
     cudaFree(p->d_presum_offs);
     p->d_presum_series = dser;
     p->d_presum_units = dunit;
     p->n_presum_units = (int32_t)pt.units.size();
     p->presum_max_rel = pt.max_rel;
-    p->d_presum_slots = dslot;
+    p->d_presum_copies = dslot;
     p->d_presum_offs = doffs;
     p->n_presum_series = (int32_t)pt.series.size();
-    p->presum_slots_max = pt.slots_max;
+    p->presum_copies_max = pt.copies_max;
+    p->presum_data_bytes = pt.data_bytes;
   } else {
     std::vector<int32_t> b0;
     std::vector<uint32_t> offs;

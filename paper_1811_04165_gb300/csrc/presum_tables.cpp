@@ -7,14 +7,19 @@
 // unit contributes
 //   S_rel[t + d(i, e)],   S_rel[u] = sum_j x[c0 + j][u + rel_j],
 //   rel_j = d(i, c0 + j) - d(i, e) >= 0   (rel_{n-1} = 0),
-// so one series serves every trial with the same tuple rel.  The plan needs:
+// so one series serves every trial with the same tuple rel.  Each series is
+// stored twice, copy 1 shifted by one sample, so that a trial whose reference
+// delay d is odd reads aligned words of copy 1 at d - 1.  The plan needs:
 //   series : every (unit, rel) any trial uses, as rows of the workspace;
-//   slots  : per (DM tile, group, chunk of units), the series the tile uses and
-//            the start of their common window (d(i0, e) rounded down to 8);
+//   copies : per (DM tile, group, chunk of units), the windows of series
+//            copies the tile reads -- one per (tuple, parity of d) that occurs,
+//            each just long enough for its trials -- packed back to back in
+//            the shared-memory stage: {row, start, (stage byte / 16) |
+//            (bytes / 16) << 16, 0}, and last {count, total bytes};
 //   offs   : per (DM tile, group, unit, trial), the offset of the trial's first
-//            sample inside the staged chunk (slot, alignment copy, word), in
-//            4-byte words as uint16 (a stage is well below 256 KiB), so that one
-//            vector load fetches a warp's offsets for a unit.
+//            sample inside the packed stage, in 4-byte words as uint16 (a stage
+//            is well below 256 KiB), so that one vector load fetches a warp's
+//            offsets for a unit.
 // Tiles start at multiples of 64 samples, so nothing depends on the time tile.
 #include <algorithm>
 #include <array>
@@ -33,6 +38,10 @@ struct Unit {
 
 Unit unit_of(int32_t g, int32_t u, int32_t per, int32_t K) {
   return {g * per + K * u, std::min(K, per - K * u)};
+}
+
+int32_t ref_delay(const std::vector<int32_t>& d, int32_t C, int32_t i, Unit un) {
+  return d[(size_t)i * C + un.c0 + un.n - 1];
 }
 
 Rel rel_of(const std::vector<int32_t>& d, int32_t C, int32_t i, Unit un) {
@@ -56,6 +65,37 @@ int32_t index_of(const std::vector<Rel>& v, const Rel& r) {
   return (int32_t)(std::lower_bound(v.begin(), v.end(), r) - v.begin());
 }
 
+// The copy windows one unit needs in one DM tile of rows [i0, i1]: for tuple
+// k of `rels` and parity j, the trials' smallest and largest even-rounded
+// reference delay.  Window = [lo rounded down to 8, hi + Tt) samples.
+struct TileCopy {
+  int32_t k, j, lo, hi;
+};
+
+std::vector<TileCopy> tile_copies(const std::vector<int32_t>& d, int32_t C, int32_t i0, int32_t i1, Unit un,
+                                  const std::vector<Rel>& rels) {
+  std::vector<TileCopy> out;
+  for (int32_t i = i0; i <= i1; i++) {
+    const int32_t k = index_of(rels, rel_of(d, C, i, un));
+    const int32_t de = ref_delay(d, C, i, un), j = de & 1, e = de & ~1;
+    auto it = std::find_if(out.begin(), out.end(), [&](const TileCopy& c) { return c.k == k && c.j == j; });
+    if (it == out.end()) {
+      out.push_back({k, j, e, e});
+    } else {
+      it->lo = std::min(it->lo, e);
+      it->hi = std::max(it->hi, e);
+    }
+  }
+  std::sort(out.begin(), out.end(), [](const TileCopy& a, const TileCopy& b) {
+    return a.k != b.k ? a.k < b.k : a.j < b.j;
+  });
+  return out;
+}
+
+int32_t copy_start(const TileCopy& c) { return c.lo & ~7; }
+
+int32_t copy_bytes(const TileCopy& c, int32_t Tt) { return 2 * ((c.hi - copy_start(c) + Tt + 7) / 8 * 8); }
+
 }  // namespace
 
 int64_t count_presum_series(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t K) {
@@ -66,34 +106,37 @@ int64_t count_presum_series(const std::vector<int32_t>& d, int32_t rows, int32_t
   return n;
 }
 
-int32_t presum_slots(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t K, int32_t Di,
-                     int32_t cu) {
+int32_t presum_stage_data(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t K,
+                          int32_t Di, int32_t cu, int32_t Tt) {
   const int32_t U = (per + K - 1) / K;
-  int32_t best = 0;
+  int64_t best = 0;
   for (int32_t i0 = 0; i0 < rows; i0 += Di) {
     const int32_t i1 = std::min(i0 + Di, rows) - 1;
     for (int32_t g = 0; g < C / per; g++)
       for (int32_t u0 = 0; u0 < U; u0 += cu) {
-        int32_t count = 0;
-        for (int32_t u = u0; u < std::min(u0 + cu, U); u++)
-          count += (int32_t)distinct_rels(d, C, i0, i1, unit_of(g, u, per, K)).size();
-        best = std::max(best, count);
+        int64_t bytes = 0;
+        for (int32_t u = u0; u < std::min(u0 + cu, U); u++) {
+          const Unit un = unit_of(g, u, per, K);
+          for (const TileCopy& c : tile_copies(d, C, i0, i1, un, distinct_rels(d, C, i0, i1, un)))
+            bytes += copy_bytes(c, Tt);
+        }
+        best = std::max(best, bytes);
       }
   }
-  return best;
+  return (int32_t)std::min<int64_t>(best, INT32_MAX);
 }
 
 sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per,
-                               const sps_dedisp_config& cfg, int32_t dmax_tile, PresumTables* out) {
+                               const sps_dedisp_config& cfg, PresumTables* out) {
   const int32_t K = 1 << cfg.presum;
   const int32_t G = C / per;
   const int32_t U = (per + K - 1) / K;
   const int32_t Di = cfg.warps_dm * cfg.dms_per_thread;
+  const int32_t Tt = cfg.warps_time * 32 * cfg.samples_per_thread;
   const int32_t di_pad = presum_di_pad(cfg);
   const int32_t cu = presum_chunk(cfg);
   const int32_t n_chunks = (U + cu - 1) / cu;
   const int32_t n_tiles = (rows + Di - 1) / Di;
-  const int32_t wb = presum_window_bytes(cfg, dmax_tile);
 
   // series: per unit, every tuple over all trials
   std::vector<int32_t> sbase((size_t)G * U);
@@ -116,53 +159,53 @@ sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int3
       out->max_rel = std::max(out->max_rel, max_rel);
     }
 
-  // slot lists per (tile, group, chunk): each unit's tuples within the tile
-  const size_t n_keys = (size_t)n_tiles * G * U;
-  std::vector<std::vector<Rel>> tile_rels(n_keys);
-  std::vector<int32_t> first_slot(n_keys), b0_of(n_keys);
-  std::vector<std::vector<int2>> chunks((size_t)n_tiles * G * n_chunks);
-  int32_t slots_max = 0;
+  // copy lists per (tile, group, chunk), packed in order; the offsets of each
+  // trial point at its (tuple, parity) copy
+  const size_t n_chunk_rows = (size_t)n_tiles * G * n_chunks;
+  std::vector<std::vector<int4>> lists(n_chunk_rows);
+  std::vector<int32_t> used(n_chunk_rows, 0);
+  out->offs.assign((size_t)n_tiles * G * U * di_pad, 0);
+  int32_t copies_max = 0, data_bytes = 0;
   for (int32_t tile = 0; tile < n_tiles; tile++) {
     const int32_t i0 = tile * Di, i1 = std::min(i0 + Di, rows) - 1;
     for (int32_t g = 0; g < G; g++)
       for (int32_t u = 0; u < U; u++) {
         const Unit un = unit_of(g, u, per, K);
-        const size_t key = ((size_t)tile * G + g) * U + u;
-        std::vector<int2>& ck = chunks[((size_t)tile * G + g) * n_chunks + u / cu];
-        tile_rels[key] = distinct_rels(d, C, i0, i1, un);
-        b0_of[key] = d[(size_t)i0 * C + un.c0 + un.n - 1] & ~7;
-        first_slot[key] = (int32_t)ck.size();
-        for (const Rel& r : tile_rels[key])
-          ck.push_back({sbase[(size_t)g * U + u] + index_of(all[(size_t)g * U + u], r), b0_of[key]});
-        slots_max = std::max<int32_t>(slots_max, (int32_t)ck.size());
-      }
-  }
-  out->slots_max = slots_max;
-  out->wb = wb;
-  out->slots.assign(chunks.size() * (size_t)(slots_max + 1), int2{-1, 0});
-  for (size_t q = 0; q < chunks.size(); q++) {
-    int2* row = &out->slots[q * (slots_max + 1)];
-    for (size_t k = 0; k < chunks[q].size(); k++) row[k] = chunks[q][k];
-    row[slots_max] = int2{(int32_t)chunks[q].size(), 0};
-  }
-
-  // offsets: slot of the trial's tuple, alignment copy and word of its first sample
-  out->offs.assign(n_keys * di_pad, 0);
-  for (int32_t tile = 0; tile < n_tiles; tile++) {
-    const int32_t i0 = tile * Di;
-    for (int32_t g = 0; g < G; g++)
-      for (int32_t u = 0; u < U; u++) {
-        const Unit un = unit_of(g, u, per, K);
+        const size_t row = ((size_t)tile * G + g) * n_chunks + u / cu;
+        const std::vector<Rel> rels = distinct_rels(d, C, i0, i1, un);
+        const std::vector<TileCopy> copies = tile_copies(d, C, i0, i1, un, rels);
+        std::vector<int32_t> dst(copies.size());
+        for (size_t q = 0; q < copies.size(); q++) {
+          const TileCopy& c = copies[q];
+          const int32_t series = sbase[(size_t)g * U + u] + index_of(all[(size_t)g * U + u], rels[c.k]);
+          dst[q] = used[row];
+          lists[row].push_back({2 * series + c.j, copy_start(c), (dst[q] >> 4) | ((copy_bytes(c, Tt) >> 4) << 16), 0});
+          used[row] += copy_bytes(c, Tt);
+        }
+        copies_max = std::max<int32_t>(copies_max, (int32_t)lists[row].size());
+        data_bytes = std::max(data_bytes, used[row]);
         const size_t key = ((size_t)tile * G + g) * U + u;
         for (int32_t r = 0; r < di_pad; r++) {
           const int32_t i = std::min(i0 + std::min(r, Di - 1), rows - 1);
-          const int32_t slot = first_slot[key] + index_of(tile_rels[key], rel_of(d, C, i, un));
-          const int32_t rel = d[(size_t)i * C + un.c0 + un.n - 1] - b0_of[key];
-          const int64_t word = ((int64_t)(slot * 2 + (rel & 1)) * wb + (rel & ~1) * 2) / 4;
+          const int32_t k = index_of(rels, rel_of(d, C, i, un));
+          const int32_t de = ref_delay(d, C, i, un);
+          size_t q = 0;
+          while (copies[q].k != k || copies[q].j != (de & 1)) q++;
+          const int64_t word = ((int64_t)dst[q] + 2 * ((de & ~1) - copy_start(copies[q]))) / 4;
           if (word > 0xFFFF) return fail(SPS_ERR_UNSUPPORTED, "pre-summed staging window beyond 256 KiB");
           out->offs[key * di_pad + r] = (uint16_t)word;
         }
       }
+  }
+  if (data_bytes >= (1 << 18) || copies_max >= (1 << 14))
+    return fail(SPS_ERR_UNSUPPORTED, "pre-summed stage beyond 256 KiB or 16383 windows");
+  out->copies_max = copies_max;
+  out->data_bytes = data_bytes;
+  out->copies.assign(n_chunk_rows * (size_t)(copies_max + 1), int4{-1, 0, 0, 0});
+  for (size_t q = 0; q < n_chunk_rows; q++) {
+    int4* row = &out->copies[q * (copies_max + 1)];
+    for (size_t k = 0; k < lists[q].size(); k++) row[k] = lists[q][k];
+    row[copies_max] = int4{(int32_t)lists[q].size(), used[q], 0, 0};
   }
   return SPS_OK;
 }

@@ -53,8 +53,10 @@ struct U8PassArgs {
 struct PresumPassArgs {
   const uint16_t* q;       // [n_series][2][q_pitch]: unit-sum series, second copy shifted by one
   int32_t q_pitch;         // samples per series row (N_in rounded up to 16)
-  const int2* slots;       // [tiles][groups][chunks][slots_max + 1]: {series, window start}; last .x = count
-  int32_t slots_max;
+  const int4* copies;      // [tiles][groups][chunks][copies_max + 1]: {row, start,
+                           // (stage byte / 16) | (bytes / 16) << 16, 0}; last {count, total bytes}
+  int32_t copies_max;
+  int32_t data_bytes;      // bytes of series windows per stage (the table follows)
   const uint16_t* offs;    // [tiles][groups][units][di_pad]: staged offsets in 4-byte words
   int32_t di_pad;
   int32_t n_dm;            // delay-table rows
@@ -86,10 +88,10 @@ struct PresumTables {
   std::vector<PresumSeries> series;
   std::vector<PresumUnit> units;
   int32_t max_rel = 0;
-  std::vector<int2> slots;
+  std::vector<int4> copies;
   std::vector<uint16_t> offs;
-  int32_t slots_max = 0;
-  int32_t wb = 0;
+  int32_t copies_max = 0;
+  int32_t data_bytes = 0;
 };
 
 // Step two over uint16 subband series.
@@ -136,17 +138,18 @@ sps_status launch_presum_series(const uint8_t* x, int64_t pitch, int32_t in_len,
                                 int32_t n_series, uint16_t* q, int32_t q_pitch, cudaStream_t st);
 sps_status launch_presum_pass(const PresumPassArgs& a, const sps_dedisp_config& cfg, cudaStream_t st);
 bool presum_config_supported(const sps_dedisp_config& cfg, std::string* why);
-size_t presum_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile, int32_t slots_max);
+size_t presum_smem_bytes(const sps_dedisp_config& cfg, int32_t data_bytes);
 int presum_window_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
 int presum_di_pad(const sps_dedisp_config& cfg);
 int presum_chunk(const sps_dedisp_config& cfg);  // units staged per chunk
-// Host tables (presum_tables.cpp): series count over all rows, most slots of
-// any (tile, group, chunk), and the full tables of one configuration.
+// Host tables (presum_tables.cpp): series count over all rows, the largest
+// packed window data of any (tile, group, chunk), and the full tables of one
+// configuration.
 int64_t count_presum_series(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t K);
-int32_t presum_slots(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t K, int32_t Di,
-                     int32_t units_per_chunk);
+int32_t presum_stage_data(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t K, int32_t Di,
+                          int32_t units_per_chunk, int32_t Tt);
 sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per,
-                               const sps_dedisp_config& cfg, int32_t dmax_tile, PresumTables* out);
+                               const sps_dedisp_config& cfg, PresumTables* out);
 bool u8_config_supported(const sps_dedisp_config& cfg, std::string* why);
 bool step2_config_supported(const sps_dedisp_config& cfg, std::string* why);
 bool snr_config_supported(const sps_snr_config& cfg, std::string* why);
@@ -214,16 +217,17 @@ struct sps_plan {
   sps::PresumUnit* d_presum_units = nullptr;
   int32_t n_presum_units = 0;
   int32_t presum_max_rel = 0;
-  int2* d_presum_slots = nullptr;
+  int4* d_presum_copies = nullptr;
   uint16_t* d_presum_offs = nullptr;
   int32_t n_presum_series = 0;   // of the current configuration's table
-  int32_t presum_slots_max = 0;
+  int32_t presum_copies_max = 0;
+  int32_t presum_data_bytes = 0;
   int32_t q_pitch = 0;           // samples per series row
   int64_t max_presum_series = 0; // over presum 1 and 2 (sizes the workspace)
 
   int max_smem = 0;              // opt-in shared memory per block of the device
   mutable std::map<int64_t, int32_t> spread_cache;     // tile delay spread by (table, rows)
-  mutable std::map<int64_t, int32_t> presum_slot_cache;  // slots by (table, K, rows, units)
+  mutable std::map<int64_t, int32_t> presum_stage_cache;  // stage data by (table, K, rows, units, samples)
 
   sps_kernel_config cfg{};
   // delay spread of one DM tile for the current configuration
