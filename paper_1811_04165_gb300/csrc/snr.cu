@@ -120,14 +120,17 @@ __device__ Moments shfl_down(const Moments& m, int o) {
 }
 
 // (N P - S1) / sqrt(N S2 - S1^2) from exact moments; 0 for a constant series.
+// Both integers are exact; the variance numerator is rounded once to double and
+// the quotient taken as num * rsqrt(var) (FP64, within 2 ulp): a few FP64
+// operations, which matter on this part's narrow FP64 path.
 __device__ double snr_from_moments(int64_t N, const Moments& m) {
   const unsigned __int128 s2 = ((unsigned __int128)m.s2hi << 64) | m.s2lo;
   const unsigned __int128 var_num = (unsigned __int128)N * s2 - (unsigned __int128)m.s1 * m.s1;
   if (var_num == 0) return 0.0;
   const int64_t num = N * (int64_t)m.best - (int64_t)m.s1;
-  const double v = __dadd_rn(__dmul_rn((double)(unsigned long long)(var_num >> 64), 18446744073709551616.0),
-                             (double)(unsigned long long)var_num);
-  return __ddiv_rn((double)num, __dsqrt_rn(v));
+  const double v = fma((double)(unsigned long long)(var_num >> 64), 18446744073709551616.0,
+                       (double)(unsigned long long)var_num);
+  return (double)num * rsqrt(v);
 }
 
 // One pass over widths [w_begin, w_begin + NWP) (ascending).  `flush`: samples a
@@ -210,13 +213,25 @@ __global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_be
     gmax[k] = best;
   }
   __syncthreads();
-  // first position of the maximum: only threads holding it scan their samples again
+  // first position of the maximum: the warp of each thread holding it searches
+  // that thread's samples (u = owner + m * blockDim.x) together, 32 at a time
 #pragma unroll
   for (int k = 0; k < NWP; k++) {
-    if ((int32_t)mx[k] == gmax[k]) {
-      const int N = n_t - W[k] + 1;
-      for (int u = threadIdx.x; u < N; u += blockDim.x)
-        if ((int32_t)(P[u + W[k]] - P[u]) == gmax[k]) { atomicMin(&first[k], u); break; }
+    const int N = n_t - W[k] + 1;
+    unsigned owners = __ballot_sync(0xffffffffu, (int32_t)mx[k] == gmax[k]);
+    while (owners) {
+      const int o = __ffs(owners) - 1;
+      owners &= owners - 1;
+      const int owner = warp * 32 + o;
+      for (int m0 = 0; owner + m0 * (int)blockDim.x < N; m0 += 32) {
+        const int u = owner + (m0 + lane) * (int)blockDim.x;
+        const bool hit = u < N && (int32_t)(P[u + W[k]] - P[u]) == gmax[k];
+        const unsigned h = __ballot_sync(0xffffffffu, hit);
+        if (h) {
+          if (lane == 0) atomicMin(&first[k], owner + (m0 + __ffs(h) - 1) * (int)blockDim.x);
+          break;
+        }
+      }
     }
   }
   __syncthreads();
