@@ -139,7 +139,12 @@ __device__ double snr_from_moments(int64_t N, const Moments& m) {
 // maximum; the first position of the block's maximum is found afterwards by the
 // few threads whose own maximum equals it.
 template <int NWP>
-__global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_begin, int flush, int use_tma) {
+//
+// `narrow`: the host has shown that a warp's S2 total fits 64 bits (32 threads'
+// samples times the largest square), so warps reduce S1 and S2 as 64-bit sums
+// and the maximum with one redux; otherwise the full 128-bit merge runs.
+__global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_begin, int flush, int use_tma,
+                                                             int narrow) {
   extern __shared__ __align__(16) uint32_t buf[];
   __shared__ uint32_t scratch[32];
   __shared__ uint64_t bar;
@@ -198,12 +203,26 @@ __global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_be
     if (++count == flush) { flush_partials(); count = 0; }
   }
   flush_partials();
+  if (narrow) {
 #pragma unroll
-  for (int k = 0; k < NWP; k++) {
-    Moments m{s1t[k], s2lo[k], s2hi[k], (int32_t)mx[k], 0};
+    for (int k = 0; k < NWP; k++) {
+      unsigned long long s1 = s1t[k], s2 = s2lo[k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) merge(m, shfl_down(m, o));
-    if (lane == 0) part[warp][k] = m;
+      for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      }
+      const uint32_t m = __reduce_max_sync(0xffffffffu, mx[k]);
+      if (lane == 0) part[warp][k] = Moments{s1, s2, 0ull, (int32_t)m, 0};
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NWP; k++) {
+      Moments m{s1t[k], s2lo[k], s2hi[k], (int32_t)mx[k], 0};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) merge(m, shfl_down(m, o));
+      if (lane == 0) part[warp][k] = m;
+    }
   }
   __syncthreads();
   if (threadIdx.x < NWP) {
@@ -335,7 +354,7 @@ bool snr_config_supported(const sps_snr_config& c, std::string* why) {
   return true;
 }
 
-typedef void (*SnrKernel)(SnrArgs, int, int, int);
+typedef void (*SnrKernel)(SnrArgs, int, int, int, int);
 
 SnrKernel snr_variant(int nwp) {
   switch (nwp) {
@@ -359,11 +378,15 @@ sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st
   const unsigned long long f1 = 0xFFFFFFFFull / bmax;
   const unsigned long long f2 = 0xFFFFFFFFFFFFFFFFull / (bmax * bmax);
   const int flush = (int)std::max<unsigned long long>(1ull, std::min<unsigned long long>({f1, f2, 1ull << 30}));
+  // a warp's S2: 32 threads x ceil(n_t / threads) samples x bmax^2, in 64 bits?
+  const unsigned long long per_thread = (unsigned long long)((a.n_t + c.threads - 1) / c.threads);
+  const long double warp_s2 = 32.0L * (long double)per_thread * (long double)bmax * (long double)bmax;
+  const int narrow = warp_s2 < 1.8e19L ? 1 : 0;
   const size_t smem = prefix_smem(a.n_t);
   for (int w0 = 0; w0 < a.n_widths; w0 += kWidthsPerPass) {
     SnrKernel fn = snr_variant(std::min(kWidthsPerPass, a.n_widths - w0));
     SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    fn<<<a.n_dms, c.threads, smem, st>>>(a, w0, flush, tma_ok(a.D, a.n_t) ? 1 : 0);
+    fn<<<a.n_dms, c.threads, smem, st>>>(a, w0, flush, tma_ok(a.D, a.n_t) ? 1 : 0, narrow);
     SPS_CUDA(cudaGetLastError());
   }
   return SPS_OK;
