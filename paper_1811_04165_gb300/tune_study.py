@@ -1,0 +1,176 @@
+"""Auto-tuning study on the GPU (Sec. 4 and Sec. 5; the analogue of Figs. 3-5).
+
+    python -m paper_1811_04165_gb300.tune_study [--seeds 50] [--budget 500] [--beam-evals 200] [--out FILE]
+
+1. The tiny 64-channel search in two-step subband mode, reduced joint space of
+   5000 points (step one warps_dm x chunk, step two dms_per_thread x warps_dm x
+   chunk, S/N threads): every point is timed live (exhaustive search), giving
+   the exact optimum and a fitness table.
+2. On that table, the library's GA (population 32, tournament pools of 20 %,
+   uniform crossover p_cross 0.8, mutation 0.1) and pure random search run with
+   equal budgets of distinct evaluations over many seeds: best-of-run relative
+   to the optimum, the share of runs within 5 %, and the coefficient of
+   variation of the best fitness over runs (Sec. 5 reports it for repeated GA
+   runs).
+3. Sweeps of p_mut, p_cross, population, crossover kind and budget on the same
+   table (Fig. 3), and a histogram of the GA's best over seeds (Fig. 5).
+4. One live GA run on the tiny plan, and one on the 1536-channel Apertif beam's
+   full brute-force gene space (7 genes), against the library's default
+   configuration.
+
+Everything runs through the C ABI (`sps_tune`, `sps_optimize`); fitness is the
+median over three trials of the mean time of back-to-back searches.
+"""
+import argparse
+import json
+import statistics
+import sys
+import time
+
+import numpy as np
+
+from . import (CROSS_ONE_POINT, CROSS_UNIFORM, SPACE_FULL, SPACE_REDUCED, TUNE_EXHAUSTIVE, TUNE_GA, TUNE_RANDOM,
+               Plan, search_desc, sps_optimize, sps_tune, sps_tune_config, sps_tune_space, synth)
+
+
+def tiny_subband():
+    """The tiny search (64 ch, 4096 samples, 32 DMs 0..62) in subband mode: 8
+    subbands, 4 coarse DMs (0, 16, 32, 48)."""
+    wl = synth.tiny_brute()
+    wl.n_subbands = 8
+    wl.coarse_dms = wl.dms[::8].copy()
+    wl.name = "tiny-64ch-4096s-32dm-subband8"
+    return wl
+
+
+def _input(plan, wl):
+    import torch
+    x = synth.filterbank(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, plan.input_samples, wl.seed, wl.pulses,
+                         pitch=plan.pitch)
+    return torch.from_numpy(x).cuda()
+
+
+def _runs(nv, ko, table, algorithm, seeds, budget, **kw):
+    best = []
+    for s in seeds:
+        _, res, _ = sps_optimize(nv, ko, table.__getitem__, None,
+                                 search_desc(algorithm=algorithm, max_evaluations=budget, seed=s, **kw))
+        best.append(res.best_fitness)
+    return best
+
+
+def _summary(best, opt):
+    r = [b / opt for b in best]
+    mean = statistics.fmean(best)
+    return {"runs": len(r), "mean_ratio": statistics.fmean(r), "median_ratio": statistics.median(r),
+            "worst_ratio": max(r), "within_5pct": sum(x <= 1.05 for x in r) / len(r),
+            "cv": statistics.pstdev(best) / mean if mean > 0 else 0.0}
+
+
+def study_table(seeds, budget, reps):
+    import torch
+    wl = tiny_subband()
+    plan = Plan.from_workload(wl)
+    x = _input(plan, wl)
+    nv, ko, _ = sps_tune_space(plan, SPACE_REDUCED)
+    t0 = time.perf_counter()
+    _, res, trace = sps_tune(plan, x, which=SPACE_REDUCED, desc=search_desc(algorithm=TUNE_EXHAUSTIVE), reps=reps)
+    torch.cuda.synchronize()
+    t_exh = time.perf_counter() - t0
+    table = {pt: f for pt, f in trace}
+    finite = [f for f in table.values() if np.isfinite(f)]
+    opt = min(finite)
+    out = {"workload": wl.name, "space": "reduced", "points": int(np.prod(nv)), "valid": len(finite),
+           "exhaustive_s": t_exh, "optimum_ms": opt, "median_ms": statistics.median(finite),
+           "worst_ms": max(finite), "budget": budget}
+    seeds = list(seeds)
+    ga = _runs(nv, ko, table, TUNE_GA, seeds, budget)
+    rnd = _runs(nv, ko, table, TUNE_RANDOM, seeds, budget)
+    out["ga"] = _summary(ga, opt)
+    out["random"] = _summary(rnd, opt)
+    # Fig. 5 analogue: histogram of the GA's best relative to the optimum
+    edges = [1.0, 1.01, 1.02, 1.05, 1.1, 1.2, 1.5, float("inf")]
+    h = np.histogram([b / opt for b in ga], bins=edges)[0]
+    out["ga_histogram"] = {f"[{edges[i]:.2f},{edges[i + 1]:.2f})": int(h[i]) for i in range(len(h))}
+    # Fig. 3 analogue: sweeps on the same table, 20 seeds each
+    sw = seeds[:20]
+    sweeps = {}
+    for p in (0.05, 0.1, 0.2, 0.4):
+        sweeps[f"p_mut={p}"] = _summary(_runs(nv, ko, table, TUNE_GA, sw, budget, p_mut=p), opt)["mean_ratio"]
+    for p in (0.5, 0.8, 1.0):
+        sweeps[f"p_cross={p}"] = _summary(_runs(nv, ko, table, TUNE_GA, sw, budget, p_cross=p), opt)["mean_ratio"]
+    for n in (16, 32, 64):
+        sweeps[f"population={n}"] = _summary(_runs(nv, ko, table, TUNE_GA, sw, budget, population=n),
+                                             opt)["mean_ratio"]
+    for name, c in (("uniform", CROSS_UNIFORM), ("one_point", CROSS_ONE_POINT)):
+        sweeps[f"crossover={name}"] = _summary(_runs(nv, ko, table, TUNE_GA, sw, budget, crossover=c),
+                                               opt)["mean_ratio"]
+    for b in (100, 250, 500, 1000):
+        sweeps[f"budget={b}/ga"] = _summary(_runs(nv, ko, table, TUNE_GA, sw, b), opt)["mean_ratio"]
+        sweeps[f"budget={b}/random"] = _summary(_runs(nv, ko, table, TUNE_RANDOM, sw, b), opt)["mean_ratio"]
+    out["sweeps_mean_ratio"] = sweeps
+    # one live GA run with the same budget: its configuration's table time vs the optimum
+    best, res, tr = sps_tune(plan, x, which=SPACE_REDUCED,
+                             desc=search_desc(algorithm=TUNE_GA, max_evaluations=budget, seed=seeds[0]), reps=reps)
+    out["live_ga"] = {"evaluations": res.evaluations, "best_ms_live": res.best_fitness,
+                      "best_ms_in_table": table[tuple(best)], "ratio_in_table": table[tuple(best)] / opt}
+    return out
+
+
+def study_beam(evals, reps, seed):
+    import torch
+    wl = synth.apertif_beam()
+    plan = Plan.from_workload(wl)
+    x = _input(plan, wl)
+    default = plan.config
+    out_buf = plan.alloc_outputs()
+    ws = plan.workspace()
+
+    def time_cfg(n=20):
+        for _ in range(3):
+            plan.search(x, out=out_buf, workspace=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            plan.search(x, out=out_buf, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    t_default = time_cfg()
+    nv, ko, _ = sps_tune_space(plan, SPACE_FULL)
+    t0 = time.perf_counter()
+    best, res, trace = sps_tune(plan, x, which=SPACE_FULL, out=out_buf, workspace=ws,
+                                desc=search_desc(algorithm=TUNE_GA, max_evaluations=evals, seed=seed), reps=reps)
+    t_ga = time.perf_counter() - t0
+    cfg = sps_tune_config(plan, SPACE_FULL, best)
+    t_best = time_cfg()
+    plan.config = default
+    return {"workload": wl.name, "space": "full brute-force (7 genes)", "points": int(np.prod(nv)),
+            "evaluations": res.evaluations, "finite": int(sum(bool(np.isfinite(f)) for _, f in trace)), "ga_s": t_ga,
+            "default_config": default.as_dict(), "default_ms": t_default, "ga_config": cfg.as_dict(),
+            "ga_ms": t_best, "speedup": t_default / t_best}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--seeds", type=int, default=50)
+    ap.add_argument("--budget", type=int, default=500, help="distinct evaluations per search (10 % of 5000)")
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--beam-evals", type=int, default=200, help="0 skips the live run on the beam")
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    res = {"tiny_subband": study_table(range(a.seeds), a.budget, a.reps)}
+    if a.beam_evals:
+        res["apertif_beam"] = study_beam(a.beam_evals, a.reps, seed=1)
+    text = json.dumps(res, indent=1, default=lambda v: v.item() if hasattr(v, "item") else str(v))
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(text + "\n")
+    print(text)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

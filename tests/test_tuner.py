@@ -182,3 +182,20 @@ def test_library_optimize_penalties_and_errors(lib):
         lib.sps_optimize([4, 4], [0, 1], fit, None, lib.search_desc(population=7))
     with pytest.raises(lib.SpsError):
         lib.sps_optimize([2], [0], lambda p: math.inf, None, lib.search_desc(algorithm=lib.TUNE_EXHAUSTIVE))
+
+
+def test_tune_study_helpers_on_a_synthetic_table(lib):
+    """The study's GA / random runs and summaries on a known table (host only)."""
+    from paper_1811_04165_gb300 import tune_study
+    nv, ko = [5, 4, 5, 5, 3], [0, 0, 1, 1, 2]
+    rng = np.random.Generator(np.random.PCG64(5))
+    table = {pt: float(1.0 + rng.random()) for pt in np.ndindex(*nv)}
+    opt = min(table.values())
+    ga = tune_study._runs(nv, ko, table, lib.TUNE_GA, range(6), 100)
+    rnd = tune_study._runs(nv, ko, table, lib.TUNE_RANDOM, range(6), 100)
+    assert len(ga) == len(rnd) == 6 and min(ga) >= opt and min(rnd) >= opt
+    s = tune_study._summary(ga, opt)
+    assert s["runs"] == 6 and 1.0 <= s["median_ratio"] <= s["worst_ratio"] and 0.0 <= s["within_5pct"] <= 1.0
+    # exhaustive with the whole space as budget finds the optimum
+    ex = tune_study._runs(nv, ko, table, lib.TUNE_EXHAUSTIVE, [0], 10 ** 6)
+    assert ex == [opt]
