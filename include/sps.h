@@ -301,6 +301,41 @@ sps_status sps_tune(sps_plan* plan, int32_t which, const sps_search_desc* desc, 
                     int32_t* peak_t, int32_t* peak_val, int32_t reps, double limit_ms, sps_trace_fn trace,
                     void* user, int32_t* best_point, sps_search_result* result, void* stream);
 
+/* ------------------------------------------------------- batched beams */
+
+/* Batched beams.  A fixed set of beams (one plan each, in any mix of shapes
+ * and configurations) searched by ONE launch: sps_batch_create captures every
+ * beam's sps_search into a CUDA graph whose beams run on `branches`
+ * concurrent branches (beams spread over the branches by work, largest
+ * first); sps_batch_launch replays the graph on a stream.  The ALERT setting
+ * searches hundreds of beams at once (Sec. 1: beams spread over a GPU
+ * cluster); the paper has no batched entry point, this is a library one.
+ * buffers[b]: the device buffers of beam b as for sps_search (x with its
+ * pitch, D, snr, peak_t, peak_val; best may be NULL); they stay owned by the
+ * caller and must outlive the batch.  workspace: device, >=
+ * sps_batch_workspace_bytes for the same plans and branch count, 256-byte
+ * aligned; each branch uses its own region, so beams on different branches run
+ * concurrently.  The graph holds the plans' current configurations:
+ * sps_batch_launch returns INVALID_ARG, launching nothing, once a plan has been
+ * reconfigured since the capture; plans must outlive the batch.  Launches of
+ * one batch on different streams must not overlap (they share the workspace). */
+typedef struct sps_batch sps_batch;
+typedef struct {
+  const uint8_t* x;
+  int64_t x_pitch;
+  int32_t* D;
+  double* snr;
+  int32_t* peak_t;
+  int32_t* peak_val;
+  int32_t* best;
+} sps_beam_buffers;
+sps_status sps_batch_workspace_bytes(const sps_plan* const* plans, int32_t n_beams, int32_t branches,
+                                     size_t* bytes);
+sps_status sps_batch_create(const sps_plan* const* plans, const sps_beam_buffers* buffers, int32_t n_beams,
+                            int32_t branches, void* workspace, size_t workspace_bytes, sps_batch** out);
+sps_status sps_batch_launch(sps_batch* batch, void* stream);
+sps_status sps_batch_destroy(sps_batch* batch);
+
 /* ---------------------------------------------------------------- misc */
 
 /* Reads (synchronously) the plan's device status word, which kernels set when

@@ -344,6 +344,66 @@ class Plan:
         return out
 
 
+class BeamBuffers(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("x_pitch", ctypes.c_int64), ("D", ctypes.c_void_p), ("snr", ctypes.c_void_p),
+                ("peak_t", ctypes.c_void_p), ("peak_val", ctypes.c_void_p), ("best", ctypes.c_void_p)]
+
+
+def batch_workspace_bytes(plans, branches=8) -> int:
+    """Workspace one Batch of these plans needs (`sps_batch_workspace_bytes`)."""
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+    nbytes = ctypes.c_size_t()
+    check(_L.sps_batch_workspace_bytes(arr, len(plans), int(branches), ctypes.byref(nbytes)),
+          "sps_batch_workspace_bytes")
+    return int(nbytes.value)
+
+
+class Batch:
+    """A fixed set of beams searched by one CUDA-graph launch (`sps_batch_*`).
+
+    plans: one Plan per beam; xs: each beam's device filterbank (uint8
+    [channels][pitch]); outs: each beam's outputs as from Plan.alloc_outputs
+    (allocated here when None).  The batch keeps references to everything the
+    graph points at, so the buffers live as long as it does."""
+
+    def __init__(self, plans, xs, outs=None, branches=8):
+        t = _torch()
+        if len(plans) != len(xs):
+            raise ValueError("one input per plan")
+        self.plans = list(plans)
+        self.xs = list(xs)
+        self.outs = list(outs) if outs is not None else [p.alloc_outputs() for p in self.plans]
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
+        self._arr = arr
+        self.workspace = t.empty(max(batch_workspace_bytes(self.plans, branches), 256), dtype=t.uint8, device="cuda")
+        bufs = (BeamBuffers * len(self.plans))()
+        for b, (p, x, o) in enumerate(zip(self.plans, self.xs, self.outs)):
+            shp = (p.n_widths, p.n_dms)
+            bufs[b] = BeamBuffers(_dev(x, t.uint8, "x").value, int(x.shape[1]),
+                                  _dev(o["D"], t.int32, "D", (p.n_dms, p.n_samples)).value,
+                                  _dev(o["snr"], t.float64, "snr", shp).value,
+                                  _dev(o["peak_t"], t.int32, "peak_t", shp).value,
+                                  _dev(o["peak_val"], t.int32, "peak_val", shp).value,
+                                  _dev(o["best"], t.int32, "best", (4,)).value)
+        self._bufs = bufs
+        h = ctypes.c_void_p()
+        check(_L.sps_batch_create(arr, bufs, len(self.plans), int(branches), self.workspace.data_ptr(),
+                                  ctypes.c_size_t(self.workspace.numel()), ctypes.byref(h)), "sps_batch_create")
+        self.handle = h.value
+
+    def launch(self, stream=None):
+        check(_L.sps_batch_launch(self.handle, _stream(stream)), "sps_batch_launch")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                _L.sps_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
 def upload_filterbank(x_np: np.ndarray, pitch: int | None = None):
     """Copy a host uint8 [channels, samples] array into a pitched device tensor."""
     import torch

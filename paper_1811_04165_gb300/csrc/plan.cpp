@@ -282,6 +282,7 @@ sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg) {
     p->step2_tiles_host = tiles;
   }
   p->cfg = cfg;
+  p->config_gen++;
   p->dmax_brute = dmax_b;
   p->dmax_step1 = dmax_1;
   p->dmax_step2 = dmax_2;

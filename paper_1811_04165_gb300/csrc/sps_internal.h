@@ -230,6 +230,7 @@ struct sps_plan {
   mutable std::map<int64_t, int32_t> presum_stage_cache;  // stage data by (table, K, rows, units, samples)
 
   sps_kernel_config cfg{};
+  uint64_t config_gen = 0;       // bumped whenever the device tables are rebuilt
   // delay spread of one DM tile for the current configuration
   int32_t dmax_brute = 0, dmax_step1 = 0, dmax_step2 = 0;
 

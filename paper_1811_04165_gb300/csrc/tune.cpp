@@ -425,6 +425,7 @@ sps_status sps_tune(sps_plan* p, int32_t which, const sps_search_desc* desc, con
     return fail(SPS_ERR_CUDA, "cudaEventCreate");
   }
   sps_status hard = SPS_OK;  // an error that is not the configuration's fault stops the search
+  std::string hard_msg;
   Problem pr;
   for (size_t g = 0; g < genes.size(); g++) {
     pr.n_values.push_back((int32_t)genes[g].values.size());
@@ -433,24 +434,31 @@ sps_status sps_tune(sps_plan* p, int32_t which, const sps_search_desc* desc, con
   }
   pr.valid = [&](const Point& pt) { return check_config(p, point_config(p, genes, pt.data()), nullptr) == SPS_OK; };
   // fitness: median over three trials of the mean time of `reps` back-to-back searches
+  // A configuration the plan rejects, or whose workspace exceeds the one given,
+  // scores +inf; a CUDA error stops the search.
+  auto search_once = [&]() -> bool {
+    const sps_status r = run_search(p, x, x_pitch, D, workspace, workspace_bytes, snr, peak_t, peak_val, nullptr, st);
+    if (r == SPS_ERR_CUDA) {
+      hard = r;
+      hard_msg = sps_last_error();
+    }
+    return r == SPS_OK;
+  };
   pr.fitness = [&](const Point& pt) -> double {
     if (hard) return kInf;
     if (apply_config(p, point_config(p, genes, pt.data())) != SPS_OK) return kInf;
-    if (run_search(p, x, x_pitch, D, workspace, workspace_bytes, snr, peak_t, peak_val, nullptr, st) != SPS_OK) {
-      hard = SPS_ERR_CUDA;
-      return kInf;
-    }
+    if (plan_workspace_bytes(p) > workspace_bytes) return kInf;
+    if (!search_once()) return kInf;
     double trial[3];
     for (int t = 0; t < 3; t++) {
       cudaEventRecord(e0, st);
       for (int r = 0; r < reps; r++)
-        if (run_search(p, x, x_pitch, D, workspace, workspace_bytes, snr, peak_t, peak_val, nullptr, st) != SPS_OK) {
-          hard = SPS_ERR_CUDA;
-          return kInf;
-        }
+        if (!search_once()) return kInf;
       cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) {
+      const cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
         hard = SPS_ERR_CUDA;
+        hard_msg = cudaGetErrorString(e);
         return kInf;
       }
       float ms = 0.f;
@@ -464,7 +472,7 @@ sps_status sps_tune(sps_plan* p, int32_t which, const sps_search_desc* desc, con
   sps_status s = run_problem(pr, desc, best_point, result);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (s == SPS_OK && hard) s = fail(hard, "a launch failed during tuning");
+  if (s == SPS_OK && hard) s = fail(hard, "a launch failed during tuning: " + hard_msg);
   // leave the plan on the best configuration found (or where it was)
   if (s == SPS_OK && std::isfinite(result->best_fitness)) {
     s = apply_config(p, point_config(p, genes, best_point));

@@ -130,3 +130,31 @@ def apertif_beam(seed: int = 2, subband: bool = False) -> Workload:
         wl.n_subbands = 32
         wl.coarse_dms = dms[::32].copy()
     return wl
+
+
+def batch_beams(n_beams: int = 40, seed: int = 4, n_t: int = 12500, channels=(1536, 384),
+                dm_trials=(512, 4096), dm_steps=(0.1, 0.5), max_widths: int = 7) -> list:
+    """Beams for one batch: alternately ``channels[0]`` and ``channels[1]``
+    channels over 1250-1550 MHz, 81.92 us, ``n_t`` samples; per beam a DM count
+    uniform in ``dm_trials`` (a multiple of 32), a step uniform in ``dm_steps``
+    (0.01 resolution), the first 1..``max_widths`` widths of 1, 2, 4, ..., 64,
+    and two pulses (DM within the beam's range, width 2^U{0..5}, S/N U(8, 20))."""
+    rng = np.random.Generator(np.random.PCG64(seed + 104729))
+    out = []
+    for b in range(n_beams):
+        ch = int(channels[b % len(channels)])
+        n_dm = int(rng.integers(dm_trials[0] // 32, dm_trials[1] // 32 + 1)) * 32
+        step = round(float(rng.uniform(*dm_steps)), 2)
+        k = int(rng.integers(1, max_widths + 1))
+        widths = np.array([2 ** i for i in range(k)], np.int32)
+        dms = dm_grid(n_dm, step)
+        pulses = []
+        for _ in range(2):
+            dm = float(rng.uniform(0.05, 0.9) * dms[-1])
+            w = float(2 ** int(rng.integers(0, 6)))
+            snr = float(rng.uniform(8.0, 20.0))
+            t0 = float(np.floor(rng.uniform(0.0, n_t - 64.0)))
+            pulses.append(Pulse(dm, w, pulse_amplitude(snr, ch, w), t0))
+        out.append(Workload(f"beam{b}-{ch}ch-{n_t}s-{n_dm}dm-step{step}", ch, 1250.0, 1550.0, 81.92e-6, n_t, dms,
+                            widths, seed=seed * 1000 + b, pulses=pulses))
+    return out

@@ -1,0 +1,94 @@
+"""Batched beams through the C ABI (`sps_batch_*`): one CUDA-graph launch must
+give every beam exactly what its own sps_search gives, launch after launch,
+with beams of different shapes and kernel configurations on concurrent
+branches; the oracle checks one beam outright."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_04165_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _beams():
+    return synth.batch_beams(6, seed=9, n_t=2000, channels=(96, 48), dm_trials=(64, 256), dm_steps=(0.5, 2.0),
+                             max_widths=4)
+
+
+def _setup(lib, wls):
+    import torch
+    plans = [lib.Plan.from_workload(wl) for wl in wls]
+    xs = []
+    for p, wl in zip(plans, wls):
+        x = synth.filterbank(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, p.input_samples, wl.seed, wl.pulses,
+                             pitch=p.pitch)
+        xs.append(torch.from_numpy(x).cuda())
+    return plans, xs
+
+
+def _alone(plans, xs):
+    import torch
+    ref = []
+    for p, x in zip(plans, xs):
+        o = p.search(x)
+        torch.cuda.synchronize()
+        ref.append({k: v.clone() for k, v in o.items()})
+    return ref
+
+
+@pytest.mark.parametrize("branches", [1, 3, 8])
+def test_batch_matches_each_beam_alone(lib, branches):
+    import torch
+    wls = _beams()
+    plans, xs = _setup(lib, wls)
+    c = plans[1].config  # one beam on the single-channel kernel, the rest on their defaults
+    c.brute.presum = 0
+    plans[1].config = c
+    ref = _alone(plans, xs)
+    batch = lib.Batch(plans, xs, branches=branches)
+    for _ in range(2):  # a replay finds the previous launch's contents everywhere
+        for o in batch.outs:
+            o["D"].fill_(-1)
+            o["snr"].fill_(-1.0)
+        batch.launch()
+        torch.cuda.synchronize()
+        for b, (o, r) in enumerate(zip(batch.outs, ref)):
+            for k in ("D", "peak_t", "peak_val", "best"):
+                assert torch.equal(o[k], r[k]), (b, k)
+            assert torch.equal(o["snr"], r["snr"]), b  # same kernels, same arithmetic
+    for p in plans:
+        assert p.status() == 0
+
+
+def test_batch_beam_against_the_oracle(lib):
+    import torch
+    wls = _beams()
+    plans, xs = _setup(lib, wls)
+    batch = lib.Batch(plans, xs, branches=2)
+    batch.launch()
+    torch.cuda.synchronize()
+    b = 2
+    wl, x = wls[b], xs[b].cpu().numpy()
+    D = batch.outs[b]["D"].cpu().numpy()
+    want = oracle.dedisperse(x, oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms), wl.n_t)
+    assert np.array_equal(D, want)
+    s, pt, pv = oracle.snr(want, wl.widths)
+    got = batch.outs[b]["snr"].cpu().numpy()
+    assert np.allclose(got, s, rtol=1e-5, atol=1e-9)
+    assert np.array_equal(batch.outs[b]["peak_t"].cpu().numpy(), pt)
+    assert np.array_equal(batch.outs[b]["peak_val"].cpu().numpy(), pv)
+    oi, ow = oracle.detect(s)
+    assert batch.outs[b]["best"].cpu().numpy()[:2].tolist() == [oi, ow]
+
+
+def test_batch_refuses_a_reconfigured_plan(lib):
+    wls = _beams()[:2]
+    plans, xs = _setup(lib, wls)
+    batch = lib.Batch(plans, xs, branches=2)
+    c = plans[0].config
+    c.snr.threads = 128 if c.snr.threads != 128 else 256
+    plans[0].config = c
+    with pytest.raises(lib.SpsError) as e:
+        batch.launch()
+    assert e.value.status == 1 and "reconfigured" in str(e.value)
