@@ -336,6 +336,50 @@ sps_status sps_batch_create(const sps_plan* const* plans, const sps_beam_buffers
 sps_status sps_batch_launch(sps_batch* batch, void* stream);
 sps_status sps_batch_destroy(sps_batch* batch);
 
+/* ------------------------------------------------------- real-time serving */
+
+/* A server for beams that stream consecutive batches in real time (Sec. 1:
+ * ALERT searches every beam's 1.024 s of data within 1.024 s).  Not in the
+ * paper; a library runtime.  Single-threaded: one host thread calls every
+ * entry point of a server.
+ *   - Admission: a beam is admitted when its device footprint (two input
+ *     buffers, D, the S/N tables, and, if it needs a larger one, its share of
+ *     the workspace slots) fits `hbm_budget_bytes`; otherwise UNSUPPORTED.
+ *   - Overlap tails: each beam keeps its input device-resident in two buffers
+ *     used alternately; a batch's buffer starts with the previous batch's last
+ *     N_in - N_t samples (zeros before the first batch), so every batch is
+ *     searched over N_t new samples plus the delay tail.
+ *   - sps_server_submit and sps_server_poll dispatch queued batches in
+ *     arrival order onto `max_inflight` concurrent slots (stream + workspace),
+ *     a beam's batches one at a time and in order; each runs the tail copy, the
+ *     host-to-device copy of the new samples, sps_search and the copies of the
+ *     S/N table and best back to the host pointers given at submission, which
+ *     must stay valid until the batch is reported complete.
+ *   - Times are seconds on the host's steady clock; a completion time is the
+ *     GPU-timeline end of the batch's last copy, mapped to that clock. */
+typedef struct sps_server sps_server;
+typedef struct {
+  size_t hbm_budget_bytes;  /* device bytes the server may allocate            */
+  int32_t max_inflight;     /* concurrent batches (1 = one batch at a time)    */
+} sps_server_desc;
+sps_status sps_server_create(const sps_server_desc* desc, sps_server** out);
+/* Admits a beam searched with `plan` (which must outlive the server and keep
+ * its configuration); beam ids count from 0. */
+sps_status sps_server_add_beam(sps_server* server, const sps_plan* plan, int32_t* beam_id);
+/* Queues one batch of a beam: host uint8 [channels][host_pitch], N_t new
+ * samples per channel (pinned memory keeps the copy asynchronous).  snr_host:
+ * double [n_widths][n_dms]; best_host: int32[4] (either may be NULL). */
+sps_status sps_server_submit(sps_server* server, int32_t beam_id, const uint8_t* host_x, int64_t host_pitch,
+                             double* snr_host, int32_t* best_host, uint64_t tag);
+/* Dispatches what it can, then reports up to `max` completed batches (tags
+ * and completion times) in completion-check order; *n = how many. */
+sps_status sps_server_poll(sps_server* server, uint64_t* tags, double* done_s, int32_t max, int32_t* n);
+/* Batches queued or in flight. */
+sps_status sps_server_pending(const sps_server* server, int32_t* n);
+/* The host steady clock in seconds (the clock of submission and completion times). */
+double sps_server_clock(void);
+sps_status sps_server_destroy(sps_server* server);
+
 /* ---------------------------------------------------------------- misc */
 
 /* Reads (synchronously) the plan's device status word, which kernels set when

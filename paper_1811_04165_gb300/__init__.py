@@ -404,6 +404,68 @@ class Batch:
             self.handle = None
 
 
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32)]
+
+
+class Server:
+    """Real-time serving of streaming beams (`sps_server_*`).  Host buffers
+    handed to submit() must stay alive until poll() reports their tag."""
+
+    def __init__(self, hbm_budget_bytes, max_inflight=4):
+        h = ctypes.c_void_p()
+        check(_L.sps_server_create(ctypes.byref(ServerDesc(int(hbm_budget_bytes), int(max_inflight))),
+                                   ctypes.byref(h)), "sps_server_create")
+        self.handle = h.value
+        self.plans = []
+        self._keep = {}
+
+    def add_beam(self, plan) -> int:
+        b = ctypes.c_int32()
+        check(_L.sps_server_add_beam(self.handle, plan.handle, ctypes.byref(b)), "sps_server_add_beam")
+        self.plans.append(plan)
+        return b.value
+
+    def submit(self, beam, x_host, snr_host=None, best_host=None, tag=0):
+        """x_host: uint8 array [channels][pitch >= N_t] (pinned torch tensor or numpy)."""
+        def ptr(a):
+            if a is None:
+                return None
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        pitch = int(x_host.shape[1])
+        self._keep[int(tag)] = (x_host, snr_host, best_host)
+        check(_L.sps_server_submit(self.handle, int(beam), ptr(x_host), pitch, ptr(snr_host), ptr(best_host),
+                                   ctypes.c_uint64(int(tag))), "sps_server_submit")
+
+    def poll(self, max_n=256):
+        tags = (ctypes.c_uint64 * max_n)()
+        done = (ctypes.c_double * max_n)()
+        n = ctypes.c_int32()
+        check(_L.sps_server_poll(self.handle, tags, done, int(max_n), ctypes.byref(n)), "sps_server_poll")
+        out = [(int(tags[i]), float(done[i])) for i in range(n.value)]
+        for t, _ in out:
+            self._keep.pop(t, None)
+        return out
+
+    def pending(self) -> int:
+        n = ctypes.c_int32()
+        check(_L.sps_server_pending(self.handle, ctypes.byref(n)), "sps_server_pending")
+        return n.value
+
+    @staticmethod
+    def clock() -> float:
+        return float(_L.sps_server_clock())
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                _L.sps_server_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
 def upload_filterbank(x_np: np.ndarray, pitch: int | None = None):
     """Copy a host uint8 [channels, samples] array into a pitched device tensor."""
     import torch

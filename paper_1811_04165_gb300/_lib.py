@@ -37,6 +37,13 @@ SIGNATURES = {
     "sps_batch_create": (_I32, [_P, _P, _I32, _I32, _P, _SZ, _P]),
     "sps_batch_launch": (_I32, [_P, _P]),
     "sps_batch_destroy": (_I32, [_P]),
+    "sps_server_create": (_I32, [_P, _P]),
+    "sps_server_add_beam": (_I32, [_P, _P, _P]),
+    "sps_server_submit": (_I32, [_P, _I32, _P, _I64, _P, _P, ctypes.c_uint64]),
+    "sps_server_poll": (_I32, [_P, _P, _P, _I32, _P]),
+    "sps_server_pending": (_I32, [_P, _P]),
+    "sps_server_clock": (ctypes.c_double, []),
+    "sps_server_destroy": (_I32, [_P]),
     "sps_optimize": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "sps_tune_space": (_I32, [_P, _I32, _I32, _P, _P, _P, _P]),
     "sps_tune_config": (_I32, [_P, _I32, _P, _P]),
