@@ -18,6 +18,10 @@ Sclocco, AMBER auto-tuning with genetic algorithms):
   boxcar             Sec. 2 "downsampling (smoothing)", as a sliding boxcar
   snr                Sec. 2 S/N step; (peak - mean) / population sigma
   detect             argmax over (DM, width) of the S/N table
+  zap_channels       Sec. 3, footnote: channels zapped for terrestrial RFI
+  decimate           Table 2 DOWNSAMPLING / NRSAMPLES: decimating downsampling
+  snr_decimated      Sec. 2 S/N, Sec. 5: on every downsampled series (factor 1 =
+                     the series itself)
 
 Parity pins for every function are in tests/test_oracle_pins.py.
 """
@@ -207,6 +211,43 @@ def detect(snr_table: np.ndarray) -> tuple[int, int]:
     bi, bw = ctypes.c_int32(), ctypes.c_int32()
     lib.oracle_detect(_ptr(s), n_dms, n_w, ctypes.byref(bi), ctypes.byref(bw))
     return bi.value, bw.value
+
+
+def zap_channels(x: np.ndarray, zap) -> np.ndarray:
+    """x with every zapped channel's row set to 0 (zap: one flag per channel,
+    non-zero = zapped): such channels add nothing to any sum."""
+    out = np.array(x, copy=True)
+    out[np.asarray(zap).astype(bool)] = 0
+    return out
+
+
+def decimate(D: np.ndarray, f: int) -> np.ndarray:
+    """Downsampling by factor f: X[i][j] = sum_{u<f} D[i][j * f + u] for
+    j < n_t // f (the trailing n_t mod f samples form no sample), int64."""
+    D = np.asarray(D)
+    if not 1 <= f <= D.shape[1]:
+        raise ValueError("factor out of range")
+    n = D.shape[1] // f
+    return D[:, :n * f].astype(np.int64).reshape(D.shape[0], n, f).sum(axis=2)
+
+
+def snr_decimated(D: np.ndarray, factors) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """S/N of every downsampled series, laid out [n_factors, n_dms]: for factor
+    f, (max X - mean X) / population sigma over the n_t // f samples of
+    X = decimate(D, f); peak_t = f * (first j with X[j] = max), in input
+    samples; peak_val = max X."""
+    D = np.asarray(D)
+    factors = [int(f) for f in factors]
+    s = np.empty((len(factors), D.shape[0]), np.float64)
+    pt = np.empty((len(factors), D.shape[0]), np.int32)
+    pv = np.empty((len(factors), D.shape[0]), np.int32)
+    for k, f in enumerate(factors):
+        X = decimate(D, f)
+        if X.size and (X.max() > np.iinfo(np.int32).max or X.min() < 0):
+            raise ValueError("downsampled sums outside [0, 2^31)")
+        sk, ptk, pvk = snr(X.astype(np.int32), [1])
+        s[k], pt[k], pv[k] = sk[0], ptk[0] * f, pvk[0]
+    return s, pt, pv
 
 
 def coarse_index(n_dms: int, n_coarse: int) -> np.ndarray:

@@ -296,3 +296,50 @@ def test_detect_tie_break():
     assert oracle.detect(s) == (1, 2)
     s[1, 1] = 5.0
     assert oracle.detect(s) == (1, 1)
+
+
+
+# ----------------------------------------------------------------------------- RFI zapping, downsampling
+def test_zapping_is_linear_in_the_channel_set():
+    """Zapped + zapped-only de-dispersions add up to the full one; zapping every
+    channel gives zeros (Sec. 3 footnote: zapped channels are left out)."""
+    rng = np.random.Generator(np.random.PCG64(41))
+    C, n_t = 12, 40
+    d = rng.integers(0, 9, size=(5, C)).astype(np.int32)
+    x = rng.integers(0, 256, size=(C, n_t + 9)).astype(np.uint8)
+    m = rng.integers(0, 2, size=C).astype(np.uint8)
+    a = oracle.dedisperse(oracle.zap_channels(x, m), d, n_t)
+    b = oracle.dedisperse(oracle.zap_channels(x, 1 - m), d, n_t)
+    assert np.array_equal(a.astype(np.int64) + b, oracle.dedisperse(x, d, n_t))
+    assert not oracle.dedisperse(oracle.zap_channels(x, np.ones(C)), d, n_t).any()
+
+
+@pytest.mark.parametrize("f", [1, 2, 3, 7, 10, 40])
+def test_decimated_series_is_the_boxcar_at_stride_f(f):
+    """X_f[j] = B_f[j f]: decimation samples the sliding boxcar (an independent
+    code path, the C boxcar) at multiples of f; the trailing partial window is
+    dropped, so the sums telescope to the first (n_t // f) f samples."""
+    rng = np.random.Generator(np.random.PCG64(f))
+    D = rng.integers(0, 5000, size=(4, 97)).astype(np.int32)
+    X = oracle.decimate(D, f)
+    n = 97 // f
+    assert X.shape == (4, n)
+    for i in range(4):
+        assert np.array_equal(X[i], oracle.boxcar(D[i], f)[::f][:n])
+    assert np.array_equal(X.sum(axis=1), D[:, :n * f].astype(np.int64).sum(axis=1))
+
+
+@pytest.mark.parametrize("f,t0", [(1, 0), (4, 13), (10, 99), (7, 96), (7, 99)])
+def test_decimated_snr_single_spike_closed_form(f, t0):
+    """One spike of height h in a zero series: one non-zero bin among N = n_t // f,
+    so S/N = sqrt(N - 1) whatever h, at peak_t = f * (t0 // f)."""
+    n_t, h = 100, 777
+    D = np.zeros((1, n_t), np.int32)
+    D[0, t0] = h
+    s, pt, pv = oracle.snr_decimated(D, [f])
+    N = n_t // f
+    if t0 < N * f:
+        assert s[0, 0] == pytest.approx(np.sqrt(N - 1), rel=1e-12)
+        assert pt[0, 0] == f * (t0 // f) and pv[0, 0] == h
+    else:  # the spike falls in the dropped tail: a constant (zero) series
+        assert s[0, 0] == 0.0 and pv[0, 0] == 0
