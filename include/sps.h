@@ -50,6 +50,7 @@ typedef enum {
 } sps_status;
 
 enum { SPS_MODE_BRUTE = 0, SPS_MODE_SUBBAND = 1 };
+enum { SPS_SMOOTH_SLIDING = 0, SPS_SMOOTH_DECIMATE = 1 };
 
 typedef struct sps_plan sps_plan; /* opaque */
 
@@ -63,7 +64,16 @@ typedef struct sps_plan sps_plan; /* opaque */
  *   step one shifts channels inside a subband with the coarse DM of the trial,
  *   step two shifts subbands with the full trial DM.
  * coarse_dms (ascending) lists the step-one DMs; coarse_of[i] (non-decreasing,
- * < n_coarse) maps trial i to its coarse DM, NULL = i / (n_dms / n_coarse). */
+ * < n_coarse) maps trial i to its coarse DM, NULL = i / (n_dms / n_coarse).
+ * smoothing (Sec. 2 "downsampling (smoothing)"; Table 2 DOWNSAMPLING, NRSAMPLES):
+ *   SLIDING  - widths are boxcar widths: B_w[t] = sum_{u<w} D[t+u], t <= N_t - w;
+ *   DECIMATE - widths are downsampling factors f: X_f[j] = sum_{u<f} D[j f + u],
+ *              j < N_t / f (the trailing N_t mod f samples are dropped); S/N is
+ *              taken over the N_t / f downsampled samples (factor 1 = the
+ *              series itself, Sec. 5) and peak_t is in input samples, f * j.
+ * zap (Sec. 3, footnote: channels zapped for terrestrial RFI): zapped channels
+ * contribute nothing to any sum; the search then reads a masked copy of x in
+ * the workspace (sps_plan_workspace_bytes includes it). */
 typedef struct {
   int32_t channels;
   double f_lo_mhz;
@@ -79,6 +89,8 @@ typedef struct {
   const double* coarse_dms; /* SUBBAND only, host, n_coarse entries                */
   int32_t n_coarse;
   const int32_t* coarse_of; /* SUBBAND only, host, n_dms entries or NULL           */
+  int32_t smoothing;        /* SPS_SMOOTH_SLIDING (0) or SPS_SMOOTH_DECIMATE (1)   */
+  const uint8_t* zap;       /* host, `channels` flags, non-zero = zapped, or NULL  */
 } sps_plan_desc;
 
 /* Launch and tiling parameters of one de-dispersion kernel (the Table 3 genes,
@@ -189,7 +201,9 @@ sps_status sps_subband_step1(const sps_plan* plan, const uint8_t* x, int64_t x_p
 sps_status sps_subband_step2(const sps_plan* plan, const uint16_t* Y, int32_t* D, void* stream);
 
 /* Boxcar integration, materialised (for checking):
- *   B[w][i][t] = sum_{u < width_w} D[i][t + u] for t <= N_t - width_w, else 0.
+ *   B[w][i][t] = sum_{u < width_w} D[i][t + u] for t <= N_t - width_w, else 0;
+ * with DECIMATE smoothing, B[w][i][j] = X_f[j] (f = width_w) for j < N_t / f,
+ * else 0.
  * D: device int32 [n_dms][N_t]; B: device int32 [n_widths][n_dms][N_t]. */
 sps_status sps_integrate(const sps_plan* plan, const int32_t* D, int32_t* B, void* stream);
 
@@ -197,7 +211,9 @@ sps_status sps_integrate(const sps_plan* plan, const int32_t* D, int32_t* B, voi
  * over the N = N_t - width + 1 valid boxcar samples B:
  *   snr = (N*max(B) - sum B) / sqrt(N*sum B^2 - (sum B)^2),
  * i.e. (peak - mean) / population sigma, from exact integer moments; 0 when
- * the series is constant.  peak_t = first t with B[t] = max(B).
+ * the series is constant.  peak_t = first t with B[t] = max(B).  With
+ * DECIMATE smoothing the same over the N = N_t / f samples X_f[j]; peak_t is
+ * then f times the first j of the maximum.
  * D must hold what sps_dedisperse produces for this plan: values in
  * [0, 255 * channels]; the kernel sizes its partial sums from that bound.
  * snr: device double [n_widths][n_dms]; peak_t, peak_val: device int32, same

@@ -28,6 +28,8 @@ from ._lib import SpsError, check, lib, lib_path  # noqa: F401
 
 MODE_BRUTE = 0
 MODE_SUBBAND = 1
+SMOOTH_SLIDING = 0
+SMOOTH_DECIMATE = 1
 
 
 class DedispConfig(ctypes.Structure):
@@ -60,7 +62,8 @@ class PlanDesc(ctypes.Structure):
                 ("n_samples", ctypes.c_int32), ("dms", ctypes.c_void_p), ("n_dms", ctypes.c_int32),
                 ("widths", ctypes.c_void_p), ("n_widths", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("n_subbands", ctypes.c_int32), ("coarse_dms", ctypes.c_void_p),
-                ("n_coarse", ctypes.c_int32), ("coarse_of", ctypes.c_void_p)]
+                ("n_coarse", ctypes.c_int32), ("coarse_of", ctypes.c_void_p), ("smoothing", ctypes.c_int32),
+                ("zap", ctypes.c_void_p)]
 
 
 class _Lazy:
@@ -112,13 +115,18 @@ class _Arrays:  # keeps the descriptor's host arrays alive during sps_plan_creat
     widths: np.ndarray
     coarse: np.ndarray | None
     coarse_of: np.ndarray | None
+    zap: np.ndarray | None = None
 
 
 def sps_plan_create(channels, f_lo_mhz, f_hi_mhz, t_samp_s, n_samples, dms, widths,
-                    mode=MODE_BRUTE, n_subbands=0, coarse_dms=None, coarse_of=None):
+                    mode=MODE_BRUTE, n_subbands=0, coarse_dms=None, coarse_of=None, smoothing=SMOOTH_SLIDING,
+                    zap=None):
     arr = _Arrays(np.ascontiguousarray(dms, np.float64), np.ascontiguousarray(widths, np.int32),
                   None if coarse_dms is None else np.ascontiguousarray(coarse_dms, np.float64),
-                  None if coarse_of is None else np.ascontiguousarray(coarse_of, np.int32))
+                  None if coarse_of is None else np.ascontiguousarray(coarse_of, np.int32),
+                  None if zap is None else (np.asarray(zap) != 0).astype(np.uint8))
+    if arr.zap is not None and arr.zap.size != int(channels):
+        raise ValueError("zap needs one flag per channel")
     d = PlanDesc()
     d.channels, d.f_lo_mhz, d.f_hi_mhz, d.t_samp_s = int(channels), float(f_lo_mhz), float(f_hi_mhz), float(t_samp_s)
     d.n_samples = int(n_samples)
@@ -128,6 +136,8 @@ def sps_plan_create(channels, f_lo_mhz, f_hi_mhz, t_samp_s, n_samples, dms, widt
     d.coarse_dms = arr.coarse.ctypes.data if arr.coarse is not None else None
     d.n_coarse = arr.coarse.size if arr.coarse is not None else 0
     d.coarse_of = arr.coarse_of.ctypes.data if arr.coarse_of is not None else None
+    d.smoothing = int(smoothing)
+    d.zap = arr.zap.ctypes.data if arr.zap is not None else None
     h = ctypes.c_void_p()
     check(_L.sps_plan_create(ctypes.byref(d), ctypes.byref(h)), "sps_plan_create")
     return h
@@ -233,9 +243,11 @@ class Plan:
     """A search plan (frequencies, delay tables, kernel configuration) on the current device."""
 
     def __init__(self, channels, f_lo_mhz, f_hi_mhz, t_samp_s, n_samples, dms, widths,
-                 mode=MODE_BRUTE, n_subbands=0, coarse_dms=None, coarse_of=None):
+                 mode=MODE_BRUTE, n_subbands=0, coarse_dms=None, coarse_of=None, smoothing=SMOOTH_SLIDING,
+                 zap=None):
         self.handle = sps_plan_create(channels, f_lo_mhz, f_hi_mhz, t_samp_s, n_samples, dms, widths,
-                                      mode, n_subbands, coarse_dms, coarse_of)
+                                      mode, n_subbands, coarse_dms, coarse_of, smoothing, zap)
+        self.smoothing = int(smoothing)
         self.channels = int(channels)
         self.n_samples = int(n_samples)
         self.dms = np.asarray(dms, np.float64).copy()
@@ -250,10 +262,11 @@ class Plan:
     def from_workload(cls, wl, mode=None):
         if mode is None:
             mode = MODE_SUBBAND if wl.n_subbands else MODE_BRUTE
+        extra = dict(smoothing=getattr(wl, "smoothing", SMOOTH_SLIDING), zap=getattr(wl, "zap", None))
         if mode == MODE_SUBBAND:
             return cls(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_t, wl.dms, wl.widths, MODE_SUBBAND,
-                       wl.n_subbands, wl.coarse_dms)
-        return cls(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_t, wl.dms, wl.widths)
+                       wl.n_subbands, wl.coarse_dms, **extra)
+        return cls(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_t, wl.dms, wl.widths, **extra)
 
     def __del__(self):
         h = getattr(self, "handle", None)

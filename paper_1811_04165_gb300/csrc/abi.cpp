@@ -61,10 +61,27 @@ size_t y_offset(const sps_plan* p) {
   return ((uses_presum(p) ? q_bytes(p, p->n_presum_series) : x4_bytes(p)) + 255) / 256 * 256;
 }
 
-size_t workspace_needed(const sps_plan* p) { return y_offset(p) + y_bytes(p); }
+// With zapped channels the workspace starts with the masked copy of x.
+size_t zap_bytes(const sps_plan* p) {
+  return p->zap.empty() ? 0 : ((size_t)p->channels * p->pitch4 + 255) / 256 * 256;
+}
+
+size_t workspace_needed(const sps_plan* p) { return zap_bytes(p) + y_offset(p) + y_bytes(p); }
 
 size_t workspace_any_config(const sps_plan* p) {
-  return (std::max(x4_bytes(p), q_bytes(p, p->max_presum_series)) + 255) / 256 * 256 + y_bytes(p);
+  return zap_bytes(p) + (std::max(x4_bytes(p), q_bytes(p, p->max_presum_series)) + 255) / 256 * 256 + y_bytes(p);
+}
+
+// Points the search at the masked copy of x when channels are zapped; moves
+// the workspace past it.
+sps_status prepare_input(const sps_plan* p, const uint8_t** x, int64_t* pitch, uint8_t** ws, cudaStream_t st) {
+  if (p->zap.empty()) return SPS_OK;
+  if (sps_status s = launch_zap_copy(*x, *pitch, (int32_t)p->n_in, p->d_zap, p->channels, *ws, p->pitch4, st))
+    return s;
+  *x = *ws;
+  *pitch = p->pitch4;
+  *ws += zap_bytes(p);
+  return SPS_OK;
 }
 
 U8PassArgs u8_args(const sps_plan* p, const uint8_t* x, int64_t pitch, const uint8_t* x4) {
@@ -163,6 +180,7 @@ sps_status run_dedisperse(const sps_plan* p, const uint8_t* x, int64_t pitch, in
   if (!D || !aligned16(D)) return fail(SPS_ERR_INVALID_ARG, "D must be non-null and 16-byte aligned");
   if ((s = check_workspace(p, ws, ws_bytes))) return s;
   uint8_t* x4 = static_cast<uint8_t*>(ws);
+  if ((s = prepare_input(p, &x, &pitch, &x4, st))) return s;
   if (p->mode == SPS_MODE_BRUTE)
     return run_u8_pass(p, p->cfg.brute, x, pitch, x4, (int32_t)p->dms.size(), p->channels, p->n_t, p->n_t,
                        p->dmax_brute, D, 0, st);
@@ -185,6 +203,7 @@ sps_status run_snr(const sps_plan* p, const int32_t* D, double* snr, int32_t* pe
   a.snr = snr;
   a.peak_t = peak_t;
   a.peak_val = peak_val;
+  a.decimate = p->smoothing == SPS_SMOOTH_DECIMATE ? 1 : 0;
   sps_status s = launch_snr(a, p->cfg.snr, st);
   if (s || !best) return s;
   return launch_detect(snr, peak_t, peak_val, a.n_dms, a.n_widths, best, st);
@@ -232,6 +251,7 @@ sps_status sps_plan_destroy(sps_plan* p) {
   cudaFree(p->d_offs);
   cudaFree(p->d_presum_series);
   cudaFree(p->d_presum_units);
+  cudaFree(p->d_zap);
   cudaFree(p->d_presum_copies);
   cudaFree(p->d_presum_offs);
   if (swap) cudaSetDevice(cur);
@@ -307,7 +327,9 @@ sps_status sps_subband_step1(const sps_plan* p, const uint8_t* x, int64_t pitch,
   if (sps_status s = check_x(p, x, pitch)) return s;
   if (!Y || !aligned16(Y)) return fail(SPS_ERR_INVALID_ARG, "Y must be non-null and 16-byte aligned");
   if (sps_status s = check_workspace(p, ws, ws_bytes)) return s;
-  return run_step1(p, x, pitch, static_cast<uint8_t*>(ws), Y, (cudaStream_t)stream);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  if (sps_status s = prepare_input(p, &x, &pitch, &w, (cudaStream_t)stream)) return s;
+  return run_step1(p, x, pitch, w, Y, (cudaStream_t)stream);
 }
 
 sps_status sps_subband_step2(const sps_plan* p, const uint16_t* Y, int32_t* D, void* stream) {
@@ -322,8 +344,8 @@ sps_status sps_integrate(const sps_plan* p, const int32_t* D, int32_t* B, void* 
   clear_error();
   if (sps_status s = check_plan(p)) return s;
   if (!D || !B) return fail(SPS_ERR_INVALID_ARG, "null pointer");
-  return launch_integrate(D, (int32_t)p->dms.size(), p->n_t, p->d_widths, (int32_t)p->widths.size(), B,
-                          p->d_status, (cudaStream_t)stream);
+  return launch_integrate(D, (int32_t)p->dms.size(), p->n_t, p->d_widths, (int32_t)p->widths.size(),
+                          p->smoothing == SPS_SMOOTH_DECIMATE ? 1 : 0, B, p->d_status, (cudaStream_t)stream);
 }
 
 sps_status sps_snr(const sps_plan* p, const int32_t* D, double* snr, int32_t* peak_t, int32_t* peak_val,

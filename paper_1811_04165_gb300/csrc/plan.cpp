@@ -310,6 +310,8 @@ sps_status plan_create(const sps_plan_desc* d, sps_plan** out) {
   }
   if (d->mode != SPS_MODE_BRUTE && d->mode != SPS_MODE_SUBBAND)
     return fail(SPS_ERR_INVALID_ARG, "unknown mode");
+  if (d->smoothing != SPS_SMOOTH_SLIDING && d->smoothing != SPS_SMOOTH_DECIMATE)
+    return fail(SPS_ERR_INVALID_ARG, "unknown smoothing");
 
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
@@ -328,6 +330,9 @@ sps_status plan_create(const sps_plan_desc* d, sps_plan** out) {
   p->n_t = d->n_samples;
   p->dms.assign(d->dms, d->dms + d->n_dms);
   p->widths.assign(d->widths, d->widths + d->n_widths);
+  p->smoothing = d->smoothing;
+  if (d->zap && std::any_of(d->zap, d->zap + d->channels, [](uint8_t z) { return z != 0; }))
+    for (int32_t c = 0; c < d->channels; c++) p->zap.push_back(d->zap[c] ? 1 : 0);
   const int32_t C = d->channels, n_dms = d->n_dms;
   const double f_ref = centre_mhz(p->f_lo, p->f_hi, C, C - 1);
   int64_t max_total = 0;
@@ -410,6 +415,7 @@ sps_status plan_create(const sps_plan_desc* d, sps_plan** out) {
   if (max_sum > INT32_MAX) { delete p; return fail(SPS_ERR_UNSUPPORTED, "boxcar sums could exceed int32"); }
 
   sps_status st = upload(p->widths, &p->d_widths);
+  if (st == SPS_OK) st = upload(p->zap, &p->d_zap);
   if (st == SPS_OK) {
     std::vector<uint32_t> zero(1, 0u);
     st = upload(zero, &p->d_status);

@@ -138,11 +138,15 @@ __device__ double snr_from_moments(int64_t N, const Moments& m) {
 // overflow (from the largest possible boxcar value).  The pass tracks only the
 // maximum; the first position of the block's maximum is found afterwards by the
 // few threads whose own maximum equals it.
-template <int NWP>
 //
 // `narrow`: the host has shown that a warp's S2 total fits 64 bits (32 threads'
 // samples times the largest square), so warps reduce S1 and S2 as 64-bit sums
 // and the maximum with one redux; otherwise the full 128-bit merge runs.
+//
+// DEC: the widths are downsampling factors f; the series is X_f[j] =
+// P[(j+1) f] - P[j f] for j < N_t / f (Table 2 DOWNSAMPLING), and peak_t is
+// reported as f j.
+template <int NWP, bool DEC>
 __global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_begin, int flush, int use_tma,
                                                              int narrow) {
   extern __shared__ __align__(16) uint32_t buf[];
@@ -174,33 +178,49 @@ __global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_be
       s2p[k] = 0ull;
     }
   };
-  const int n_all = n_t - W[NWP - 1] + 1;  // every width of the pass is valid below this
-  const int n_any = n_t - W[0] + 1;
-  int count = 0;
-  int t = threadIdx.x;
-  for (; t < n_all; t += blockDim.x) {
-    const uint32_t p0 = P[t];
+  if constexpr (DEC) {
+    // each factor strides its own samples; partials are flushed per factor
 #pragma unroll
     for (int k = 0; k < NWP; k++) {
-      const uint32_t B = P[t + W[k]] - p0;
-      s1p[k] += B;
-      s2p[k] += (unsigned long long)B * B;
-      mx[k] = max(mx[k], B);
+      const int N = n_t / W[k];
+      int count = 0;
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const uint32_t B = P[(j + 1) * W[k]] - P[j * W[k]];
+        s1p[k] += B;
+        s2p[k] += (unsigned long long)B * B;
+        mx[k] = max(mx[k], B);
+        if (++count == flush) { flush_partials(); count = 0; }
+      }
     }
-    if (++count == flush) { flush_partials(); count = 0; }
-  }
-  for (; t < n_any; t += blockDim.x) {
-    const uint32_t p0 = P[t];
+  } else {
+    const int n_all = n_t - W[NWP - 1] + 1;  // every width of the pass is valid below this
+    const int n_any = n_t - W[0] + 1;
+    int count = 0;
+    int t = threadIdx.x;
+    for (; t < n_all; t += blockDim.x) {
+      const uint32_t p0 = P[t];
 #pragma unroll
-    for (int k = 0; k < NWP; k++) {
-      if (t + W[k] <= n_t) {
+      for (int k = 0; k < NWP; k++) {
         const uint32_t B = P[t + W[k]] - p0;
         s1p[k] += B;
         s2p[k] += (unsigned long long)B * B;
         mx[k] = max(mx[k], B);
       }
+      if (++count == flush) { flush_partials(); count = 0; }
     }
-    if (++count == flush) { flush_partials(); count = 0; }
+    for (; t < n_any; t += blockDim.x) {
+      const uint32_t p0 = P[t];
+#pragma unroll
+      for (int k = 0; k < NWP; k++) {
+        if (t + W[k] <= n_t) {
+          const uint32_t B = P[t + W[k]] - p0;
+          s1p[k] += B;
+          s2p[k] += (unsigned long long)B * B;
+          mx[k] = max(mx[k], B);
+        }
+      }
+      if (++count == flush) { flush_partials(); count = 0; }
+    }
   }
   flush_partials();
   if (narrow) {
@@ -236,7 +256,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_be
   // that thread's samples (u = owner + m * blockDim.x) together, 32 at a time
 #pragma unroll
   for (int k = 0; k < NWP; k++) {
-    const int N = n_t - W[k] + 1;
+    const int N = DEC ? n_t / W[k] : n_t - W[k] + 1;
     unsigned owners = __ballot_sync(0xffffffffu, (int32_t)mx[k] == gmax[k]);
     while (owners) {
       const int o = __ffs(owners) - 1;
@@ -244,7 +264,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_be
       const int owner = warp * 32 + o;
       for (int m0 = 0; owner + m0 * (int)blockDim.x < N; m0 += 32) {
         const int u = owner + (m0 + lane) * (int)blockDim.x;
-        const bool hit = u < N && (int32_t)(P[u + W[k]] - P[u]) == gmax[k];
+        const uint32_t v = u < N ? (DEC ? P[(u + 1) * W[k]] - P[u * W[k]] : P[u + W[k]] - P[u]) : 0u;
+        const bool hit = u < N && (int32_t)v == gmax[k];
         const unsigned h = __ballot_sync(0xffffffffu, hit);
         if (h) {
           if (lane == 0) atomicMin(&first[k], owner + (m0 + __ffs(h) - 1) * (int)blockDim.x);
@@ -259,15 +280,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_be
     Moments r = part[0][k];
     for (int q = 1; q < nw; q++) merge(r, part[q][k]);
     const int64_t o = (int64_t)(w_begin + k) * a.n_dms + i;
-    a.snr[o] = snr_from_moments(n_t - W[k] + 1, r);
-    a.peak_t[o] = first[k];
+    a.snr[o] = snr_from_moments(DEC ? n_t / W[k] : n_t - W[k] + 1, r);
+    a.peak_t[o] = DEC ? first[k] * W[k] : first[k];
     a.peak_val[o] = gmax[k];
   }
 }
 
 __global__ void __launch_bounds__(kMaxThreads, 1)
 integrate_kernel(const int32_t* D, int n_dms, int n_t, const int32_t* widths, int n_widths, int32_t* B,
-                 int use_tma, uint32_t* status) {
+                 int use_tma, int decimate, uint32_t* status) {
   extern __shared__ __align__(16) uint32_t buf[];
   __shared__ uint32_t scratch[32];
   __shared__ uint64_t bar;
@@ -276,9 +297,10 @@ integrate_kernel(const int32_t* D, int n_dms, int n_t, const int32_t* widths, in
   const uint32_t* P = buf + kPad - 1;
   for (int wi = 0; wi < n_widths; wi++) {
     const int w = __ldg(widths + wi);
-    const int N = n_t - w + 1;
+    const int N = decimate ? n_t / w : n_t - w + 1;
     int32_t* out = B + ((int64_t)wi * n_dms + i) * n_t;
-    for (int t = threadIdx.x; t < n_t; t += blockDim.x) out[t] = t < N ? (int32_t)(P[t + w] - P[t]) : 0;
+    for (int t = threadIdx.x; t < n_t; t += blockDim.x)
+      out[t] = t < N ? (int32_t)(decimate ? P[(t + 1) * w] - P[t * w] : P[t + w] - P[t]) : 0;
   }
 }
 
@@ -356,16 +378,17 @@ bool snr_config_supported(const sps_snr_config& c, std::string* why) {
 
 typedef void (*SnrKernel)(SnrArgs, int, int, int, int);
 
+template <bool DEC>
 SnrKernel snr_variant(int nwp) {
   switch (nwp) {
-    case 1: return snr_kernel<1>;
-    case 2: return snr_kernel<2>;
-    case 3: return snr_kernel<3>;
-    case 4: return snr_kernel<4>;
-    case 5: return snr_kernel<5>;
-    case 6: return snr_kernel<6>;
-    case 7: return snr_kernel<7>;
-    default: return snr_kernel<8>;
+    case 1: return snr_kernel<1, DEC>;
+    case 2: return snr_kernel<2, DEC>;
+    case 3: return snr_kernel<3, DEC>;
+    case 4: return snr_kernel<4, DEC>;
+    case 5: return snr_kernel<5, DEC>;
+    case 6: return snr_kernel<6, DEC>;
+    case 7: return snr_kernel<7, DEC>;
+    default: return snr_kernel<8, DEC>;
   }
 }
 
@@ -384,7 +407,8 @@ sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st
   const int narrow = warp_s2 < 1.8e19L ? 1 : 0;
   const size_t smem = prefix_smem(a.n_t);
   for (int w0 = 0; w0 < a.n_widths; w0 += kWidthsPerPass) {
-    SnrKernel fn = snr_variant(std::min(kWidthsPerPass, a.n_widths - w0));
+    const int nwp = std::min(kWidthsPerPass, a.n_widths - w0);
+    SnrKernel fn = a.decimate ? snr_variant<true>(nwp) : snr_variant<false>(nwp);
     SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     fn<<<a.n_dms, c.threads, smem, st>>>(a, w0, flush, tma_ok(a.D, a.n_t) ? 1 : 0, narrow);
     SPS_CUDA(cudaGetLastError());
@@ -393,11 +417,12 @@ sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st
 }
 
 sps_status launch_integrate(const int32_t* D, int32_t n_dms, int32_t n_t, const int32_t* widths,
-                            int32_t n_widths, int32_t* B, uint32_t* status, cudaStream_t st) {
+                            int32_t n_widths, int32_t decimate, int32_t* B, uint32_t* status, cudaStream_t st) {
   if (sps_status s = check_row_fits(n_t, 256)) return s;
   const size_t smem = prefix_smem(n_t);
   SPS_CUDA(cudaFuncSetAttribute(integrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  integrate_kernel<<<n_dms, 256, smem, st>>>(D, n_dms, n_t, widths, n_widths, B, tma_ok(D, n_t) ? 1 : 0, status);
+  integrate_kernel<<<n_dms, 256, smem, st>>>(D, n_dms, n_t, widths, n_widths, B, tma_ok(D, n_t) ? 1 : 0, decimate,
+                                             status);
   SPS_CUDA(cudaGetLastError());
   return SPS_OK;
 }

@@ -120,6 +120,7 @@ struct SnrArgs {
   int32_t* peak_t;
   int32_t* peak_val;
   uint32_t* status;
+  int32_t decimate;        // 1: widths are downsampling factors
 };
 
 // Kernel launchers (dedisperse.cu, snr.cu).  They validate the configuration
@@ -128,7 +129,7 @@ sps_status launch_u8_pass(const U8PassArgs& a, const sps_dedisp_config& cfg, cud
 sps_status launch_step2(const Step2Args& a, const sps_dedisp_config& cfg, cudaStream_t st);
 sps_status launch_snr(const SnrArgs& a, const sps_snr_config& cfg, cudaStream_t st);
 sps_status launch_integrate(const int32_t* D, int32_t n_dms, int32_t n_t, const int32_t* widths,
-                            int32_t n_widths, int32_t* B, uint32_t* status, cudaStream_t st);
+                            int32_t n_widths, int32_t decimate, int32_t* B, uint32_t* status, cudaStream_t st);
 sps_status launch_expand(const uint8_t* x, int64_t pitch, int32_t in_len, int32_t channels, uint8_t* x4,
                          int64_t pitch4, cudaStream_t st);
 sps_status launch_detect(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
@@ -137,6 +138,8 @@ sps_status launch_presum_series(const uint8_t* x, int64_t pitch, int32_t in_len,
                                 int32_t n_units, int32_t unit_channels, int32_t max_rel, const PresumSeries* series,
                                 int32_t n_series, uint16_t* q, int32_t q_pitch, cudaStream_t st);
 sps_status launch_presum_pass(const PresumPassArgs& a, const sps_dedisp_config& cfg, cudaStream_t st);
+sps_status launch_zap_copy(const uint8_t* x, int64_t pitch, int32_t in_len, const uint8_t* zap, int32_t channels,
+                           uint8_t* out, int64_t out_pitch, cudaStream_t st);
 bool presum_config_supported(const sps_dedisp_config& cfg, std::string* why);
 size_t presum_smem_bytes(const sps_dedisp_config& cfg, int32_t data_bytes);
 int presum_window_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
@@ -203,6 +206,9 @@ struct sps_plan {
   int32_t* d_d1 = nullptr;
   int32_t* d_d2 = nullptr;
   int32_t* d_widths = nullptr;
+  int32_t smoothing = SPS_SMOOTH_SLIDING;
+  std::vector<uint8_t> zap;      // per channel, 1 = zapped (empty: none zapped)
+  uint8_t* d_zap = nullptr;
   int32_t* d_step2_tiles = nullptr;
   int32_t n_step2_tiles = 0;
   uint32_t* d_status = nullptr;  // kernels' status word (bounded-wait timeouts)

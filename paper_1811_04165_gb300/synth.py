@@ -46,6 +46,8 @@ class Workload:
     pulses: list = field(default_factory=list)
     n_subbands: int = 0
     coarse_dms: np.ndarray | None = None
+    smoothing: int = 0                 # 0 sliding boxcars, 1 decimating downsampling
+    zap: np.ndarray | None = None      # per-channel RFI flags (non-zero = zapped)
 
     @property
     def dm_trial_samples(self) -> int:
