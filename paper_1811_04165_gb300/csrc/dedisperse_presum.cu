@@ -305,6 +305,38 @@ __device__ __forceinline__ void add_window16x2(const uint32_t (&W)[6], int o, ui
   }
 }
 
+// add_window16x2 with the offset o (0 .. 7) known at compile time: every word
+// index and shift is a constant (no selects).
+template <int O>
+__device__ __forceinline__ void add_window16x2_c(const uint32_t (&W)[6], uint32_t (&v)[2][8]) {
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    const int oj = O + j;
+    const int wi = oj >> 2, sh = (oj & 3) * 8;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t w = sh ? __funnelshift_r(W[wi + k], W[wi + k + 1 < 6 ? wi + k + 1 : 5], sh) : W[wi + k];
+      v[j][2 * k] += __byte_perm(w, 0u, 0x4140);
+      v[j][2 * k + 1] += __byte_perm(w, 0u, 0x4342);
+    }
+  }
+}
+
+// The offset is the same for every thread of a (series, channel), so the
+// switch does not diverge.
+__device__ __forceinline__ void add_window16x2_u(const uint32_t (&W)[6], int o, uint32_t (&v)[2][8]) {
+  switch (o) {
+    case 0: add_window16x2_c<0>(W, v); break;
+    case 1: add_window16x2_c<1>(W, v); break;
+    case 2: add_window16x2_c<2>(W, v); break;
+    case 3: add_window16x2_c<3>(W, v); break;
+    case 4: add_window16x2_c<4>(W, v); break;
+    case 5: add_window16x2_c<5>(W, v); break;
+    case 6: add_window16x2_c<6>(W, v); break;
+    default: add_window16x2_c<7>(W, v); break;
+  }
+}
+
 // Bytes u .. u + 23 of a channel row (u & 7 == 0) as six words; bytes at and
 // beyond in_len read as 0.  `row` is 16-byte aligned.
 __device__ __forceinline__ void load_row24(const uint8_t* row, int u, int in_len, uint32_t (&W)[6]) {
@@ -397,7 +429,7 @@ __global__ void __launch_bounds__(kSeriesThreads) presum_series_kernel(const uin
         W[2 * k] = t.x;
         W[2 * k + 1] = t.y;
       }
-      add_window16x2(W, off - b, v);
+      add_window16x2_u(W, off - b, v);
     }
     store_series(q, q_pitch, s, u0, v);
   }
