@@ -146,9 +146,13 @@ __device__ double snr_from_moments(int64_t N, const Moments& m) {
 // DEC: the widths are downsampling factors f; the series is X_f[j] =
 // P[(j+1) f] - P[j f] for j < N_t / f (Table 2 DOWNSAMPLING), and peak_t is
 // reported as f j.
-template <int NWP, bool DEC>
-__global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_begin, int flush, int use_tma,
-                                                             int narrow) {
+//
+// FAST: the host has shown that no thread's partials ever need flushing and
+// that warp sums fit 64 bits (`narrow`), so a thread keeps only its 32-bit S1,
+// 64-bit S2 and maximum per width; at most 64 registers, twice the blocks per SM.
+template <int NWP, bool DEC, bool FAST>
+__global__ void __launch_bounds__(kMaxThreads, FAST ? 2 : 1) snr_kernel(SnrArgs a, int w_begin, int flush,
+                                                                        int use_tma, int narrow) {
   extern __shared__ __align__(16) uint32_t buf[];
   __shared__ uint32_t scratch[32];
   __shared__ uint64_t bar;
@@ -170,12 +174,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_be
   }
   if (threadIdx.x < NWP) first[threadIdx.x] = 0x7fffffff;
   auto flush_partials = [&]() {
+    if constexpr (!FAST) {
 #pragma unroll
-    for (int k = 0; k < NWP; k++) {
-      s1t[k] += s1p[k];
-      add128(s2lo[k], s2hi[k], s2p[k]);
-      s1p[k] = 0u;
-      s2p[k] = 0ull;
+      for (int k = 0; k < NWP; k++) {
+        s1t[k] += s1p[k];
+        add128(s2lo[k], s2hi[k], s2p[k]);
+        s1p[k] = 0u;
+        s2p[k] = 0ull;
+      }
     }
   };
   if constexpr (DEC) {
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_be
         s1p[k] += B;
         s2p[k] += (unsigned long long)B * B;
         mx[k] = max(mx[k], B);
-        if (++count == flush) { flush_partials(); count = 0; }
+        if (!FAST && ++count == flush) { flush_partials(); count = 0; }
       }
     }
   } else {
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_be
         s2p[k] += (unsigned long long)B * B;
         mx[k] = max(mx[k], B);
       }
-      if (++count == flush) { flush_partials(); count = 0; }
+      if (!FAST && ++count == flush) { flush_partials(); count = 0; }
     }
     for (; t < n_any; t += blockDim.x) {
       const uint32_t p0 = P[t];
@@ -219,14 +225,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1) snr_kernel(SnrArgs a, int w_be
           mx[k] = max(mx[k], B);
         }
       }
-      if (++count == flush) { flush_partials(); count = 0; }
+      if (!FAST && ++count == flush) { flush_partials(); count = 0; }
     }
   }
   flush_partials();
-  if (narrow) {
+  if (FAST || narrow) {
 #pragma unroll
     for (int k = 0; k < NWP; k++) {
-      unsigned long long s1 = s1t[k], s2 = s2lo[k];
+      unsigned long long s1 = FAST ? (unsigned long long)s1p[k] : s1t[k], s2 = FAST ? s2p[k] : s2lo[k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
@@ -378,17 +384,17 @@ bool snr_config_supported(const sps_snr_config& c, std::string* why) {
 
 typedef void (*SnrKernel)(SnrArgs, int, int, int, int);
 
-template <bool DEC>
+template <bool DEC, bool FAST>
 SnrKernel snr_variant(int nwp) {
   switch (nwp) {
-    case 1: return snr_kernel<1, DEC>;
-    case 2: return snr_kernel<2, DEC>;
-    case 3: return snr_kernel<3, DEC>;
-    case 4: return snr_kernel<4, DEC>;
-    case 5: return snr_kernel<5, DEC>;
-    case 6: return snr_kernel<6, DEC>;
-    case 7: return snr_kernel<7, DEC>;
-    default: return snr_kernel<8, DEC>;
+    case 1: return snr_kernel<1, DEC, FAST>;
+    case 2: return snr_kernel<2, DEC, FAST>;
+    case 3: return snr_kernel<3, DEC, FAST>;
+    case 4: return snr_kernel<4, DEC, FAST>;
+    case 5: return snr_kernel<5, DEC, FAST>;
+    case 6: return snr_kernel<6, DEC, FAST>;
+    case 7: return snr_kernel<7, DEC, FAST>;
+    default: return snr_kernel<8, DEC, FAST>;
   }
 }
 
@@ -405,10 +411,13 @@ sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st
   const unsigned long long per_thread = (unsigned long long)((a.n_t + c.threads - 1) / c.threads);
   const long double warp_s2 = 32.0L * (long double)per_thread * (long double)bmax * (long double)bmax;
   const int narrow = warp_s2 < 1.8e19L ? 1 : 0;
+  // no thread ever flushes: its sample count stays within `flush`
+  const bool fast = narrow && per_thread <= (unsigned long long)flush;
   const size_t smem = prefix_smem(a.n_t);
   for (int w0 = 0; w0 < a.n_widths; w0 += kWidthsPerPass) {
     const int nwp = std::min(kWidthsPerPass, a.n_widths - w0);
-    SnrKernel fn = a.decimate ? snr_variant<true>(nwp) : snr_variant<false>(nwp);
+    SnrKernel fn = a.decimate ? (fast ? snr_variant<true, true>(nwp) : snr_variant<true, false>(nwp))
+                              : (fast ? snr_variant<false, true>(nwp) : snr_variant<false, false>(nwp));
     SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     fn<<<a.n_dms, c.threads, smem, st>>>(a, w0, flush, tma_ok(a.D, a.n_t) ? 1 : 0, narrow);
     SPS_CUDA(cudaGetLastError());
