@@ -164,6 +164,7 @@ sps_status run_step2(const sps_plan* p, const uint16_t* Y, int32_t* D, cudaStrea
   a.dmax_tile = p->dmax_step2;
   a.flush_every = p->step2_flush;
   a.D = D;
+  a.status = p->d_status;
   return launch_step2(a, p->cfg.step2, st);
 }
 

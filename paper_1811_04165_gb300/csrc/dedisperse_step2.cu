@@ -10,52 +10,70 @@
 // Step-one sums of <= 257 channels fit 16 bits, so Y is uint16 and a 32-bit
 // shared load carries two consecutive samples already in 16-bit lanes: one
 // add accumulates two samples.  Two copies of each window (the second shifted
-// by one sample) keep every load aligned.  Lanes are folded into int32 every
-// `flush_every` subbands, before a 16-bit lane could overflow.
+// by one sample) keep every load aligned: copy 0 arrives by bulk asynchronous
+// copy (TMA), copy 1 is built from it in shared memory.  Chunks of subbands
+// run through two stages: while the block computes one chunk, the next one's
+// copies land.  Lanes are folded into int32 every `flush_every` subbands,
+// before a 16-bit lane could overflow.
 #include <algorithm>
 
 #include "sps_internal.h"
+#include "tma.cuh"
 
 namespace sps {
 namespace {
 
 constexpr int kMaxThreads = 512;
 
-// Elements [p, p + 10) of a Y row, zero at and beyond `len`.
-__device__ __forceinline__ void load_y10(const uint16_t* row, int64_t p, int32_t len, uint32_t r[5]) {
-  if (p + 10 <= len) {
-    uint4 v = __ldg(reinterpret_cast<const uint4*>(row + p));
-    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
-    r[4] = __ldg(reinterpret_cast<const uint32_t*>(row + p + 8));
-  } else {
-#pragma unroll
-    for (int k = 0; k < 5; k++) {
-      int64_t q = p + 2 * k;
-      uint32_t e0 = q < len ? (uint32_t)__ldg(row + q) : 0u;
-      uint32_t e1 = q + 1 < len ? (uint32_t)__ldg(row + q + 1) : 0u;
-      r[k] = e0 | (e1 << 16);
-    }
-  }
-}
-
 template <int ND, int NW>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 step2_kernel(Step2Args a, int wd, int cs_max, int wb) {
-  extern __shared__ __align__(16) uint8_t smem[];
+  extern __shared__ __align__(128) uint8_t smem[];
   const int Di = wd * ND;
   const int wt = (int)(blockDim.x >> 5) / wd;
   const int Tt = wt * 64 * NW;
-  const int copy_stride = cs_max * wb;
-  uint32_t* tbl = reinterpret_cast<uint32_t*>(smem + 2 * copy_stride);
+  const int copy_stride = cs_max * wb;                       // one copy of a chunk's windows
+  const int stage_bytes = 2 * copy_stride + (Di * cs_max * 4 + 15) / 16 * 16;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int dm_sub = warp % wd, t_sub = warp / wd;
   const int t0 = blockIdx.x * Tt;
   const int k = a.tiles[3 * blockIdx.y], ib = a.tiles[3 * blockIdx.y + 1], nd = a.tiles[3 * blockIdx.y + 2];
   const int S = a.n_subbands;
+  const int n_chunks = (S + cs_max - 1) / cs_max;
   const uint32_t toff = (uint32_t)(t_sub * 128 * NW + lane * 4);  // bytes
   const int32_t* d2row0 = a.d2 + (int64_t)ib * S;
   const uint16_t* ybase = a.y + (int64_t)k * S * a.y_pitch;
+
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // warp 0: copy 0 of every window of chunk c into its stage, lane sl taking subband sl
+  auto issue = [&](int c) {
+    const int st = c & 1, sb = c * cs_max, cs = min(cs_max, S - sb);
+    uint32_t bytes = 0;
+    int64_t start = 0;
+    if (lane < cs) {
+      start = (int64_t)((t0 + __ldg(&d2row0[sb + lane])) & ~7);
+      bytes = (uint32_t)min((int64_t)wb, 2 * (a.y_pitch - start));
+    }
+    uint32_t total = bytes;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&full[st], total);
+    }
+    __syncwarp();
+    if (lane < cs)
+      bulk_g2s(smem + st * stage_bytes + lane * wb, ybase + (int64_t)(sb + lane) * a.y_pitch + start, bytes,
+               &full[st]);
+  };
 
   uint32_t lanes[ND][NW];
   int32_t acc[ND][NW][2];
@@ -75,22 +93,27 @@ step2_kernel(Step2Args a, int wd, int cs_max, int wb) {
       }
   };
 
+  if (warp == 0) issue(0);
   int pending = 0;
-  const int segs = wb >> 4;
-  for (int sb = 0; sb < S; sb += cs_max) {
-    const int cs = min(cs_max, S - sb);
-    __syncthreads();
-    for (int e = tid; e < cs * segs; e += blockDim.x) {
-      const int sl = e / segs, q = e - sl * segs;
-      const int s = sb + sl;
-      const int64_t start = (int64_t)((t0 + d2row0[s]) & ~7);
-      uint32_t r[5];
-      load_y10(ybase + (int64_t)s * a.y_pitch, start + 8 * q, a.y_len, r);
-      uint8_t* dst = smem + sl * wb + 16 * q;
-      *reinterpret_cast<uint4*>(dst) = make_uint4(r[0], r[1], r[2], r[3]);
-      *reinterpret_cast<uint4*>(dst + copy_stride) =
-          make_uint4(__byte_perm(r[0], r[1], 0x5432), __byte_perm(r[1], r[2], 0x5432),
-                     __byte_perm(r[2], r[3], 0x5432), __byte_perm(r[3], r[4], 0x5432));
+  const int wwords = wb >> 2;
+  for (int c = 0; c < n_chunks; c++) {
+    const int st = c & 1, sb = c * cs_max, cs = min(cs_max, S - sb);
+    uint8_t* stage = smem + st * stage_bytes;
+    uint32_t* tbl = reinterpret_cast<uint32_t*>(stage + 2 * copy_stride);
+    const bool ok = mbar_wait(&full[st], (c >> 1) & 1, a.status);
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      // this chunk's copies (the only ones issued and not yet waited for) may
+      // still be in flight: one more bounded wait before the block leaves
+      if (tid == 0) mbar_wait(&full[st], (c >> 1) & 1, nullptr);
+      return;
+    }
+    // copy 1 = copy 0 one sample later
+    const uint32_t* c0 = reinterpret_cast<const uint32_t*>(stage);
+    uint32_t* c1 = reinterpret_cast<uint32_t*>(stage + copy_stride);
+    for (int e = tid; e < cs * wwords; e += blockDim.x) {
+      const int j = e % wwords;
+      const uint32_t w0 = c0[e], w1 = j + 1 < wwords ? c0[e + 1] : 0u;
+      c1[e] = __byte_perm(w0, w1, 0x5432);
     }
     for (int e = tid; e < Di * cs; e += blockDim.x) {
       const int r = e / cs, sl = e - r * cs;
@@ -100,13 +123,14 @@ step2_kernel(Step2Args a, int wd, int cs_max, int wb) {
       const int rel = t0 + a.d2[(int64_t)i * S + s] - start;  // elements
       tbl[r * cs_max + sl] = (uint32_t)((rel & 1) * copy_stride + sl * wb + 2 * (rel & ~1));
     }
-    __syncthreads();
+    __syncthreads();  // copy 1 and the table are ready; the other stage's chunk is no longer read
+    if (warp == 0 && c + 1 < n_chunks) issue(c + 1);
 
     const uint32_t* trow = tbl + dm_sub * ND * cs_max;
     for (int sl = 0; sl < cs; sl++) {
 #pragma unroll
       for (int r = 0; r < ND; r++) {
-        const uint8_t* p = smem + trow[r * cs_max + sl] + toff;
+        const uint8_t* p = stage + trow[r * cs_max + sl] + toff;
 #pragma unroll
         for (int m = 0; m < NW; m++) lanes[r][m] += *reinterpret_cast<const uint32_t*>(p + 128 * m);
       }
@@ -172,8 +196,8 @@ bool step2_config_supported(const sps_dedisp_config& c, std::string* why) {
     *why = "warps_dm * warps_time must lie in [1, 16]";
     return false;
   }
-  if (c.chunk < 1 || c.chunk > 256) {
-    *why = "chunk must lie in [1, 256]";
+  if (c.chunk < 1 || c.chunk > 32) {
+    *why = "chunk must lie in [1, 32] (one issuing lane per subband of a chunk)";
     return false;
   }
   return true;
@@ -181,7 +205,8 @@ bool step2_config_supported(const sps_dedisp_config& c, std::string* why) {
 
 size_t step2_smem_bytes(const sps_dedisp_config& c, int32_t dmax_tile) {
   const size_t Di = (size_t)c.warps_dm * c.dms_per_thread;
-  return 2 * (size_t)c.chunk * copy_bytes(c, dmax_tile) + Di * c.chunk * 4;
+  const size_t stage = 2 * (size_t)c.chunk * copy_bytes(c, dmax_tile) + (Di * c.chunk * 4 + 15) / 16 * 16;
+  return 2 * stage + 16;  // two stages and their barriers
 }
 
 sps_status launch_step2(const Step2Args& a, const sps_dedisp_config& c, cudaStream_t st) {

@@ -107,6 +107,7 @@ struct Step2Args {
   int32_t dmax_tile;       // largest step-two delay spread inside a tile
   int32_t flush_every;     // subbands per 16-bit accumulation
   int32_t* D;              // [n_dms][n_t]
+  uint32_t* status;        // device status word (bounded-wait timeouts)
 };
 
 struct SnrArgs {
