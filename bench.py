@@ -292,6 +292,9 @@ def main():
     outs = plan.alloc_outputs()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    # the device's measured integer add rate (roofline context; outside the timed region)
+    int_peak_tadd = sps.sps_measure_int_add_rate() / 1e12
+
     # ---- timed region: K steps of the brute-force path
     barrier(world)
     torch.cuda.synchronize()
@@ -324,7 +327,9 @@ def main():
                 "unit": "Tadd/s", "frac": achieved / peak_tadd, "traffic": traffic,
                 "algorithmic_bytes_per_launch": wl.channels * pitch + 4 * wl.dm_trial_samples,
                 "algorithmic_adds_per_launch": adds, "ms_per_launch": dd_ms,
-                "peak_derivation": "152 SMs x 128 INT32 lanes/clk x 2070 MHz"}
+                "peak_derivation": "152 SMs x 128 INT32 lanes/clk x 2070 MHz",
+                "peak_measured": int_peak_tadd, "frac_of_measured": achieved / int_peak_tadd,
+                "peak_measured_how": "sps_measure_int_add_rate: independent add chains on the ALU and FMA pipes"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -403,6 +403,13 @@ sps_status sps_server_destroy(sps_server* server);
  * Returns TIMEOUT when it is non-zero. */
 sps_status sps_plan_status(const sps_plan* plan, uint32_t* host_status, int32_t clear);
 
+/* Measures the device's 32-bit integer add rate (adds/s over all SMs: independent
+ * add chains split between the ALU pipe and multiply-adds by one on the FMA
+ * pipe, best of three timed runs), the denominator against which the
+ * de-dispersion kernels' integer work is compared.  Not in the paper; a
+ * measurement helper.  Synchronises `stream`. */
+sps_status sps_measure_int_add_rate(double* adds_per_s, void* stream);
+
 const char* sps_status_string(sps_status s);
 /* Message of the last failed call on this thread ("" if none). */
 const char* sps_last_error(void);

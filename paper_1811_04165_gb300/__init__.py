@@ -479,6 +479,13 @@ class Server:
             self.handle = None
 
 
+def sps_measure_int_add_rate(stream=None) -> float:
+    """The device's measured 32-bit integer add rate, adds/s."""
+    v = ctypes.c_double()
+    check(_L.sps_measure_int_add_rate(ctypes.byref(v), _stream(stream)), "sps_measure_int_add_rate")
+    return float(v.value)
+
+
 def upload_filterbank(x_np: np.ndarray, pitch: int | None = None):
     """Copy a host uint8 [channels, samples] array into a pitched device tensor."""
     import torch

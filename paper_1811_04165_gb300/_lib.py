@@ -44,6 +44,7 @@ SIGNATURES = {
     "sps_server_pending": (_I32, [_P, _P]),
     "sps_server_clock": (ctypes.c_double, []),
     "sps_server_destroy": (_I32, [_P]),
+    "sps_measure_int_add_rate": (_I32, [_P, _P]),
     "sps_optimize": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "sps_tune_space": (_I32, [_P, _I32, _I32, _P, _P, _P, _P]),
     "sps_tune_config": (_I32, [_P, _I32, _P, _P]),
