@@ -145,11 +145,11 @@ sps_status sps_plan_delay_table(const sps_plan* plan, int32_t* host_out);
 sps_status sps_plan_subband_tables(const sps_plan* plan, int32_t* host_d1, int32_t* host_d2);
 
 /* Bytes of device workspace that sps_dedisperse / sps_search need under any
- * kernel configuration: the staged form of the batch (three copies shifted by
- * 1, 2 and 3 samples for the single-channel kernel, or the pre-summed pair
- * series for the pair kernel, whichever is larger), plus, in SUBBAND mode, the
- * step-one output Y.  The calls themselves accept any workspace at least as
- * large as the current configuration uses. */
+ * kernel configuration: with zapped channels, a masked copy of x; then the
+ * staged form of the batch (three copies shifted by 1, 2 and 3 samples for the
+ * single-channel kernel, or the pre-summed pair or quad series, whichever is
+ * largest); plus, in SUBBAND mode, the step-one output Y.  The calls themselves
+ * accept any workspace at least as large as the current configuration uses. */
 sps_status sps_plan_workspace_bytes(const sps_plan* plan, size_t* bytes);
 
 sps_status sps_plan_get_config(const sps_plan* plan, sps_kernel_config* out);

@@ -29,7 +29,8 @@ namespace {
 
 // 96 MiB: enough for the brute-force search of one 1536-channel, 1.024 s beam
 // with the single-channel kernel (three shifted copies of 1536 x 17136 bytes,
-// 79 MB), not for the pair kernel's series (236 MB) nor for the subband path.
+// 79 MB), not for the pre-summed pair or quad series (236 or 614 MB) nor for
+// the subband path.
 constexpr size_t kStaticScratchBytes = size_t(96) << 20;
 constexpr int kMaxDevices = 64;
 

@@ -124,7 +124,8 @@ struct SnrArgs {
   int32_t decimate;        // 1: widths are downsampling factors
 };
 
-// Kernel launchers (dedisperse.cu, snr.cu).  They validate the configuration
+// Kernel launchers (dedisperse_u8.cu, dedisperse_presum.cu, dedisperse_step2.cu,
+// snr.cu, zap.cu).  They validate the configuration
 // against the kernel's compiled variants and return UNSUPPORTED otherwise.
 sps_status launch_u8_pass(const U8PassArgs& a, const sps_dedisp_config& cfg, cudaStream_t st);
 sps_status launch_step2(const Step2Args& a, const sps_dedisp_config& cfg, cudaStream_t st);
