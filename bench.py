@@ -245,6 +245,54 @@ def time_pipelined(torch, plan, xs, steps, warmup, n_streams=2):
     return e0.elapsed_time(e1)
 
 
+def e2e_pipelined(torch, plan, xh, steps, warmup, device, n_workers=2):
+    """Wall time (s) of `steps` batches through the host entry point
+    (sps_search_host: pinned host batch in, S/N tables and detection back,
+    stream synchronised) on `n_workers` host threads, each with its own stream
+    and device buffers, taking steps in turn; ctypes releases the GIL during
+    the call, so one batch's copies overlap another's search."""
+    import threading
+    import paper_1811_04165_gb300 as sps
+    shp = (plan.n_widths, plan.n_dms)
+    workers = []
+    for _ in range(n_workers):
+        workers.append(dict(stream=torch.cuda.Stream(device=device),
+                            xd=torch.empty((plan.channels, plan.pitch), dtype=torch.uint8, device=device),
+                            out=plan.alloc_outputs(),
+                            ws=torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=device),
+                            hs=torch.empty(shp, dtype=torch.float64).pin_memory(),
+                            ht=torch.empty(shp, dtype=torch.int32).pin_memory(),
+                            hv=torch.empty(shp, dtype=torch.int32).pin_memory(),
+                            hb=torch.empty(4, dtype=torch.int32).pin_memory()))
+    errors = []
+
+    def run(w, first, n):
+        try:
+            torch.cuda.set_device(device)
+            o = workers[w]
+            for s in range(first + w, first + n, n_workers):
+                sps.sps_search_host(plan, xh[s % len(xh)], o["xd"], o["out"]["D"], o["out"]["snr"],
+                                    o["out"]["peak_t"], o["out"]["peak_val"], o["out"]["best"], o["hs"], o["ht"],
+                                    o["hv"], o["hb"], workspace=o["ws"], stream=o["stream"])
+        except Exception as e:  # surfaced after join
+            errors.append(e)
+
+    def batch(first, n):
+        ts = [threading.Thread(target=run, args=(w, first, n)) for w in range(n_workers)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        if errors:
+            raise errors[0]
+
+    batch(0, warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch(warmup, steps)
+    return time.perf_counter() - t0
+
+
 def time_path(torch, plan, xs, outs, steps, warmup, ws, flush, with_events=True):
     """Per-step CUDA-event times (ms) of [dedisperse, snr+detect] on the current stream."""
     import paper_1811_04165_gb300 as sps
@@ -375,11 +423,15 @@ def main():
                             outs["best"], hs, ht, hv, hb)
         if s >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
-    e2e_total = max_over_ranks(sum(e2e_t), world, dev)
+    e2e_seq = max_over_ranks(sum(e2e_t), world, dev)
+    e2e_total = max_over_ranks(e2e_pipelined(torch, plan, xh, args.steps, args.warmup, dev), world, dev)
     line["e2e"] = {"value": world * samples * args.steps / e2e_total, "unit": UNIT,
                    "h2d_bytes_per_step": wl.channels * pitch,
                    "d2h_bytes_per_step": int(hs.numel() * 8 + ht.numel() * 4 + hv.numel() * 4 + 16),
-                   "ms_per_step": 1e3 * e2e_total / args.steps}
+                   "ms_per_step": 1e3 * e2e_total / args.steps,
+                   "how": "sps_search_host on 2 host threads taking steps in turn (own stream and buffers each); "
+                          "every step copies its pinned batch in and its S/N tables and detection out",
+                   "sequential_ms_per_step": 1e3 * e2e_seq / args.steps}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
