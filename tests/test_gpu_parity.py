@@ -407,3 +407,10 @@ def test_argument_errors(lib):
                                 ctypes.c_void_p(Ds.data_ptr()), ctypes.c_void_p(small.data_ptr()),
                                 small.numel(), None) == 1
     assert p.status() == 0  # no kernel's bounded wait ran out
+
+
+def test_int_add_rate_is_plausible(lib):
+    """The measured integer add rate (the roofline's measured denominator) lies
+    between 1e12 adds/s and 2.5 x the 152 SM x 128 lane x 2.07 GHz unit count."""
+    r = lib.sps_measure_int_add_rate()
+    assert 1e12 < r < 2.5 * 152 * 128 * 2.07e9
