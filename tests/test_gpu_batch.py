@@ -61,6 +61,32 @@ def test_batch_matches_each_beam_alone(lib, branches):
         assert p.status() == 0
 
 
+def test_batch_mixes_smoothing_modes_and_zapping(lib):
+    """A decimating, RFI-zapped beam in the same graph as plain ones."""
+    import torch
+    wls = _beams()[:3]
+    b = wls[1]
+    rng = np.random.Generator(np.random.PCG64(4))
+    b.zap = (rng.random(b.channels) < 0.25).astype(np.uint8)
+    b.smoothing = lib.SMOOTH_DECIMATE
+    b.widths = np.array([1, 3, 16], np.int32)
+    plans, xs = _setup(lib, wls)
+    ref = _alone(plans, xs)
+    batch = lib.Batch(plans, xs, branches=3)
+    batch.launch()
+    torch.cuda.synchronize()
+    for o, r in zip(batch.outs, ref):
+        for k in ("D", "snr", "peak_t", "peak_val", "best"):
+            assert torch.equal(o[k], r[k]), k
+    x = xs[1].cpu().numpy()
+    want = oracle.dedisperse(oracle.zap_channels(x, b.zap),
+                             oracle.delay_table(b.f_lo, b.f_hi, b.channels, b.t_samp, b.dms), b.n_t)
+    assert np.array_equal(batch.outs[1]["D"].cpu().numpy(), want)
+    s, pt, pv = oracle.snr_decimated(want, b.widths)
+    assert np.allclose(batch.outs[1]["snr"].cpu().numpy(), s, rtol=1e-5, atol=1e-9)
+    assert np.array_equal(batch.outs[1]["peak_t"].cpu().numpy(), pt)
+
+
 def test_batch_beam_against_the_oracle(lib):
     import torch
     wls = _beams()
