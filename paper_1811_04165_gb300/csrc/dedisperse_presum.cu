@@ -305,36 +305,54 @@ __device__ __forceinline__ void add_window16x2(const uint32_t (&W)[6], int o, ui
   }
 }
 
-// add_window16x2 with the offset o (0 .. 7) known at compile time: every word
-// index and shift is a constant (no selects).
+// Adds bytes O .. O + 8 of W (16 bytes, O in 0 .. 7) into v as 16-bit lanes:
+// samples 0 .. 7 as four words (two per word), sample 8 in the low lane of
+// v[4]; every word index and shift is a constant.
 template <int O>
-__device__ __forceinline__ void add_window16x2_c(const uint32_t (&W)[6], uint32_t (&v)[2][8]) {
+__device__ __forceinline__ void add_window9_c(const uint32_t (&W)[4], uint32_t (&v)[5]) {
 #pragma unroll
-  for (int j = 0; j < 2; j++) {
-    const int oj = O + j;
-    const int wi = oj >> 2, sh = (oj & 3) * 8;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const uint32_t w = sh ? __funnelshift_r(W[wi + k], W[wi + k + 1 < 6 ? wi + k + 1 : 5], sh) : W[wi + k];
-      v[j][2 * k] += __byte_perm(w, 0u, 0x4140);
-      v[j][2 * k + 1] += __byte_perm(w, 0u, 0x4342);
-    }
+  for (int k = 0; k < 2; k++) {
+    const int wi = (O >> 2) + k, sh = (O & 3) * 8;
+    const uint32_t w = sh ? __funnelshift_r(W[wi], W[wi + 1], sh) : W[wi];
+    v[2 * k] += __byte_perm(w, 0u, 0x4140);
+    v[2 * k + 1] += __byte_perm(w, 0u, 0x4342);
+  }
+  constexpr int b8 = O + 8;
+  v[4] += __byte_perm(W[b8 >> 2], 0u, 0x4440 | (b8 & 3));
+}
+
+template <int O>
+__device__ __forceinline__ void add_window9x2_c(const uint32_t (&W0)[4], const uint32_t (&W1)[4], uint32_t (&v0)[5],
+                                                uint32_t (&v1)[5]) {
+  add_window9_c<O>(W0, v0);
+  add_window9_c<O>(W1, v1);
+}
+
+// Both halves of a thread share the offset o, and it is the same for every
+// thread of a (series, channel), so the switch does not diverge.
+__device__ __forceinline__ void add_window9x2_u(const uint32_t (&W0)[4], const uint32_t (&W1)[4], int o,
+                                                uint32_t (&v0)[5], uint32_t (&v1)[5]) {
+  switch (o) {
+    case 0: add_window9x2_c<0>(W0, W1, v0, v1); break;
+    case 1: add_window9x2_c<1>(W0, W1, v0, v1); break;
+    case 2: add_window9x2_c<2>(W0, W1, v0, v1); break;
+    case 3: add_window9x2_c<3>(W0, W1, v0, v1); break;
+    case 4: add_window9x2_c<4>(W0, W1, v0, v1); break;
+    case 5: add_window9x2_c<5>(W0, W1, v0, v1); break;
+    case 6: add_window9x2_c<6>(W0, W1, v0, v1); break;
+    default: add_window9x2_c<7>(W0, W1, v0, v1); break;
   }
 }
 
-// The offset is the same for every thread of a (series, channel), so the
-// switch does not diverge.
-__device__ __forceinline__ void add_window16x2_u(const uint32_t (&W)[6], int o, uint32_t (&v)[2][8]) {
-  switch (o) {
-    case 0: add_window16x2_c<0>(W, v); break;
-    case 1: add_window16x2_c<1>(W, v); break;
-    case 2: add_window16x2_c<2>(W, v); break;
-    case 3: add_window16x2_c<3>(W, v); break;
-    case 4: add_window16x2_c<4>(W, v); break;
-    case 5: add_window16x2_c<5>(W, v); break;
-    case 6: add_window16x2_c<6>(W, v); break;
-    default: add_window16x2_c<7>(W, v); break;
-  }
+// Eight samples of both copies of series s from u on: copy 0 from the nine
+// summed samples v, copy 1 (one sample later) a byte permutation of them.
+__device__ __forceinline__ void store_series9(uint16_t* q, int64_t q_pitch, int s, int u, const uint32_t (&v)[5]) {
+  uint16_t* row0 = q + (int64_t)s * 2 * q_pitch + u;
+  *reinterpret_cast<uint4*>(row0) = make_uint4(v[0], v[1], v[2], v[3]);
+  // copy 1: word k = (sample 2 k + 1, sample 2 k + 2)
+  *reinterpret_cast<uint4*>(row0 + q_pitch) =
+      make_uint4(__byte_perm(v[0], v[1], 0x5432), __byte_perm(v[1], v[2], 0x5432), __byte_perm(v[2], v[3], 0x5432),
+                 __byte_perm(v[3], v[4], 0x5432));
 }
 
 // Bytes u .. u + 23 of a channel row (u & 7 == 0) as six words; bytes at and
@@ -361,7 +379,7 @@ __device__ __forceinline__ void load_row24(const uint8_t* row, int u, int in_len
   }
 }
 
-constexpr int kSeriesThreads = 256;
+constexpr int kSeriesThreads = 128;
 constexpr int kSeriesBlock = kSeriesThreads * 16;  // samples per block
 
 __device__ __forceinline__ void store_series(uint16_t* q, int64_t q_pitch, int s, int u0, const uint32_t (&v)[2][8]) {
@@ -374,64 +392,74 @@ __device__ __forceinline__ void store_series(uint16_t* q, int64_t q_pitch, int s
 }
 
 // Series s, both copies j: q[(2 s + j) * q_pitch + u] = sum_c x[c0 + c][u + j + rel_c]
-// (rel of the last channel 0).  A block takes one unit and kSeriesBlock samples:
-// it stages the unit's channel rows once in shared memory (win_bytes per row,
-// covering the block plus the unit's largest relative delay), then every
-// thread writes 16 samples of both copies of each of the unit's series.
+// (rel of the last channel 0), written for u in the series' range [lo, hi).
+// A block takes one unit and kSeriesBlock samples: it stages the unit's
+// channel rows once in shared memory (win_bytes per row, covering the block
+// plus the unit's largest relative delay), then every thread computes eight
+// samples of both copies of each of the unit's series in each half of the
+// block (thread k: samples 8 k and 8 (k + kSeriesThreads) on), so that a
+// warp's 16-byte stores cover 512 contiguous bytes.  The thread sums nine
+// samples of copy 0; copy 1 (one sample later) is a byte permutation of them.
 __global__ void __launch_bounds__(kSeriesThreads) presum_series_kernel(const uint8_t* x, int64_t pitch,
                                                                        int32_t in_len, const PresumUnit* units,
                                                                        const PresumSeries* series, uint16_t* q,
                                                                        int32_t q_pitch, int32_t win_bytes) {
   extern __shared__ __align__(16) uint8_t win[];
-  const int4 uh = __ldg(reinterpret_cast<const int4*>(units + blockIdx.x));  // {c0, n, s_begin, s_end}
+  const int4 uh = __ldg(reinterpret_cast<const int4*>(units + blockIdx.x));      // {c0, n, s_begin, s_end}
+  const int4 ur = __ldg(reinterpret_cast<const int4*>(units + blockIdx.x) + 1);  // {max_rel, lo, hi, 0}
   const int ub = blockIdx.y * kSeriesBlock;
+  if (ub >= ur.z || ub + kSeriesBlock <= ur.y) return;  // no series of the unit needs these samples
+  // asynchronous 16-byte copies (all in flight at once); bytes at and beyond
+  // in_len are zero-filled and never read
   for (int c = 0; c < uh.y; c++) {
     const uint8_t* row = x + (int64_t)(uh.x + c) * pitch;
     for (int k = threadIdx.x; k < win_bytes / 16; k += kSeriesThreads) {
       const int p = ub + 16 * k;
-      uint4 v;
-      if (p + 16 <= in_len) {
-        v = __ldg(reinterpret_cast<const uint4*>(row + p));
-      } else {
-        uint32_t w[4];
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-          uint32_t t = 0;
-#pragma unroll
-          for (int b = 0; b < 4; b++)
-            if (p + 4 * i + b < in_len) t |= (uint32_t)__ldg(row + p + 4 * i + b) << (8 * b);
-          w[i] = t;
-        }
-        v = make_uint4(w[0], w[1], w[2], w[3]);
-      }
-      *reinterpret_cast<uint4*>(win + c * win_bytes + 16 * k) = v;
+      const int n = min(16, max(0, in_len - p));
+      const uint8_t* src = n > 0 ? row + p : row;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(win + c * win_bytes + 16 * k)),
+                   "l"(src), "r"(n)
+                   : "memory");
     }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-  const int u0 = ub + 16 * (int)threadIdx.x;
-  if (u0 >= q_pitch) return;
+  const int l0 = 8 * (int)threadIdx.x, l1 = l0 + 8 * kSeriesThreads;  // sample offsets of the halves
+  const int u0 = ub + l0, u1 = ub + l1;
+  // each series' header {c0, n, rel0, rel1}, {rel2, lo, hi, 0} is fetched one series ahead
+  int4 hn = make_int4(0, 0, 0, 0), rn = make_int4(0, 0, 0, 0);
+  if (uh.z < uh.w) {
+    hn = __ldg(reinterpret_cast<const int4*>(series + uh.z));
+    rn = __ldg(reinterpret_cast<const int4*>(series + uh.z) + 1);
+  }
   for (int s = uh.z; s < uh.w; s++) {
-    const int4 h = __ldg(reinterpret_cast<const int4*>(series + s));  // {c0, n, rel0, rel1}
-    const int rel2 = __ldg(&series[s].rel[2]);
-    uint32_t v[2][8];
-#pragma unroll
-    for (int j = 0; j < 2; j++)
-#pragma unroll
-      for (int k = 0; k < 8; k++) v[j][k] = 0u;
-    for (int c = 0; c < h.y; c++) {
-      const int rel = c + 1 == h.y ? 0 : (c == 0 ? h.z : (c == 1 ? h.w : rel2));
-      const int off = 16 * (int)threadIdx.x + rel, b = off & ~7;
-      const uint2* src = reinterpret_cast<const uint2*>(win + c * win_bytes + b);
-      uint32_t W[6];
-#pragma unroll
-      for (int k = 0; k < 3; k++) {
-        const uint2 t = src[k];
-        W[2 * k] = t.x;
-        W[2 * k + 1] = t.y;
-      }
-      add_window16x2_u(W, off - b, v);
+    const int4 h = hn, r = rn;
+    if (s + 1 < uh.w) {
+      hn = __ldg(reinterpret_cast<const int4*>(series + s + 1));
+      rn = __ldg(reinterpret_cast<const int4*>(series + s + 1) + 1);
     }
-    store_series(q, q_pitch, s, u0, v);
+    const bool need0 = u0 < q_pitch && u0 + 8 > r.y && u0 < r.z;
+    const bool need1 = u1 < q_pitch && u1 + 8 > r.y && u1 < r.z;
+    if (!need0 && !need1) continue;
+    uint32_t v0[5] = {0u, 0u, 0u, 0u, 0u}, v1[5] = {0u, 0u, 0u, 0u, 0u};
+    auto channel = [&](int c, int rel) {
+      const uint8_t* base = win + c * win_bytes + (rel & ~7);  // l0, l1 are multiples of 8
+      const uint2* s0 = reinterpret_cast<const uint2*>(base + l0);
+      const uint2* s1 = reinterpret_cast<const uint2*>(base + l1);
+      const uint2 a0 = s0[0], a1 = s0[1], b0 = s1[0], b1 = s1[1];
+      const uint32_t W0[4] = {a0.x, a0.y, a1.x, a1.y}, W1[4] = {b0.x, b0.y, b1.x, b1.y};
+      add_window9x2_u(W0, W1, rel & 7, v0, v1);
+    };
+    if (h.y == 4) {  // a full quad (every unit but a short last one of a group)
+      channel(0, h.z);
+      channel(1, h.w);
+      channel(2, r.x);
+      channel(3, 0);
+    } else {
+      for (int c = 0; c < h.y; c++) channel(c, c + 1 == h.y ? 0 : (c == 0 ? h.z : (c == 1 ? h.w : r.x)));
+    }
+    if (need0) store_series9(q, q_pitch, s, u0, v0);
+    if (need1) store_series9(q, q_pitch, s, u1, v1);
   }
 }
 
@@ -447,7 +475,9 @@ __global__ void __launch_bounds__(256) presum_series_direct_kernel(const uint8_t
   const int s = (int)(id / per_row);
   const int u0 = (int)(id - (int64_t)s * per_row) << 4;
   const int4 h = __ldg(reinterpret_cast<const int4*>(series + s));
-  const int rel2 = __ldg(&series[s].rel[2]);
+  const int4 r = __ldg(reinterpret_cast<const int4*>(series + s) + 1);  // {rel2, lo, hi, 0}
+  if (u0 + 16 <= r.y || u0 >= r.z) return;
+  const int rel2 = r.x;
   uint32_t v[2][8];
 #pragma unroll
   for (int j = 0; j < 2; j++)
@@ -524,8 +554,8 @@ sps_status launch_presum_series(const uint8_t* x, int64_t pitch, int32_t in_len,
                                 int32_t n_series, uint16_t* q, int32_t q_pitch, cudaStream_t st) {
   if (n_series == 0) return SPS_OK;
   // staged window per channel row: the block's samples, the largest relative
-  // delay, and the 24-byte reach of the last thread's loads
-  const int64_t win = ((int64_t)kSeriesBlock + max_rel + 32 + 15) / 16 * 16;
+  // delay, and the 16-byte reach of the last thread's loads
+  const int64_t win = ((int64_t)kSeriesBlock + max_rel + 16 + 15) / 16 * 16;
   const int64_t smem = win * unit_channels;
   if (smem <= 96 * 1024) {
     SPS_CUDA(cudaFuncSetAttribute(presum_series_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -220,9 +220,9 @@ sps_status apply_config(sps_plan* p, const sps_kernel_config& cfg) {
   if (pass.presum) {
     PresumTables pt;
     sps_status s = p->mode == SPS_MODE_BRUTE
-                       ? build_presum_tables(p->delays, n_dms, p->channels, p->channels, pass, &pt)
+                       ? build_presum_tables(p->delays, n_dms, p->channels, p->channels, (int32_t)p->n_t, pass, &pt)
                        : build_presum_tables(p->d1, (int32_t)p->coarse_dms.size(), p->channels,
-                                             p->channels / p->n_subbands, pass, &pt);
+                                             p->channels / p->n_subbands, (int32_t)p->n_1, pass, &pt);
     if (s) return s;
     PresumSeries* dser = nullptr;
     PresumUnit* dunit = nullptr;

@@ -10,7 +10,10 @@
 // so one series serves every trial with the same tuple rel.  Each series is
 // stored twice, copy 1 shifted by one sample, so that a trial whose reference
 // delay d is odd reads aligned words of copy 1 at d - 1.  The plan needs:
-//   series : every (unit, rel) any trial uses, as rows of the workspace;
+//   series : every (unit, rel) any trial uses, as rows of the workspace, with
+//            the sample range its trials read for outputs t < n_out:
+//            [min d', max d' + n_out), d' = the reference delay rounded down
+//            to even (copy 1 at d - 1 holds the samples from d on);
 //   copies : per (DM tile, group, chunk of units), the windows of series
 //            copies the tile reads -- one per (tuple, parity of d) that occurs,
 //            each just long enough for its trials -- packed back to back in
@@ -126,7 +129,7 @@ int32_t presum_stage_data(const std::vector<int32_t>& d, int32_t rows, int32_t C
   return (int32_t)std::min<int64_t>(best, INT32_MAX);
 }
 
-sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per,
+sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t n_out,
                                const sps_dedisp_config& cfg, PresumTables* out) {
   const int32_t K = 1 << cfg.presum;
   const int32_t G = C / per;
@@ -152,10 +155,24 @@ sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int3
       for (const Rel& r : v)
         if (std::min({r[0], r[1], r[2]}) < 0)
           return fail(SPS_ERR_INVALID_ARG, "a lower channel arrives before a higher one");
+      std::vector<int32_t> lo(v.size(), INT32_MAX), hi(v.size(), INT32_MIN);
+      for (int32_t i = 0; i < rows; i++) {
+        const size_t k = (size_t)index_of(v, rel_of(d, C, i, un));
+        const int32_t de = ref_delay(d, C, i, un) & ~1;
+        lo[k] = std::min(lo[k], de);
+        hi[k] = std::max(hi[k], de);
+      }
       sbase[(size_t)g * U + u] = (int32_t)out->series.size();
-      for (const Rel& r : v) out->series.push_back({un.c0, un.n, {r[0], r[1], r[2]}, {0, 0, 0}});
+      int32_t ulo = INT32_MAX, uhi = 0;
+      for (size_t k = 0; k < v.size(); k++) {
+        const int32_t slo = lo[k] & ~7, shi = (hi[k] + n_out + 7) / 8 * 8;
+        out->series.push_back({un.c0, un.n, {v[k][0], v[k][1], v[k][2]}, slo, shi, 0});
+        ulo = std::min(ulo, slo);
+        uhi = std::max(uhi, shi);
+      }
       const int32_t max_rel = v.back()[0];  // tuples sorted: the last has the largest first delay
-      out->units.push_back({un.c0, un.n, sbase[(size_t)g * U + u], (int32_t)out->series.size(), max_rel, {0, 0, 0}});
+      out->units.push_back({un.c0, un.n, sbase[(size_t)g * U + u], (int32_t)out->series.size(), max_rel, ulo, uhi,
+                            0});
       out->max_rel = std::max(out->max_rel, max_rel);
     }
 

@@ -5,9 +5,14 @@
 // (TMA) and is turned in place into prefix sums P[t] = sum_{u<t} D[u] (32-bit
 // wrap-around arithmetic: every boxcar B_w[t] = P[t + w] - P[t] is below 2^31,
 // so the wrapped difference is exact).  A single pass over t then serves all
-// widths of the pass at once, accumulating per width the exact integer moments
-// S1 = sum B, S2 = sum B^2 (128-bit at block level), the maximum and its first
-// position over the N = N_t - w + 1 valid samples.  One FP64 expression gives
+// widths of the pass at once, accumulating per width the exact integer moment
+// S2 = sum B^2 (128-bit at block level), the maximum and its first position
+// over the N = N_t - w + 1 valid samples.  S1 = sum B needs no pass: every
+// sample u lies in w boxcars except near the ends, so
+//   S1 = w T - sum_{j=1}^{w-1} P[j] - sum_{j=1}^{w-1} (T - P[N_t - j]),
+// T = P[N_t] (for decimation by f it telescopes to P[floor(N_t / f) f]); each
+// thread adds w times its share of T and subtracts its share of the end
+// terms, all exact in 64 bits.  One FP64 expression gives
 //   snr = (N P - S1) / sqrt(N S2 - S1^2),
 // i.e. (peak - mean) / population sigma, since N S2 - S1^2 = N^2 sigma^2.
 // Nothing is materialised; the integrate kernel writes B for checking.
@@ -50,9 +55,10 @@ __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* scratch) {
 }
 
 // Load row i into buf[kPad .. kPad + n_t) and turn it into prefix sums in place:
-// afterwards buf[kPad - 1 + k] = sum_{u<k} D[u] for k = 0..n_t.
+// afterwards buf[kPad - 1 + k] = sum_{u<k} D[u] for k = 0..n_t.  *seg = the sum
+// of the samples this thread scanned (the threads' segments tile the row).
 __device__ bool load_prefix(const int32_t* row, int n_t, uint32_t* buf, uint32_t* scratch, uint64_t* bar,
-                            bool use_tma, uint32_t* status) {
+                            bool use_tma, uint32_t* status, uint32_t* seg) {
   bool ok = true;
   if (use_tma) {
     if (threadIdx.x == 0) {
@@ -79,6 +85,7 @@ __device__ bool load_prefix(const int32_t* row, int n_t, uint32_t* buf, uint32_t
   const int b = min(n_t, (int)threadIdx.x * per), e = min(n_t, b + per);
   uint32_t s = 0;
   for (int t = b; t < e; t++) s += buf[kPad + t];
+  *seg = s;
   uint32_t run = block_exclusive_scan(s, scratch);
   for (int t = b; t < e; t++) {
     run += buf[kPad + t];
@@ -161,25 +168,24 @@ __global__ void __launch_bounds__(kMaxThreads, FAST ? 2 : 1) snr_kernel(SnrArgs 
   const int i = blockIdx.x;
   const int n_t = a.n_t;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (!load_prefix(a.D + (int64_t)i * n_t, n_t, buf, scratch, &bar, use_tma != 0, a.status)) return;
+  uint32_t seg = 0;
+  if (!load_prefix(a.D + (int64_t)i * n_t, n_t, buf, scratch, &bar, use_tma != 0, a.status, &seg)) return;
   const uint32_t* P = buf + kPad - 1;
 
   int W[NWP];
-  uint32_t s1p[NWP], mx[NWP];
-  unsigned long long s2p[NWP], s1t[NWP], s2lo[NWP], s2hi[NWP];
+  uint32_t mx[NWP];
+  unsigned long long s2p[NWP], s2lo[NWP], s2hi[NWP];
 #pragma unroll
   for (int k = 0; k < NWP; k++) {
     W[k] = __ldg(a.widths + w_begin + k);
-    s1p[k] = 0u; mx[k] = 0u; s2p[k] = 0ull; s1t[k] = 0ull; s2lo[k] = 0ull; s2hi[k] = 0ull;
+    mx[k] = 0u; s2p[k] = 0ull; s2lo[k] = 0ull; s2hi[k] = 0ull;
   }
   if (threadIdx.x < NWP) first[threadIdx.x] = 0x7fffffff;
   auto flush_partials = [&]() {
     if constexpr (!FAST) {
 #pragma unroll
       for (int k = 0; k < NWP; k++) {
-        s1t[k] += s1p[k];
         add128(s2lo[k], s2hi[k], s2p[k]);
-        s1p[k] = 0u;
         s2p[k] = 0ull;
       }
     }
@@ -192,7 +198,6 @@ __global__ void __launch_bounds__(kMaxThreads, FAST ? 2 : 1) snr_kernel(SnrArgs 
       int count = 0;
       for (int j = threadIdx.x; j < N; j += blockDim.x) {
         const uint32_t B = P[(j + 1) * W[k]] - P[j * W[k]];
-        s1p[k] += B;
         s2p[k] += (unsigned long long)B * B;
         mx[k] = max(mx[k], B);
         if (!FAST && ++count == flush) { flush_partials(); count = 0; }
@@ -208,7 +213,6 @@ __global__ void __launch_bounds__(kMaxThreads, FAST ? 2 : 1) snr_kernel(SnrArgs 
 #pragma unroll
       for (int k = 0; k < NWP; k++) {
         const uint32_t B = P[t + W[k]] - p0;
-        s1p[k] += B;
         s2p[k] += (unsigned long long)B * B;
         mx[k] = max(mx[k], B);
       }
@@ -220,7 +224,6 @@ __global__ void __launch_bounds__(kMaxThreads, FAST ? 2 : 1) snr_kernel(SnrArgs 
       for (int k = 0; k < NWP; k++) {
         if (t + W[k] <= n_t) {
           const uint32_t B = P[t + W[k]] - p0;
-          s1p[k] += B;
           s2p[k] += (unsigned long long)B * B;
           mx[k] = max(mx[k], B);
         }
@@ -229,10 +232,29 @@ __global__ void __launch_bounds__(kMaxThreads, FAST ? 2 : 1) snr_kernel(SnrArgs 
     }
   }
   flush_partials();
+  // this thread's share of S1 (wrap-around 64-bit terms; the block total is exact)
+  unsigned long long s1t[NWP];
+  if constexpr (DEC) {
+    // S1 = P[N f]: T less the samples after the last whole window (fewer than f)
+#pragma unroll
+    for (int k = 0; k < NWP; k++)
+      s1t[k] = (unsigned long long)seg -
+               (threadIdx.x == 0 ? (unsigned long long)(P[n_t] - P[n_t / W[k] * W[k]]) : 0ull);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NWP; k++) s1t[k] = (unsigned long long)W[k] * seg;
+    // end terms: P[j] and T - P[N_t - j] for 1 <= j < w, each below 2^31
+    for (int j = (int)threadIdx.x + 1; j < W[NWP - 1]; j += blockDim.x) {
+      const unsigned long long v = (unsigned long long)P[j] + (unsigned long long)(P[n_t] - P[n_t - j]);
+#pragma unroll
+      for (int k = 0; k < NWP; k++)
+        if (j < W[k]) s1t[k] -= v;
+    }
+  }
   if (FAST || narrow) {
 #pragma unroll
     for (int k = 0; k < NWP; k++) {
-      unsigned long long s1 = FAST ? (unsigned long long)s1p[k] : s1t[k], s2 = FAST ? s2p[k] : s2lo[k];
+      unsigned long long s1 = s1t[k], s2 = FAST ? s2p[k] : s2lo[k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
@@ -299,7 +321,8 @@ integrate_kernel(const int32_t* D, int n_dms, int n_t, const int32_t* widths, in
   __shared__ uint32_t scratch[32];
   __shared__ uint64_t bar;
   const int i = blockIdx.x;
-  if (!load_prefix(D + (int64_t)i * n_t, n_t, buf, scratch, &bar, use_tma != 0, status)) return;
+  uint32_t seg = 0;
+  if (!load_prefix(D + (int64_t)i * n_t, n_t, buf, scratch, &bar, use_tma != 0, status, &seg)) return;
   const uint32_t* P = buf + kPad - 1;
   for (int wi = 0; wi < n_widths; wi++) {
     const int w = __ldg(widths + wi);
@@ -402,11 +425,11 @@ sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st
   std::string why;
   if (!snr_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
   if (sps_status s = check_row_fits(a.n_t, sizeof(Moments) * 32 * kWidthsPerPass + 512)) return s;
-  // largest boxcar value: 255 * channels * widest width (< 2^31, checked by the plan)
+  // largest boxcar value: 255 * channels * widest width (< 2^31, checked by the plan);
+  // a thread's 64-bit S2 partial takes `flush` squares before it must be flushed
   const unsigned long long bmax = std::max<unsigned long long>(1ull, (unsigned long long)a.max_boxcar);
-  const unsigned long long f1 = 0xFFFFFFFFull / bmax;
   const unsigned long long f2 = 0xFFFFFFFFFFFFFFFFull / (bmax * bmax);
-  const int flush = (int)std::max<unsigned long long>(1ull, std::min<unsigned long long>({f1, f2, 1ull << 30}));
+  const int flush = (int)std::max<unsigned long long>(1ull, std::min<unsigned long long>(f2, 1ull << 30));
   // a warp's S2: 32 threads x ceil(n_t / threads) samples x bmax^2, in 64 bits?
   const unsigned long long per_thread = (unsigned long long)((a.n_t + c.threads - 1) / c.threads);
   const long double warp_s2 = 32.0L * (long double)per_thread * (long double)bmax * (long double)bmax;

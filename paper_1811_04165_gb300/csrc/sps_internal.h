@@ -74,15 +74,19 @@ struct PresumPassArgs {
 
 // One pre-summed series: channels c0 .. c0 + n - 1, channel c0 + j (j < n - 1)
 // taken rel[j] samples later than the last one.
+// [lo, hi): the samples of the series (both copies) that any valid output
+// reads, multiples of 8; the pre-pass writes only those.
 struct PresumSeries {
-  int32_t c0, n, rel[3], pad[3];
+  int32_t c0, n, rel[3], lo, hi, pad;
 };
 
 // One unit of K adjacent channels and the range of its series in the table;
-// max_rel = the largest relative delay of any of its series (of its first channel).
+// max_rel = the largest relative delay of any of its series (of its first
+// channel); [lo, hi) = the union of its series' sample ranges.
 struct PresumUnit {
-  int32_t c0, n, s_begin, s_end, max_rel, pad[3];
+  int32_t c0, n, s_begin, s_end, max_rel, lo, hi, pad;
 };
+static_assert(sizeof(PresumSeries) == 32 && sizeof(PresumUnit) == 32, "read as two int4 by the pre-pass");
 
 struct PresumTables {
   std::vector<PresumSeries> series;
@@ -153,7 +157,7 @@ int presum_chunk(const sps_dedisp_config& cfg);  // units staged per chunk
 int64_t count_presum_series(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t K);
 int32_t presum_stage_data(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t K, int32_t Di,
                           int32_t units_per_chunk, int32_t Tt);
-sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per,
+sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t n_out,
                                const sps_dedisp_config& cfg, PresumTables* out);
 bool u8_config_supported(const sps_dedisp_config& cfg, std::string* why);
 bool step2_config_supported(const sps_dedisp_config& cfg, std::string* why);
