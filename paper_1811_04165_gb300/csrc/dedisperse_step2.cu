@@ -13,8 +13,9 @@
 // by one sample) keep every load aligned: copy 0 arrives by bulk asynchronous
 // copy (TMA), copy 1 is built from it in shared memory.  Chunks of subbands
 // run through two stages: while the block computes one chunk, the next one's
-// copies land.  Lanes are folded into int32 every `flush_every` subbands,
-// before a 16-bit lane could overflow.
+// copies land.  The staged offset of every (trial, subband) of the tile is
+// computed once, before the first chunk.  Lanes are folded into int32 every
+// `flush_every` subbands, before a 16-bit lane could overflow.
 #include <algorithm>
 
 #include "sps_internal.h"
@@ -32,15 +33,17 @@ step2_kernel(Step2Args a, int wd, int cs_max, int wb) {
   const int Di = wd * ND;
   const int wt = (int)(blockDim.x >> 5) / wd;
   const int Tt = wt * 64 * NW;
-  const int copy_stride = cs_max * wb;                       // one copy of a chunk's windows
-  const int stage_bytes = 2 * copy_stride + (Di * cs_max * 4 + 15) / 16 * 16;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);
+  const int S = a.n_subbands;
+  const int copy_stride = cs_max * wb;  // one copy of a chunk's windows
+  const int stage_bytes = 2 * copy_stride;
+  // after the two stages: the offset table [Di][S] and two barriers
+  uint32_t* tbl = reinterpret_cast<uint32_t*>(smem + 2 * stage_bytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes + (Di * S * 4 + 15) / 16 * 16);
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = (int)(blockDim.x >> 5);
   const int dm_sub = warp % wd, t_sub = warp / wd;
   const int t0 = blockIdx.x * Tt;
   const int k = a.tiles[3 * blockIdx.y], ib = a.tiles[3 * blockIdx.y + 1], nd = a.tiles[3 * blockIdx.y + 2];
-  const int S = a.n_subbands;
   const int n_chunks = (S + cs_max - 1) / cs_max;
   const uint32_t toff = (uint32_t)(t_sub * 128 * NW + lane * 4);  // bytes
   const int32_t* d2row0 = a.d2 + (int64_t)ib * S;
@@ -94,12 +97,23 @@ step2_kernel(Step2Args a, int wd, int cs_max, int wb) {
   };
 
   if (warp == 0) issue(0);
+  // while chunk 0 lands: the staged offset of every (trial, subband).  Window
+  // start of subband s = the tile's first trial's delay rounded down to 8
+  // samples; a trial's offset = its copy (parity of rel), the subband's slot in
+  // the chunk, and its even sample offset inside the window.
+  for (int e = tid; e < Di * S; e += blockDim.x) {
+    const int r = e / S, s = e - r * S;
+    const int i = ib + min(r, nd - 1);
+    const int start = (t0 + __ldg(&d2row0[s])) & ~7;
+    const int rel = t0 + __ldg(&a.d2[(int64_t)i * S + s]) - start;  // elements
+    tbl[e] = (uint32_t)((rel & 1) * copy_stride + (s % cs_max) * wb + 2 * (rel & ~1));
+  }
+  __syncthreads();
   int pending = 0;
   const int wwords = wb >> 2;
   for (int c = 0; c < n_chunks; c++) {
     const int st = c & 1, sb = c * cs_max, cs = min(cs_max, S - sb);
     uint8_t* stage = smem + st * stage_bytes;
-    uint32_t* tbl = reinterpret_cast<uint32_t*>(stage + 2 * copy_stride);
     const bool ok = mbar_wait(&full[st], (c >> 1) & 1, a.status);
     if (__syncthreads_or(ok ? 0 : 1)) {
       // this chunk's copies (the only ones issued and not yet waited for) may
@@ -107,30 +121,22 @@ step2_kernel(Step2Args a, int wd, int cs_max, int wb) {
       if (tid == 0) mbar_wait(&full[st], (c >> 1) & 1, nullptr);
       return;
     }
-    // copy 1 = copy 0 one sample later
+    // copy 1 = copy 0 one sample later; a warp per subband window
     const uint32_t* c0 = reinterpret_cast<const uint32_t*>(stage);
     uint32_t* c1 = reinterpret_cast<uint32_t*>(stage + copy_stride);
-    for (int e = tid; e < cs * wwords; e += blockDim.x) {
-      const int j = e % wwords;
-      const uint32_t w0 = c0[e], w1 = j + 1 < wwords ? c0[e + 1] : 0u;
-      c1[e] = __byte_perm(w0, w1, 0x5432);
-    }
-    for (int e = tid; e < Di * cs; e += blockDim.x) {
-      const int r = e / cs, sl = e - r * cs;
-      const int i = ib + min(r, nd - 1);
-      const int s = sb + sl;
-      const int start = (t0 + d2row0[s]) & ~7;
-      const int rel = t0 + a.d2[(int64_t)i * S + s] - start;  // elements
-      tbl[r * cs_max + sl] = (uint32_t)((rel & 1) * copy_stride + sl * wb + 2 * (rel & ~1));
-    }
-    __syncthreads();  // copy 1 and the table are ready; the other stage's chunk is no longer read
+    for (int sl = warp; sl < cs; sl += nwarps)
+      for (int j = lane; j < wwords; j += 32) {
+        const int e = sl * wwords + j;
+        c1[e] = __byte_perm(c0[e], j + 1 < wwords ? c0[e + 1] : 0u, 0x5432);
+      }
+    __syncthreads();  // copy 1 is ready; the other stage's chunk is no longer read
     if (warp == 0 && c + 1 < n_chunks) issue(c + 1);
 
-    const uint32_t* trow = tbl + dm_sub * ND * cs_max;
+    const uint32_t* trow = tbl + dm_sub * ND * S + sb;
     for (int sl = 0; sl < cs; sl++) {
 #pragma unroll
       for (int r = 0; r < ND; r++) {
-        const uint8_t* p = stage + trow[r * cs_max + sl] + toff;
+        const uint8_t* p = stage + trow[r * S + sl] + toff;
 #pragma unroll
         for (int m = 0; m < NW; m++) lanes[r][m] += *reinterpret_cast<const uint32_t*>(p + 128 * m);
       }
@@ -203,10 +209,11 @@ bool step2_config_supported(const sps_dedisp_config& c, std::string* why) {
   return true;
 }
 
-size_t step2_smem_bytes(const sps_dedisp_config& c, int32_t dmax_tile) {
+size_t step2_smem_bytes(const sps_dedisp_config& c, int32_t dmax_tile, int32_t n_subbands) {
   const size_t Di = (size_t)c.warps_dm * c.dms_per_thread;
-  const size_t stage = 2 * (size_t)c.chunk * copy_bytes(c, dmax_tile) + (Di * c.chunk * 4 + 15) / 16 * 16;
-  return 2 * stage + 16;  // two stages and their barriers
+  const size_t stage = 2 * (size_t)c.chunk * copy_bytes(c, dmax_tile);
+  // two stages, the offset table and the barriers
+  return 2 * stage + (Di * n_subbands * 4 + 15) / 16 * 16 + 16;
 }
 
 sps_status launch_step2(const Step2Args& a, const sps_dedisp_config& c, cudaStream_t st) {
@@ -214,7 +221,7 @@ sps_status launch_step2(const Step2Args& a, const sps_dedisp_config& c, cudaStre
   if (!step2_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
   Step2Kernel fn = find(c.dms_per_thread, c.samples_per_thread / 2);
   const int Tt = c.warps_time * 32 * c.samples_per_thread;
-  const size_t smem = step2_smem_bytes(c, a.dmax_tile);
+  const size_t smem = step2_smem_bytes(c, a.dmax_tile, a.n_subbands);
   dim3 grid((a.n_t + Tt - 1) / Tt, a.n_tiles, 1);
   if (grid.y > 65535) return fail(SPS_ERR_UNSUPPORTED, "too many step-two tiles");
   SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

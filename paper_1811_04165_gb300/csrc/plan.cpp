@@ -202,7 +202,7 @@ sps_status check_config(const sps_plan* p, const sps_kernel_config& cfg, ConfigC
             : u8_smem_bytes(cfg.step1, c.dmax_1, p->channels / S);
     if (need1 > (size_t)p->max_smem)
       return fail(SPS_ERR_INVALID_ARG, "step1 config needs more shared memory than a block may use");
-    if (step2_smem_bytes(cfg.step2, c.dmax_2) > (size_t)p->max_smem)
+    if (step2_smem_bytes(cfg.step2, c.dmax_2, p->n_subbands) > (size_t)p->max_smem)
       return fail(SPS_ERR_INVALID_ARG, "step2 config needs more shared memory than a block may use");
   }
   if (out) *out = std::move(c);

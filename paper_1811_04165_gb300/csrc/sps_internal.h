@@ -165,7 +165,7 @@ bool snr_config_supported(const sps_snr_config& cfg, std::string* why);
 size_t u8_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile, int32_t group_channels);
 int u8_window_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
 int u8_di_pad(const sps_dedisp_config& cfg);
-size_t step2_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
+size_t step2_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile, int32_t n_subbands);
 
 // Workspace a plan's de-dispersion needs, and de-dispersion into a given
 // workspace (abi.cpp); used by entry points that supply their own workspace.
