@@ -107,7 +107,7 @@ def main(argv=None):
             res["real_time"][f"{n}/{mode}"] = run(plans[:n], host_x, DEADLINE_S, a.duration, inflight, seed=n,
                                                   budget=budget)
     capacity = {}
-    for period in (0.256, 0.128, 0.064, 0.032, 0.016):
+    for period in (0.256, 0.128, 0.112, 0.096, 0.085, 0.075, 0.064, 0.032):
         emulated = int(round(96 * DEADLINE_S / period))
         for mode, inflight in (("served", 8), ("per_beam", 1)):
             r = run(plans, host_x, period, a.duration * period / DEADLINE_S * 4, inflight, seed=emulated,

@@ -172,6 +172,44 @@ def test_brute_saturated_and_edges(lib):
     assert _to_np(D1).tolist() == [[201]]
 
 
+@pytest.mark.parametrize("cfg", [(4, 16, 8, 1, 16, 0), (4, 16, 8, 1, 8, 1), (4, 16, 8, 1, 16, 2)])
+def test_brute_4096_channels(lib, cfg):
+    """A LOFAR-sized band of 4096 channels: sixteen 16-bit folds for single
+    channels, 32 for pairs, 16 for quads per row, ragged time tail."""
+    torch = _torch()
+    dms = synth.dm_grid(24, 0.25)
+    p = lib.Plan(4096, 1100.0, 1500.0, 65.536e-6, 601, dms, [1, 4, 16])
+    c = p.config
+    c.brute = lib.DedispConfig(*cfg)
+    p.config = c
+    x = synth.filterbank(4096, 1100.0, 1500.0, 65.536e-6, p.input_samples, 41, pitch=p.pitch)
+    out = p.search(torch.from_numpy(x).cuda(), workspace=p.workspace())
+    torch.cuda.synchronize()
+    want = oracle.dedisperse(x, oracle.delay_table(1100.0, 1500.0, 4096, 65.536e-6, dms), 601)
+    assert np.array_equal(_to_np(out["D"]), want)
+    s, pt, pv = oracle.snr(want, [1, 4, 16])
+    _check_snr(_to_np(out["snr"]), _to_np(out["peak_t"]), _to_np(out["peak_val"]), s, pt, pv)
+
+
+def test_quads_with_long_relative_delays(lib):
+    """Quads whose channels lie up to 33346 samples apart (100-200 MHz, 10 us
+    samples): too far to stage a unit's rows in shared memory, so the
+    pre-pass reads the rows from global memory."""
+    torch = _torch()
+    dms = np.array([0.0, 1.0, 2.0])
+    p = lib.Plan(8, 100.0, 200.0, 1e-5, 100, dms, [1, 5])
+    c = p.config
+    c.brute = lib.DedispConfig(1, 4, 1, 1, 4, 2)  # one trial per tile: no delay spread inside a tile
+    p.config = c
+    x = synth.filterbank(8, 100.0, 200.0, 1e-5, p.input_samples, 77, pitch=p.pitch)
+    D = torch.full((3, 100), -7, dtype=torch.int32, device="cuda")
+    lib.sps_dedisperse(p, torch.from_numpy(x).cuda(), D, workspace=p.workspace())
+    torch.cuda.synchronize()
+    d = oracle.delay_table(100.0, 200.0, 8, 1e-5, dms)
+    assert int(d[2, 0] - d[2, 3]) == 33346
+    assert np.array_equal(_to_np(D), oracle.dedisperse(x, d, 100))
+
+
 @pytest.mark.parametrize("presum", [0, 1, 2])
 def test_apertif_brute_sampled_rows(lib, presum):
     """Full Apertif-shaped beam in the launch configurations the benchmark times."""
