@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kMaxThreads, FAST ? 2 : 1) snr_kernel(SnrArgs 
   extern __shared__ __align__(16) uint32_t buf[];
   __shared__ uint32_t scratch[32];
   __shared__ uint64_t bar;
-  __shared__ Moments part[32][NWP];
+  __shared__ Moments part[kMaxThreads / 32][NWP];  // one entry per warp and width
   __shared__ int gmax[NWP], first[NWP];
   const int i = blockIdx.x;
   const int n_t = a.n_t;
@@ -424,7 +424,7 @@ SnrKernel snr_variant(int nwp) {
 sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st) {
   std::string why;
   if (!snr_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
-  if (sps_status s = check_row_fits(a.n_t, sizeof(Moments) * 32 * kWidthsPerPass + 512)) return s;
+  if (sps_status s = check_row_fits(a.n_t, sizeof(Moments) * (kMaxThreads / 32) * kWidthsPerPass + 512)) return s;
   // largest boxcar value: 255 * channels * widest width (< 2^31, checked by the plan);
   // a thread's 64-bit S2 partial takes `flush` squares before it must be flushed
   const unsigned long long bmax = std::max<unsigned long long>(1ull, (unsigned long long)a.max_boxcar);
