@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dms", type=int, default=2048,
                     help="DM trials (fewer only for small profiling cases; bench lines use 2048)")
+    ap.add_argument("--presum", type=int, choices=[0, 1, 2], default=None,
+                    help="brute-force kernel: 0 single channels, 1 pairs, 2 quads (default: the plan's default)")
     return ap.parse_args()
 
 
@@ -370,6 +372,10 @@ def main():
         wl.dms = wl.dms[:args.dms].copy()
         wl.name += f"-first{args.dms}dm"
     plan = sps.Plan.from_workload(wl, mode=sps.MODE_BRUTE)
+    if args.presum is not None:
+        c = plan.config
+        c.brute.presum = args.presum
+        plan.config = c
     pitch = plan.pitch
     n_in = plan.input_samples
     n_batches = 8  # 8 x 26 MB: more input than the 126 MB L2
