@@ -9,12 +9,15 @@
 // Adjacent channels have nearly equal delays, so a tile of consecutive trials
 // needs only a few tuples rel per unit.  A pre-pass writes, for every unit and
 // every tuple its trials need, the series S_rel as uint16 (two copies, the
-// second shifted by one sample, so every 32-bit shared load is aligned); the
-// block then stages, per chunk of units, just the windows of the copies its
-// tile reads (a host-built list, packed) with bulk asynchronous copies (TMA)
-// into a ring of
-// kStages mbarrier-tracked stages.  A 32-bit load holds two samples of a unit sum in 16-bit
-// lanes: one add accumulates 2 K channel-samples, with no unpacking.  Unit sums
+// second shifted by one sample, so every 32-bit shared load is aligned), over
+// the samples those trials read for valid outputs only; the block then
+// stages, per chunk of units, just the windows of the copies its tile reads (a
+// host-built list, packed) with bulk asynchronous copies (TMA) into a ring of
+// kStages mbarrier-tracked stages.  A 32-bit load holds two samples of a unit
+// sum in 16-bit lanes: one add accumulates 2 K channel-samples, with no
+// unpacking.  Samples outside a series' written range reach only output lanes
+// past the end of the row (a lane's carry runs towards later samples), which
+// are never stored.  Unit sums
 // are <= 255 K, so 16-bit lanes are exact for 65535 / (255 K) units (128 pairs,
 // 64 quads); partial sums fold into int32 registers that often.  A group whose
 // size is not a multiple of K ends in a shorter unit.
