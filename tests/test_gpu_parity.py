@@ -116,6 +116,28 @@ def test_brute_configs_ragged(lib, cfg):
     assert np.array_equal(_to_np(D), want)
 
 
+@pytest.mark.parametrize("fill", [0x00, 0xFF, 0x5A])
+@pytest.mark.parametrize("presum", [1, 2])
+def test_presum_ignores_stale_workspace(lib, fill, presum):
+    """The pre-pass writes each series only over the samples its trials read
+    for valid outputs; whatever the workspace held elsewhere must not reach an
+    output (odd N_t: the last valid sample shares a 32-bit word with one that
+    is not)."""
+    torch = _torch()
+    dms = synth.dm_grid(29, 0.31)
+    p = lib.Plan(40, 1300.0, 1500.0, 65.536e-6, 1003, dms, [1, 3])
+    c = p.config
+    c.brute = lib.DedispConfig(4, 8, 2, 2, 12, presum)
+    p.config = c
+    x = synth.filterbank(40, 1300.0, 1500.0, 65.536e-6, p.input_samples, 13, pitch=p.pitch)
+    ws = torch.full((p.workspace_bytes,), fill, dtype=torch.uint8, device="cuda")
+    D = torch.full((29, 1003), -7, dtype=torch.int32, device="cuda")
+    lib.sps_dedisperse(p, torch.from_numpy(x).cuda(), D, workspace=ws)
+    torch.cuda.synchronize()
+    want = oracle.dedisperse(x, oracle.delay_table(1300.0, 1500.0, 40, 65.536e-6, dms), 1003)
+    assert np.array_equal(_to_np(D), want)
+
+
 @pytest.mark.parametrize("C", [38, 39, 40])
 @pytest.mark.parametrize("cfg", [(1, 4, 1, 1, 2, 2), (4, 8, 2, 2, 12, 2)])
 def test_quads_short_last_unit(lib, C, cfg):
@@ -306,6 +328,28 @@ def test_subband_configs(lib, cfg1, cfg2):
     lib.sps_dedisperse(p, torch.from_numpy(x).cuda(), D, workspace=p.workspace())
     torch.cuda.synchronize()
     assert np.array_equal(_to_np(D), oracle.dedisperse(x, p.delay_table(), wl.n_t))
+    d1, d2 = oracle.subband_tables(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, 8, wl.coarse_dms, wl.dms)
+    n_1, _ = oracle.subband_lengths(wl.n_t, d1, d2)
+    Do = oracle.subband_step2(oracle.subband_step1(x, d1, 8, n_1), d2,
+                              oracle.coarse_index(wl.dms.size, wl.coarse_dms.size), wl.n_t)
+    assert np.array_equal(_to_np(D), Do)
+
+
+@pytest.mark.parametrize("presum", [1, 2])
+def test_subband_presum_ignores_stale_workspace(lib, presum):
+    """Step one over pre-summed series (range-limited, N_1 outputs per row)
+    with a workspace full of 0xFF bytes."""
+    torch = _torch()
+    wl = _small_subband(8, n_dms=40, n_coarse=5, C=64, n_t=1001)
+    p = lib.Plan.from_workload(wl)
+    c = p.config
+    c.step1 = lib.DedispConfig(1, 4, 1, 1, 2, presum)
+    p.config = c
+    x = _x_for(p, wl)
+    ws = torch.full((p.workspace_bytes,), 0xFF, dtype=torch.uint8, device="cuda")
+    D = torch.full((wl.dms.size, wl.n_t), -7, dtype=torch.int32, device="cuda")
+    lib.sps_dedisperse(p, torch.from_numpy(x).cuda(), D, workspace=ws)
+    torch.cuda.synchronize()
     d1, d2 = oracle.subband_tables(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, 8, wl.coarse_dms, wl.dms)
     n_1, _ = oracle.subband_lengths(wl.n_t, d1, d2)
     Do = oracle.subband_step2(oracle.subband_step1(x, d1, 8, n_1), d2,
