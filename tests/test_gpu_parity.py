@@ -417,6 +417,33 @@ def test_integrate_and_snr_exact(lib):
     assert np.all(_to_np(out["snr"])[:, 3] == 0.0)
 
 
+@pytest.mark.parametrize("threads", [32, 256, 512])
+def test_snr_fast_form_long_widths(lib, threads):
+    """Few channels keep every boxcar small, so the fast form (64-bit partials,
+    no flushes) serves widths up to the whole row: threads whose samples end past
+    some widths' last valid start, a width with a single valid start."""
+    torch = _torch()
+    rng = np.random.Generator(np.random.PCG64(threads + 7))
+    n_dms, n_t, widths = 11, 1001, [1, 5, 300, 997, 1001]
+    p = lib.Plan(8, 1250.0, 1550.0, 81.92e-6, n_t, synth.dm_grid(n_dms, 1.0), widths)
+    c = p.config
+    c.snr = lib.SnrConfig(threads)
+    p.config = c
+    D = rng.integers(0, 255 * 8 + 1, (n_dms, n_t)).astype(np.int32)
+    D[1] = 255 * 8          # constant at the largest value: S/N 0, every sample a maximum
+    D[2] = 0
+    D[2, 1000] = 77         # a spike in the last sample
+    D[3] = 0
+    D[3, 0] = D[3, 1] = 5   # two in the first samples (a lower S/N: no tie with row 2 for the detection)
+    out = p.alloc_outputs()
+    lib.sps_snr(p, torch.from_numpy(D).cuda(), out["snr"], out["peak_t"], out["peak_val"], out["best"])
+    torch.cuda.synchronize()
+    s, pt, pv = oracle.snr(D, widths)
+    _check_snr(_to_np(out["snr"]), _to_np(out["peak_t"]), _to_np(out["peak_val"]), s, pt, pv)
+    bi, bw = oracle.detect(s)
+    assert _to_np(out["best"]).tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])]
+
+
 @pytest.mark.parametrize("threads", [32, 96, 256, 512])
 def test_snr_thread_counts(lib, threads):
     torch = _torch()
