@@ -403,6 +403,15 @@ sps_status sps_server_destroy(sps_server* server);
  * Returns TIMEOUT when it is non-zero. */
 sps_status sps_plan_status(const sps_plan* plan, uint32_t* host_status, int32_t clear);
 
+/* Failure-detection self-check (the paper has no counterpart): launches on
+ * `stream` one block that waits, through the same bounded mbarrier wait every
+ * kernel uses, on a barrier nothing arrives at, for at most `polls` polls
+ * (1 .. 2^20).  The wait runs out, sets the timeout bit of the plan's status
+ * word (read it with sps_plan_status) and the block returns normally: no
+ * fault, the context stays usable.  Asynchronous; INVALID_ARG on a null plan
+ * or polls out of range. */
+sps_status sps_plan_check_wait_timeout(const sps_plan* plan, int32_t polls, void* stream);
+
 /* Measures the device's 32-bit integer add rate (adds/s over all SMs: independent
  * add chains split between the ALU pipe and multiply-adds by one on the FMA
  * pipe, best of three timed runs), the denominator against which the

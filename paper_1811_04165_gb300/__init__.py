@@ -479,6 +479,12 @@ class Server:
             self.handle = None
 
 
+def sps_plan_check_wait_timeout(plan, polls=1000, stream=None):
+    """Launch the failure-detection self-check: a bounded wait that runs out and
+    sets the plan's status word (see Plan.status)."""
+    check(_L.sps_plan_check_wait_timeout(plan.handle, int(polls), _stream(stream)), "sps_plan_check_wait_timeout")
+
+
 def sps_measure_int_add_rate(stream=None) -> float:
     """The device's measured 32-bit integer add rate, adds/s."""
     v = ctypes.c_double()

@@ -61,12 +61,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for phase `parity` of `bar`; false (and the status bit set) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
-  for (uint32_t i = 0; i < kMaxPolls; i++)
+// Wait for phase `parity` of `bar` for at most `polls` polls; false (and the
+// status bit set) when it runs out.
+__device__ __forceinline__ bool mbar_wait_polls(uint64_t* bar, uint32_t parity, uint32_t* status, uint32_t polls) {
+  for (uint32_t i = 0; i < polls; i++)
     if (mbar_try_wait(bar, parity)) return true;
   if (status) atomicOr(status, kStatusWaitTimeout);
   return false;
+}
+
+// Bounded wait for phase `parity` of `bar`; false (and the status bit set) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
+  return mbar_wait_polls(bar, parity, status, kMaxPolls);
 }
 
 }  // namespace sps

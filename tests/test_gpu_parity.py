@@ -518,6 +518,29 @@ def test_argument_errors(lib):
     assert p.status() == 0  # no kernel's bounded wait ran out
 
 
+def test_bounded_wait_runs_out_and_reports(lib):
+    """Failure detection without a fault: a wait on an mbarrier that nothing
+    arrives at gives up after its poll bound, sets the plan's status word, and
+    the context still serves a correct search afterwards."""
+    torch = _torch()
+    wl = synth.tiny_brute()
+    p = lib.Plan.from_workload(wl)
+    assert p.status() == 0
+    lib.sps_plan_check_wait_timeout(p, polls=1000)
+    torch.cuda.synchronize()
+    assert p.status(clear=False) == 1          # kStatusWaitTimeout, read without clearing
+    assert p.status() == 1                     # read and cleared
+    assert p.status() == 0
+    with pytest.raises(lib.SpsError):
+        lib.sps_plan_check_wait_timeout(p, polls=0)
+    x = _x_for(p, wl)
+    out = p.search(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    want = oracle.dedisperse(x, oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms), wl.n_t)
+    assert np.array_equal(_to_np(out["D"]), want)
+    assert p.status() == 0
+
+
 def test_int_add_rate_is_plausible(lib):
     """The measured integer add rate (the roofline's measured denominator) lies
     between 1e12 adds/s and 2.5 x the 152 SM x 128 lane x 2.07 GHz unit count."""
