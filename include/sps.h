@@ -252,7 +252,13 @@ sps_status sps_search_host(const sps_plan* plan, const uint8_t* x_host, int64_t 
  * undone when it breaks validity), per-kernel mutation with p_mut to a
  * different valid value, next population = fitter half of parents + fitter
  * half of offspring.  The evaluation budget counts distinct individuals;
- * repeats are served from a cache. */
+ * repeats are served from a cache.
+ * Resume (checkpoint of the best per generation, Sec. 4): `known_points` /
+ * `known_fitness` hold n_known earlier evaluations (a tuning log); a point
+ * found there takes the logged fitness instead of being measured, and
+ * otherwise counts and traces like a new evaluation.  Since a search is
+ * reproducible draw for draw, re-running it with its own log replays the
+ * logged evaluations exactly and continues from where the log ends. */
 enum { SPS_TUNE_GA = 0, SPS_TUNE_RANDOM = 1, SPS_TUNE_EXHAUSTIVE = 2 };
 enum { SPS_CROSS_UNIFORM = 0, SPS_CROSS_ONE_POINT = 1 };
 enum { SPS_SPACE_FULL = 0, SPS_SPACE_REDUCED = 1 };
@@ -274,6 +280,9 @@ typedef struct {
   double pool_fraction;      /* tournament pool as a fraction of N_pop (GA)        */
   int64_t max_evaluations;   /* budget of distinct evaluations (GA, random)        */
   uint64_t seed;
+  const int32_t* known_points;  /* host [n_known][n_genes] or NULL (resume)        */
+  const double* known_fitness;  /* host [n_known] or NULL                          */
+  int64_t n_known;              /* 0 = nothing known                               */
 } sps_search_desc;
 
 typedef struct {

@@ -257,6 +257,7 @@ class Plan:
         self.mode = int(mode)
         self.n_subbands = int(n_subbands)
         self.n_coarse = 0 if coarse_dms is None else len(coarse_dms)
+        self.f_lo, self.f_hi, self.t_samp = float(f_lo_mhz), float(f_hi_mhz), float(t_samp_s)
 
     @classmethod
     def from_workload(cls, wl, mode=None):
@@ -337,6 +338,43 @@ class Plan:
     @config.setter
     def config(self, c: KernelConfig):
         check(_L.sps_plan_set_config(self.handle, ctypes.byref(c)), "sps_plan_set_config")
+
+    def shape_key(self) -> dict:
+        """What a tuned configuration depends on: the band, sampling, DM grid and
+        widths, mode and subbands (the key of a saved configuration)."""
+        return {"channels": self.channels, "f_lo_mhz": self.f_lo, "f_hi_mhz": self.f_hi, "t_samp_s": self.t_samp,
+                "n_samples": self.n_samples, "n_dms": self.n_dms, "dm_first": float(self.dms[0]),
+                "dm_last": float(self.dms[-1]), "widths": [int(w) for w in self.widths], "mode": self.mode,
+                "n_subbands": self.n_subbands, "n_coarse": self.n_coarse, "smoothing": self.smoothing}
+
+    def save_config(self, path):
+        """Write the kernel configuration as JSON keyed by the GPU's name and the
+        plan's shape (e.g. after sps_tune)."""
+        import json
+        import torch
+        rec = {"gpu": torch.cuda.get_device_name(), "plan": self.shape_key(), "config": self.config.as_dict()}
+        with open(path, "w") as f:
+            json.dump(rec, f, indent=1)
+
+    def load_config(self, path, strict=True):
+        """Apply a configuration written by save_config.  With `strict`, one saved
+        for another GPU or another plan shape is refused (ValueError); the
+        library still checks the configuration itself (SpsError)."""
+        import json
+        import torch
+        with open(path) as f:
+            rec = json.load(f)
+        if strict:
+            if rec.get("gpu") != torch.cuda.get_device_name():
+                raise ValueError(f"configuration saved for {rec.get('gpu')!r}")
+            if rec.get("plan") != self.shape_key():
+                raise ValueError("configuration saved for another plan shape")
+        cfg = rec["config"]
+        c = KernelConfig()
+        for k in ("brute", "step1", "step2"):
+            setattr(c, k, DedispConfig(*cfg[k]))
+        c.snr = SnrConfig(*cfg["snr"])
+        self.config = c
 
     # convenience wrappers allocating outputs
     def alloc_outputs(self):
@@ -520,7 +558,8 @@ class SpaceDesc(ctypes.Structure):
 class SearchDesc(ctypes.Structure):
     _fields_ = [("algorithm", ctypes.c_int32), ("crossover", ctypes.c_int32), ("population", ctypes.c_int32),
                 ("max_generations", ctypes.c_int32), ("p_cross", ctypes.c_double), ("p_mut", ctypes.c_double),
-                ("pool_fraction", ctypes.c_double), ("max_evaluations", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+                ("pool_fraction", ctypes.c_double), ("max_evaluations", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("known_points", ctypes.c_void_p), ("known_fitness", ctypes.c_void_p), ("n_known", ctypes.c_int64)]
 
 
 class SearchResult(ctypes.Structure):
@@ -529,15 +568,72 @@ class SearchResult(ctypes.Structure):
 
 
 def search_desc(algorithm=TUNE_GA, population=32, p_cross=0.8, p_mut=0.1, pool_fraction=0.2,
-                crossover=CROSS_UNIFORM, max_evaluations=500, max_generations=1000, seed=1) -> SearchDesc:
-    return SearchDesc(int(algorithm), int(crossover), int(population), int(max_generations), float(p_cross),
-                      float(p_mut), float(pool_fraction), int(max_evaluations), int(seed) & ((1 << 64) - 1))
+                crossover=CROSS_UNIFORM, max_evaluations=500, max_generations=1000, seed=1,
+                known=None) -> SearchDesc:
+    """Search descriptor.  `known`: earlier evaluations [(point, fitness), ...]
+    (e.g. read_tuning_log) served instead of measuring them: a search re-run
+    with the same settings replays its log and continues (resume)."""
+    d = SearchDesc(int(algorithm), int(crossover), int(population), int(max_generations), float(p_cross),
+                   float(p_mut), float(pool_fraction), int(max_evaluations), int(seed) & ((1 << 64) - 1))
+    if known:
+        pts = np.ascontiguousarray([list(p) for p, _ in known], np.int32)
+        fit = np.ascontiguousarray([float(f) for _, f in known], np.float64)
+        d._known_arrays = (pts, fit)  # kept alive with the descriptor
+        d.known_points, d.known_fitness, d.n_known = pts.ctypes.data, fit.ctypes.data, len(known)
+    return d
 
 
-def sps_optimize(n_values, kernel_of, fitness, valid=None, desc: SearchDesc | None = None):
+class TuningLog:
+    """JSON-lines log of a search: one line per distinct evaluation
+    {"eval", "point", "fitness"} (fitness null for +inf), flushed as it goes so
+    that an interrupted search leaves a usable log, and a closing line
+    {"best", "fitness", "evaluations", "generations"[, "config"]}."""
+
+    def __init__(self, path):
+        import json
+        self._json = json
+        self.f = open(path, "w") if path else None
+
+    def evaluation(self, i, point, fitness):
+        if self.f:
+            f = None if not np.isfinite(fitness) else float(fitness)
+            self.f.write(self._json.dumps({"eval": int(i), "point": [int(v) for v in point], "fitness": f}) + "\n")
+            self.f.flush()
+
+    def close(self, best, res, config=None):
+        if self.f:
+            line = {"best": [int(v) for v in best], "fitness": float(res.best_fitness),
+                    "evaluations": int(res.evaluations), "generations": int(res.generations)}
+            if config is not None:
+                line["config"] = config
+            self.f.write(self._json.dumps(line) + "\n")
+            self.f.close()
+            self.f = None
+
+
+def read_tuning_log(path):
+    """The evaluations of a tuning log as [(point, fitness)], in order (+inf for
+    a logged failure); the closing line, if the search finished, is skipped."""
+    import json
+    out = []
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if not line:
+                continue
+            try:
+                rec = json.loads(line)
+            except ValueError:  # a line cut by an interruption
+                break
+            if "eval" in rec:
+                out.append((tuple(rec["point"]), float("inf") if rec["fitness"] is None else float(rec["fitness"])))
+    return out
+
+
+def sps_optimize(n_values, kernel_of, fitness, valid=None, desc: SearchDesc | None = None, log=None):
     """Host-only GA / random / exhaustive search with Python callbacks.
     Returns (best_point, SearchResult, trace) where trace lists (point, fitness)
-    per distinct evaluation, in order."""
+    per distinct evaluation, in order; `log` names a JSON-lines tuning log to write."""
     nv = np.ascontiguousarray(n_values, np.int32)
     ko = np.ascontiguousarray(kernel_of, np.int32)
     sp = SpaceDesc(nv.size, nv.ctypes.data, ko.ctypes.data)
@@ -562,8 +658,11 @@ def sps_optimize(n_values, kernel_of, fitness, valid=None, desc: SearchDesc | No
             errors.append(e)
             return 0
 
+    lg = TuningLog(log)
+
     def _tr(i, ptr, f, _):
         trace.append((_pt(ptr), f))
+        lg.evaluation(i, trace[-1][0], f)
 
     cf, cv, ct = _FITNESS_FN(_fit), _VALID_FN(_val) if valid else None, _TRACE_FN(_tr)
     best = np.zeros(n, np.int32)
@@ -572,6 +671,7 @@ def sps_optimize(n_values, kernel_of, fitness, valid=None, desc: SearchDesc | No
     if errors:
         raise errors[0]
     check(st, "sps_optimize")
+    lg.close(best, res)
     return tuple(int(v) for v in best), res, trace
 
 
@@ -595,18 +695,21 @@ def sps_tune_config(plan, which, point) -> KernelConfig:
 
 
 def sps_tune(plan, x, which=SPACE_FULL, desc: SearchDesc | None = None, reps=3, limit_ms=0.0, out=None,
-             workspace=None, stream=None):
+             workspace=None, stream=None, log=None):
     """Live tuning of the plan's kernels on input x; leaves the plan on the best
-    configuration.  Returns (best_point, SearchResult, trace)."""
+    configuration.  Returns (best_point, SearchResult, trace).  `log` names a
+    JSON-lines tuning log (resume with search_desc(known=read_tuning_log(path)))."""
     t = _torch()
     out = out or plan.alloc_outputs()
     if workspace is None:
         workspace = plan.workspace()
     n = int(sps_tune_space(plan, which)[0].size)
     trace = []
+    lg = TuningLog(log)
 
     def _tr(i, ptr, f, _):
         trace.append((tuple(ptr[g] for g in range(n)), f))
+        lg.evaluation(i, trace[-1][0], f)
 
     ct = _TRACE_FN(_tr)
     best = np.zeros(n, np.int32)
@@ -619,4 +722,5 @@ def sps_tune(plan, x, which=SPACE_FULL, desc: SearchDesc | None = None, reps=3, 
                       _dev(out["snr"], t.float64, "snr", shp), _dev(out["peak_t"], t.int32, "peak_t", shp),
                       _dev(out["peak_val"], t.int32, "peak_val", shp), int(reps), float(limit_ms), ct, None,
                       best.ctypes.data, ctypes.byref(res), _stream(stream)), "sps_tune")
+    lg.close(best, res, plan.config.as_dict())
     return tuple(int(v) for v in best), res, trace

@@ -67,6 +67,7 @@ struct Problem {
   std::function<double(const Point&)> fitness;
   std::function<void(int64_t, const Point&, double)> trace;
   std::function<void(int32_t, int64_t, double, const Point&)> progress;
+  std::map<Point, double> known;  // logged evaluations served instead of measuring (resume)
 };
 
 class Evaluator {
@@ -76,7 +77,8 @@ class Evaluator {
     auto it = cache_.find(p);
     if (it != cache_.end()) return it->second;
     if (budget_ >= 0 && count_ >= budget_) return kInf;
-    double f = pr_.fitness(p);
+    const auto k = pr_.known.find(p);
+    double f = k != pr_.known.end() ? k->second : pr_.fitness(p);
     if (std::isnan(f)) f = kInf;
     cache_.emplace(p, f);
     if (pr_.trace) pr_.trace(count_, p, f);
@@ -264,8 +266,17 @@ sps_status run_exhaustive(const Problem& pr, Point* best, sps_search_result* res
   return SPS_OK;
 }
 
-sps_status run_problem(const Problem& pr, const sps_search_desc* d, int32_t* best_point, sps_search_result* res) {
+sps_status run_problem(Problem& pr, const sps_search_desc* d, int32_t* best_point, sps_search_result* res) {
   if (!d || !best_point || !res) return fail(SPS_ERR_INVALID_ARG, "null argument");
+  if (d->n_known < 0 || (d->n_known > 0 && (!d->known_points || !d->known_fitness)))
+    return fail(SPS_ERR_INVALID_ARG, "known evaluations: n_known < 0 or null arrays");
+  const size_t n_genes = pr.n_values.size();
+  for (int64_t k = 0; k < d->n_known; k++) {
+    Point p(d->known_points + k * n_genes, d->known_points + (k + 1) * n_genes);
+    for (size_t g = 0; g < n_genes; g++)
+      if (p[g] < 0 || p[g] >= pr.n_values[g]) return fail(SPS_ERR_INVALID_ARG, "known point out of the space");
+    pr.known.emplace(std::move(p), d->known_fitness[k]);
+  }
   Point best;
   sps_status s;
   switch (d->algorithm) {

@@ -97,3 +97,44 @@ def test_exhaustive_reduced_space_and_ga_on_its_table(lib):
     b, r, _ = lib.sps_optimize(nv, ko, table.__getitem__, None,
                                lib.search_desc(population=32, max_evaluations=500, seed=0))
     assert r.best_fitness == ga_best[0]
+
+
+def test_live_tuning_log_resume_and_saved_config(lib, tmp_path):
+    """A live GA writes its JSON-lines log; re-run with the log as known
+    evaluations it replays them unmeasured (identical fitness values) and goes
+    on; the tuned configuration saved as JSON loads into a plan of the same
+    shape and is refused for another shape."""
+    import json
+    wl = tiny_subband()
+    p, x = _setup(lib, wl)
+    log1 = tmp_path / "live.jsonl"
+    b1, r1, t1 = lib.sps_tune(p, x, which=lib.SPACE_REDUCED, reps=1, log=str(log1),
+                              desc=lib.search_desc(max_evaluations=12, seed=3))
+    known = lib.read_tuning_log(str(log1))
+    assert known == t1 and r1.evaluations == len(t1)
+    closing = json.loads(log1.read_text().splitlines()[-1])
+    assert tuple(closing["best"]) == b1
+    assert closing["config"] == {k: list(v) for k, v in p.config.as_dict().items()}
+    b2, r2, t2 = lib.sps_tune(p, x, which=lib.SPACE_REDUCED, reps=1,
+                              desc=lib.search_desc(max_evaluations=24, seed=3, known=known))
+    assert t2[:len(known)] == known  # replayed from the log, not measured again
+    assert r2.evaluations >= r1.evaluations and r2.best_fitness <= r1.best_fitness
+    out = p.search(x)  # the plan is left on the best configuration and stays exact
+    D = out["D"].cpu().numpy()
+    xh = x.cpu().numpy()
+    import oracle
+    d1, d2 = oracle.subband_tables(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, 8, wl.coarse_dms, wl.dms)
+    n_1, _ = oracle.subband_lengths(wl.n_t, d1, d2)
+    want = oracle.subband_step2(oracle.subband_step1(xh, d1, 8, n_1), d2,
+                                oracle.coarse_index(wl.dms.size, wl.coarse_dms.size), wl.n_t)
+    assert np.array_equal(D, want)
+    cfg = tmp_path / "tuned.json"
+    p.save_config(str(cfg))
+    q, _ = _setup(lib, tiny_subband())
+    q.load_config(str(cfg))
+    assert q.config.as_dict() == p.config.as_dict()
+    other_wl = tiny_subband()
+    other_wl.n_t = 2048
+    other, _ = _setup(lib, other_wl)
+    with pytest.raises(ValueError):
+        other.load_config(str(cfg))

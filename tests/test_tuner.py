@@ -199,3 +199,54 @@ def test_tune_study_helpers_on_a_synthetic_table(lib):
     # exhaustive with the whole space as budget finds the optimum
     ex = tune_study._runs(nv, ko, table, lib.TUNE_EXHAUSTIVE, [0], 10 ** 6)
     assert ex == [opt]
+
+
+@pytest.mark.parametrize("algorithm", ["ga", "random", "exhaustive"])
+def test_resume_from_a_tuning_log_replays_then_continues(lib, tmp_path, algorithm):
+    """Checkpoint / resume: a search cut short after 40 evaluations leaves a
+    JSON-lines log; the same search re-run with that log as known evaluations
+    measures only the points beyond it and ends exactly where an uninterrupted
+    run ends."""
+    alg = {"ga": lib.TUNE_GA, "random": lib.TUNE_RANDOM, "exhaustive": lib.TUNE_EXHAUSTIVE}[algorithm]
+    nv, ko = [4, 5, 4, 3, 5], [0, 0, 1, 1, 2]
+    fit, _ = _table_fitness(nv, 21)
+    valid, _ = _validity(nv, 21)
+    budget = 120 if algorithm != "exhaustive" else 10 ** 6
+    full = lib.sps_optimize(nv, ko, fit, valid, lib.search_desc(algorithm=alg, max_evaluations=budget, seed=9))
+    path = str(tmp_path / "tune.jsonl")
+    calls = []
+
+    def counted(p):
+        calls.append(p)
+        return fit(p)
+
+    if algorithm == "exhaustive":  # an exhaustive search cut after 40 evaluations: its log so far
+        lg = lib.TuningLog(path)
+        for i, (p, v) in enumerate(full[2][:40]):
+            lg.evaluation(i, p, v)
+        lg.f.close()
+    else:
+        lib.sps_optimize(nv, ko, counted, valid, lib.search_desc(algorithm=alg, max_evaluations=40, seed=9),
+                         log=path)
+        assert len(calls) == 40
+    known = lib.read_tuning_log(path)
+    assert known == full[2][:40]
+    calls.clear()
+    resumed = lib.sps_optimize(nv, ko, counted, valid,
+                               lib.search_desc(algorithm=alg, max_evaluations=budget, seed=9, known=known),
+                               log=str(tmp_path / "resumed.jsonl"))
+    assert resumed[0] == full[0] and resumed[2] == full[2]
+    assert resumed[1].best_fitness == full[1].best_fitness and resumed[1].evaluations == full[1].evaluations
+    assert len(calls) == len(full[2]) - 40 and set(calls).isdisjoint(p for p, _ in known)
+    # the resumed run's own log is complete: every evaluation, then the closing line
+    assert lib.read_tuning_log(str(tmp_path / "resumed.jsonl")) == full[2]
+
+
+def test_known_evaluations_are_checked(lib):
+    nv, ko = [3, 3], [0, 1]
+    with pytest.raises(lib.SpsError):
+        lib.sps_optimize(nv, ko, lambda p: 1.0, None, lib.search_desc(known=[((3, 0), 1.0)]))  # out of the space
+    d = lib.search_desc()
+    d.n_known = 2  # arrays missing
+    with pytest.raises(lib.SpsError):
+        lib.sps_optimize(nv, ko, lambda p: 1.0, None, d)
