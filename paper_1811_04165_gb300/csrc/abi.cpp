@@ -316,6 +316,7 @@ sps_status sps_plan_set_config(sps_plan* p, const sps_kernel_config* cfg) {
 sps_status sps_dedisperse(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
                           size_t ws_bytes, void* stream) {
   clear_error();
+  NvtxRange nvtx("sps_dedisperse");
   if (sps_status s = check_plan(p)) return s;
   return run_dedisperse(p, x, pitch, D, ws, ws_bytes, (cudaStream_t)stream);
 }
@@ -323,6 +324,7 @@ sps_status sps_dedisperse(const sps_plan* p, const uint8_t* x, int64_t pitch, in
 sps_status sps_subband_step1(const sps_plan* p, const uint8_t* x, int64_t pitch, uint16_t* Y, void* ws,
                              size_t ws_bytes, void* stream) {
   clear_error();
+  NvtxRange nvtx("sps_subband_step1");
   if (sps_status s = check_plan(p)) return s;
   if (p->mode != SPS_MODE_SUBBAND) return fail(SPS_ERR_INVALID_ARG, "plan is not in SUBBAND mode");
   if (sps_status s = check_x(p, x, pitch)) return s;
@@ -335,6 +337,7 @@ sps_status sps_subband_step1(const sps_plan* p, const uint8_t* x, int64_t pitch,
 
 sps_status sps_subband_step2(const sps_plan* p, const uint16_t* Y, int32_t* D, void* stream) {
   clear_error();
+  NvtxRange nvtx("sps_subband_step2");
   if (sps_status s = check_plan(p)) return s;
   if (p->mode != SPS_MODE_SUBBAND) return fail(SPS_ERR_INVALID_ARG, "plan is not in SUBBAND mode");
   if (!Y || !aligned16(Y) || !D || !aligned16(D)) return fail(SPS_ERR_INVALID_ARG, "Y and D must be 16-byte aligned");
@@ -343,6 +346,7 @@ sps_status sps_subband_step2(const sps_plan* p, const uint16_t* Y, int32_t* D, v
 
 sps_status sps_integrate(const sps_plan* p, const int32_t* D, int32_t* B, void* stream) {
   clear_error();
+  NvtxRange nvtx("sps_integrate");
   if (sps_status s = check_plan(p)) return s;
   if (!D || !B) return fail(SPS_ERR_INVALID_ARG, "null pointer");
   return launch_integrate(D, (int32_t)p->dms.size(), p->n_t, p->d_widths, (int32_t)p->widths.size(),
@@ -352,6 +356,7 @@ sps_status sps_integrate(const sps_plan* p, const int32_t* D, int32_t* B, void* 
 sps_status sps_snr(const sps_plan* p, const int32_t* D, double* snr, int32_t* peak_t, int32_t* peak_val,
                    int32_t* best, void* stream) {
   clear_error();
+  NvtxRange nvtx("sps_snr");
   if (sps_status s = check_plan(p)) return s;
   return run_snr(p, D, snr, peak_t, peak_val, best, (cudaStream_t)stream);
 }
@@ -360,6 +365,7 @@ sps_status sps_search(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_
                       size_t ws_bytes, double* snr, int32_t* peak_t, int32_t* peak_val, int32_t* best,
                       void* stream) {
   clear_error();
+  NvtxRange nvtx("sps_search");
   if (sps_status s = check_plan(p)) return s;
   sps_status s = run_dedisperse(p, x, pitch, D, ws, ws_bytes, (cudaStream_t)stream);
   if (s) return s;
@@ -371,6 +377,7 @@ sps_status sps_search_host(const sps_plan* p, const uint8_t* x_host, int64_t pit
                            int32_t* peak_val_dev, int32_t* best_dev, double* snr_host, int32_t* peak_t_host,
                            int32_t* peak_val_host, int32_t* best_host, void* stream) {
   clear_error();
+  NvtxRange nvtx("sps_search_host");
   if (sps_status s = check_plan(p)) return s;
   if (!x_host) return fail(SPS_ERR_INVALID_ARG, "null host input");
   if (sps_status s = check_x(p, x_dev, pitch)) return s;

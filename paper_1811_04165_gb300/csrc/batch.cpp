@@ -164,6 +164,7 @@ sps_status sps_batch_create(const sps_plan* const* plans, const sps_beam_buffers
 
 sps_status sps_batch_launch(sps_batch* batch, void* stream) {
   clear_error();
+  NvtxRange nvtx("sps_batch_launch");
   if (!batch) return fail(SPS_ERR_INVALID_ARG, "null batch");
   for (size_t b = 0; b < batch->plans.size(); b++)
     if (batch->plans[b]->config_gen != batch->gens[b])

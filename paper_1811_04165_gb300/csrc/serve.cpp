@@ -214,6 +214,7 @@ sps_status sps_server_add_beam(sps_server* s, const sps_plan* p, int32_t* beam_i
 sps_status sps_server_submit(sps_server* s, int32_t beam, const uint8_t* host_x, int64_t host_pitch,
                              double* snr_host, int32_t* best_host, uint64_t tag) {
   clear_error();
+  NvtxRange nvtx("sps_server_submit");
   if (!s || !host_x) return fail(SPS_ERR_INVALID_ARG, "null argument");
   if (beam < 0 || beam >= (int32_t)s->beams.size()) return fail(SPS_ERR_INVALID_ARG, "unknown beam");
   if (host_pitch < s->beams[beam].plan->n_t) return fail(SPS_ERR_INVALID_ARG, "host_pitch smaller than N_t");

@@ -11,7 +11,20 @@
 
 #include "../../include/sps.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace sps {
+
+// An NVTX range around a host entry point: profilers that record NVTX (ncu
+// --nvtx, Nsight Systems) see each call and the kernels it launched; without
+// one attached a push and a pop cost a few nanoseconds.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 // Records a message for sps_last_error() and returns the status.
 sps_status fail(sps_status s, const std::string& msg);

@@ -424,6 +424,7 @@ sps_status sps_tune(sps_plan* p, int32_t which, const sps_search_desc* desc, con
                     int32_t* peak_val, int32_t reps, double limit_ms, sps_trace_fn trace, void* user,
                     int32_t* best_point, sps_search_result* result, void* stream) {
   clear_error();
+  NvtxRange nvtx("sps_tune");
   if (!p || !desc || !best_point || !result) return fail(SPS_ERR_INVALID_ARG, "null argument");
   if (reps < 1) return fail(SPS_ERR_INVALID_ARG, "reps must be >= 1");
   cudaStream_t st = (cudaStream_t)stream;
