@@ -283,6 +283,11 @@ typedef struct {
   const int32_t* known_points;  /* host [n_known][n_genes] or NULL (resume)        */
   const double* known_fitness;  /* host [n_known] or NULL                          */
   int64_t n_known;              /* 0 = nothing known                               */
+  int32_t* final_population;    /* host [population][n_genes] or NULL: receives the
+                                   end configurations (Sec. 5): the GA's last
+                                   population; random search's last `population`
+                                   distinct individuals (rows past the evaluation
+                                   count set to -1); untouched by exhaustive search */
 } sps_search_desc;
 
 typedef struct {

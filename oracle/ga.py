@@ -34,7 +34,10 @@ Readings of the paper taken here (the text does not fix them):
     from a cache; once the budget is spent further individuals score +inf;
   * pure random search draws valid individuals until the budget of distinct
     evaluations is spent; exhaustive search evaluates every valid point in
-    lexicographic order (last gene fastest).
+    lexicographic order (last gene fastest);
+  * the end configurations of a run (Sec. 5, coefficient of variation): the
+    GA's last population; for random search, which has no population, its last
+    N_pop distinct evaluated individuals (the last "new random population").
 """
 from __future__ import annotations
 
@@ -96,6 +99,7 @@ class Result:
     generations: int
     trace: list = field(default_factory=list)       # (point, fitness) per distinct evaluation
     history: list = field(default_factory=list)     # (generation, evaluations, best fitness)
+    final_population: list = field(default_factory=list)  # end configurations (Sec. 5)
 
 
 class _Evaluator:
@@ -221,10 +225,11 @@ def genetic(space: Space, fitness, n_pop=32, p_cross=0.8, p_mut=0.1, pool_fracti
         population = [population[j] for j in par_rank] + [offspring[j] for j in off_rank]
         fit = [fit[j] for j in par_rank] + [off_fit[j] for j in off_rank]
         history.append((gen, ev.evaluations, ev.best))
-    return Result(ev.best_point, ev.best, ev.evaluations, gen, ev.trace, history)
+    return Result(ev.best_point, ev.best, ev.evaluations, gen, ev.trace, history,
+                  [tuple(p) for p in population])
 
 
-def random_search(space: Space, fitness, max_evaluations=500, seed=1, max_draws=None) -> Result:
+def random_search(space: Space, fitness, max_evaluations=500, seed=1, max_draws=None, n_pop=32) -> Result:
     """Sec. 4: new random individuals (no genetic operators) until the budget is spent."""
     rng = SplitMix64(seed)
     ev = _Evaluator(fitness, max_evaluations)
@@ -236,7 +241,25 @@ def random_search(space: Space, fitness, max_evaluations=500, seed=1, max_draws=
         if p in ev.cache:
             continue
         ev(p)
-    return Result(ev.best_point, ev.best, ev.evaluations, 0, ev.trace, [(0, ev.evaluations, ev.best)])
+    return Result(ev.best_point, ev.best, ev.evaluations, 0, ev.trace, [(0, ev.evaluations, ev.best)],
+                  [p for p, _ in ev.trace[-n_pop:]])
+
+
+def coefficients_of_variation(end_configurations, values):
+    """Sec. 5: for each gene, c_v = sigma / mu of the parameter's values over a
+    run's end configurations (population standard deviation); None where the
+    mean is zero (the paper leaves such a parameter out).  `values[g]` maps a
+    gene's value index to the parameter value."""
+    out = []
+    for g in range(len(values)):
+        v = [values[g][p[g]] for p in end_configurations]
+        mu = sum(v) / len(v)
+        if mu == 0:
+            out.append(None)
+            continue
+        var = sum((a - mu) ** 2 for a in v) / len(v)
+        out.append(math.sqrt(var) / mu)
+    return out
 
 
 def exhaustive(space: Space, fitness) -> Result:

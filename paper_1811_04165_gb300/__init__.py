@@ -559,7 +559,25 @@ class SearchDesc(ctypes.Structure):
     _fields_ = [("algorithm", ctypes.c_int32), ("crossover", ctypes.c_int32), ("population", ctypes.c_int32),
                 ("max_generations", ctypes.c_int32), ("p_cross", ctypes.c_double), ("p_mut", ctypes.c_double),
                 ("pool_fraction", ctypes.c_double), ("max_evaluations", ctypes.c_int64), ("seed", ctypes.c_uint64),
-                ("known_points", ctypes.c_void_p), ("known_fitness", ctypes.c_void_p), ("n_known", ctypes.c_int64)]
+                ("known_points", ctypes.c_void_p), ("known_fitness", ctypes.c_void_p), ("n_known", ctypes.c_int64),
+                ("final_population", ctypes.c_void_p)]
+
+
+def _with_final_population(desc, n_genes):
+    """A copy of `desc` whose final_population points at a fresh [population][n_genes]
+    array (returned beside it); the caller's descriptor is left as it was."""
+    d = SearchDesc.from_buffer_copy(desc)
+    d._known_arrays = getattr(desc, "_known_arrays", None)
+    fp = np.full((max(1, desc.population), n_genes), -1, np.int32)
+    d.final_population = fp.ctypes.data
+    return d, fp
+
+
+def _end_configurations(fp, algorithm):
+    """Rows of a final_population array that hold individuals (exhaustive search fills none)."""
+    if algorithm == TUNE_EXHAUSTIVE:
+        return []
+    return [tuple(int(v) for v in row) for row in fp if row[0] >= 0]
 
 
 class SearchResult(ctypes.Structure):
@@ -667,10 +685,12 @@ def sps_optimize(n_values, kernel_of, fitness, valid=None, desc: SearchDesc | No
     cf, cv, ct = _FITNESS_FN(_fit), _VALID_FN(_val) if valid else None, _TRACE_FN(_tr)
     best = np.zeros(n, np.int32)
     res = SearchResult()
-    st = _L.sps_optimize(ctypes.byref(sp), ctypes.byref(desc), cv, cf, ct, None, best.ctypes.data, ctypes.byref(res))
+    d, fp = _with_final_population(desc, n)
+    st = _L.sps_optimize(ctypes.byref(sp), ctypes.byref(d), cv, cf, ct, None, best.ctypes.data, ctypes.byref(res))
     if errors:
         raise errors[0]
     check(st, "sps_optimize")
+    res.final_population = _end_configurations(fp, desc.algorithm)
     lg.close(best, res)
     return tuple(int(v) for v in best), res, trace
 
@@ -715,12 +735,15 @@ def sps_tune(plan, x, which=SPACE_FULL, desc: SearchDesc | None = None, reps=3, 
     best = np.zeros(n, np.int32)
     res = SearchResult()
     shp = (plan.n_widths, plan.n_dms)
-    check(_L.sps_tune(plan.handle, int(which), ctypes.byref(desc or search_desc()), _dev(x, t.uint8, "x"),
+    desc = desc or search_desc()
+    d, fp = _with_final_population(desc, n)
+    check(_L.sps_tune(plan.handle, int(which), ctypes.byref(d), _dev(x, t.uint8, "x"),
                       ctypes.c_int64(x.shape[1]), _dev(out["D"], t.int32, "D", (plan.n_dms, plan.n_samples)),
                       _dev(workspace, workspace.dtype, "workspace"),
                       ctypes.c_size_t(workspace.numel() * workspace.element_size()),
                       _dev(out["snr"], t.float64, "snr", shp), _dev(out["peak_t"], t.int32, "peak_t", shp),
                       _dev(out["peak_val"], t.int32, "peak_val", shp), int(reps), float(limit_ms), ct, None,
                       best.ctypes.data, ctypes.byref(res), _stream(stream)), "sps_tune")
+    res.final_population = _end_configurations(fp, desc.algorithm)
     lg.close(best, res, plan.config.as_dict())
     return tuple(int(v) for v in best), res, trace

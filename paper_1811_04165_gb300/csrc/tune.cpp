@@ -219,6 +219,9 @@ sps_status run_genetic(const Problem& pr, const sps_search_desc& d, Point* best,
     fit.swap(nf);
     if (pr.progress) pr.progress(gen, ev.count(), ev.best(), ev.best_point());
   }
+  if (d.final_population)
+    for (int32_t j = 0; j < n; j++)
+      std::copy(pop[j].begin(), pop[j].end(), d.final_population + (size_t)j * pop[j].size());
   *best = ev.best_point();
   res->best_fitness = ev.best();
   res->evaluations = ev.count();
@@ -232,11 +235,24 @@ sps_status run_random(const Problem& pr, const sps_search_desc& d, Point* best, 
   int64_t draws = 0;
   const int64_t limit = 100 * std::max<int64_t>(1, d.max_evaluations);
   Point p;
+  std::vector<Point> drawn;  // distinct individuals in evaluation order
   while (ev.count() < d.max_evaluations && draws < limit) {
     if (!random_valid(pr, rng, &p)) return fail(SPS_ERR_INVALID_ARG, "no valid individual found");
     draws++;
     if (ev.seen(p)) continue;
     ev(p);
+    drawn.push_back(p);
+  }
+  if (d.final_population && d.population > 0) {
+    const size_t ng = pr.n_values.size(), np_ = (size_t)d.population;
+    const size_t first = drawn.size() > np_ ? drawn.size() - np_ : 0;
+    for (size_t j = 0; j < np_; j++) {
+      int32_t* row = d.final_population + j * ng;
+      if (first + j < drawn.size())
+        std::copy(drawn[first + j].begin(), drawn[first + j].end(), row);
+      else
+        std::fill(row, row + ng, -1);
+    }
   }
   if (pr.progress) pr.progress(0, ev.count(), ev.best(), ev.best_point());
   *best = ev.best_point();

@@ -13,7 +13,10 @@
    variation of the best fitness over runs (Sec. 5 reports it for repeated GA
    runs).
 3. Sweeps of p_mut, p_cross, population, crossover kind and budget on the same
-   table (Fig. 3), and a histogram of the GA's best over seeds (Fig. 5).
+   table (Fig. 3), a histogram of the GA's best over seeds (Fig. 5), and the
+   convergence diagnostic of Sec. 5 (Fig. 4): per gene, the coefficient of
+   variation c_v = sigma / mu of the parameter over a run's 20 end
+   configurations, averaged over 30 GA and 30 random-search runs.
 4. One live GA run on the tiny plan, and one on the 1536-channel Apertif beam's
    full brute-force gene space (7 genes), against the library's default
    configuration.
@@ -59,6 +62,36 @@ def _runs(nv, ko, table, algorithm, seeds, budget, **kw):
     return best
 
 
+GENE_NAMES = {0: ("dms_per_thread", "samples_per_thread", "warps_dm", "warps_time", "chunk", "presum"),
+              1: ("dms_per_thread", "samples_per_thread", "warps_dm", "warps_time", "chunk")}
+
+
+def gene_cv(end_configurations, values):
+    """Sec. 5: per gene, sigma / mu of the parameter values over the end
+    configurations (population standard deviation); None for a zero mean."""
+    out = []
+    for g, vals in enumerate(values):
+        v = [float(vals[p[g]]) for p in end_configurations]
+        mu = statistics.fmean(v)
+        out.append(None if mu == 0 else statistics.pstdev(v) / mu)
+    return out
+
+
+def _cv_study(nv, ko, table, values, names, seeds, budget, population=20):
+    """Averaged per-gene c_v of GA and random search (genes with one value left out)."""
+    res_all = {}
+    for name, alg in (("ga", TUNE_GA), ("random", TUNE_RANDOM)):
+        per_run = []
+        for s in seeds:
+            _, res, _ = sps_optimize(nv, ko, table.__getitem__, None,
+                                     search_desc(algorithm=alg, max_evaluations=budget, seed=s,
+                                                 population=population))
+            per_run.append(gene_cv(res.final_population, values))
+        res_all[name] = {names[g]: statistics.fmean(r[g] for r in per_run if r[g] is not None)
+                         for g in range(len(values)) if len(values[g]) > 1}
+    return res_all
+
+
 def _summary(best, opt):
     r = [b / opt for b in best]
     mean = statistics.fmean(best)
@@ -72,7 +105,7 @@ def study_table(seeds, budget, reps):
     wl = tiny_subband()
     plan = Plan.from_workload(wl)
     x = _input(plan, wl)
-    nv, ko, _ = sps_tune_space(plan, SPACE_REDUCED)
+    nv, ko, values = sps_tune_space(plan, SPACE_REDUCED)
     t0 = time.perf_counter()
     _, res, trace = sps_tune(plan, x, which=SPACE_REDUCED, desc=search_desc(algorithm=TUNE_EXHAUSTIVE), reps=reps)
     torch.cuda.synchronize()
@@ -92,6 +125,14 @@ def study_table(seeds, budget, reps):
     edges = [1.0, 1.01, 1.02, 1.05, 1.1, 1.2, 1.5, float("inf")]
     h = np.histogram([b / opt for b in ga], bins=edges)[0]
     out["ga_histogram"] = {f"[{edges[i]:.2f},{edges[i + 1]:.2f})": int(h[i]) for i in range(len(h))}
+    # Fig. 4 analogue: per-gene c_v over 20 end configurations, 30 runs each
+    kernel_names = ("step1", "step2", "snr")
+    names, field = [], {}
+    for g, k in enumerate(ko):
+        j = field.get(k, 0)
+        field[k] = j + 1
+        names.append(f"{kernel_names[k]}.threads" if k == 2 else f"{kernel_names[k]}.{GENE_NAMES[k][j]}")
+    out["gene_cv"] = _cv_study(nv, ko, table, values, names, list(range(30)), budget)
     # Fig. 3 analogue: sweeps on the same table, 20 seeds each
     sw = seeds[:20]
     sweeps = {}

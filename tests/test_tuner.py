@@ -151,6 +151,7 @@ def test_library_ga_matches_oracle_draw_for_draw(lib, seed, crossover, rates, co
     assert trace == [(tuple(p), f) for p, f in want.trace]
     assert best == want.best_point and res.best_fitness == want.best_fitness
     assert (res.evaluations, res.generations) == (want.evaluations, want.generations)
+    assert res.final_population == want.final_population  # the end configurations (Sec. 5)
 
 
 @pytest.mark.parametrize("seed", [1, 8, 99])
@@ -159,10 +160,16 @@ def test_library_random_and_exhaustive_match_oracle(lib, seed):
     kernels = [0, 1, 1, 2]
     fit, _ = _table_fitness(nv, seed)
     valid = _validity(nv, seed)[0]
-    want = ga.random_search(ga.Space(nv, kernels, valid), fit, max_evaluations=40, seed=seed)
+    want = ga.random_search(ga.Space(nv, kernels, valid), fit, max_evaluations=40, seed=seed, n_pop=16)
     best, res, trace = lib.sps_optimize(nv, kernels, fit, valid,
-                                        lib.search_desc(algorithm=lib.TUNE_RANDOM, max_evaluations=40, seed=seed))
+                                        lib.search_desc(algorithm=lib.TUNE_RANDOM, max_evaluations=40, seed=seed,
+                                                        population=16))
     assert trace == [(tuple(p), f) for p, f in want.trace] and best == want.best_point
+    assert res.final_population == want.final_population and len(want.final_population) == 16
+    short = lib.sps_optimize(nv, kernels, fit, valid, lib.search_desc(algorithm=lib.TUNE_RANDOM, max_evaluations=5,
+                                                                     seed=seed, population=16))[1]
+    assert short.final_population == [p for p, _ in ga.random_search(ga.Space(nv, kernels, valid), fit, 5, seed,
+                                                                      n_pop=16).trace]
     want = ga.exhaustive(ga.Space(nv, kernels, valid), fit)
     best, res, trace = lib.sps_optimize(nv, kernels, fit, valid, lib.search_desc(algorithm=lib.TUNE_EXHAUSTIVE))
     assert trace == [(tuple(p), f) for p, f in want.trace] and best == want.best_point
@@ -250,3 +257,55 @@ def test_known_evaluations_are_checked(lib):
     d.n_known = 2  # arrays missing
     with pytest.raises(lib.SpsError):
         lib.sps_optimize(nv, ko, lambda p: 1.0, None, d)
+
+
+def test_coefficients_of_variation_pins():
+    """Sec. 5 c_v per gene: identical end configurations give 0; two values a
+    and b in equal numbers give |a - b| / (a + b); a zero-mean gene is left out."""
+    values = [[1, 2, 4, 8], [0, 1], [32, 64]]
+    same = [(2, 1, 0)] * 6
+    assert ga.coefficients_of_variation(same, values) == [0.0, 0.0, 0.0]
+    mixed = [(0, 0, 0), (3, 0, 1)] * 3
+    cv = ga.coefficients_of_variation(mixed, values)
+    assert cv[0] == pytest.approx(7 / 9) and cv[1] is None and cv[2] == pytest.approx(32 / 96)
+
+
+def test_ga_converges_more_than_random_search_in_cv(lib):
+    """Sec. 5: averaged over runs, the GA's end configurations vary less per gene
+    than random search's (genetic memory), on a table with one good region."""
+    nv, ko = [4, 4, 5, 5, 3], [0, 0, 1, 1, 2]
+    values = [[1, 2, 4, 8], [4, 8, 16, 32], [1, 2, 4, 8, 16], [1, 2, 4, 8, 16], [32, 64, 128]]
+    grid = np.array(list(np.ndindex(*nv)))
+    t = {tuple(p): float(np.sum((p - np.array([2, 1, 3, 1, 2])) ** 2)) + 1.0 for p in grid}
+    cv = {}
+    for name, alg in (("ga", lib.TUNE_GA), ("random", lib.TUNE_RANDOM)):
+        runs = []
+        for seed in range(10):
+            _, res, _ = lib.sps_optimize(nv, ko, lambda p: t[tuple(p)], None,
+                                         lib.search_desc(algorithm=alg, population=20, max_evaluations=150,
+                                                         seed=seed))
+            runs.append(ga.coefficients_of_variation(res.final_population, values))
+        cv[name] = np.mean([[c for c in r if c is not None] for r in runs], axis=0)
+    assert np.all(cv["ga"] < cv["random"])
+
+
+def test_study_gene_cv_matches_the_oracle_definition():
+    """The study's per-gene c_v (product side) against the oracle's (Sec. 5)."""
+    from paper_1811_04165_gb300 import tune_study
+    rng = np.random.Generator(np.random.PCG64(3))
+    values = [[1, 2, 4, 8], [0, 1, 2], [32, 64, 128, 256, 512], [0]]
+    ends = [tuple(int(rng.integers(len(v))) for v in values) for _ in range(20)]
+    as_numpy = [list(np.array(v, np.int32)) for v in values]  # as sps_tune_space returns them
+    got, want = tune_study.gene_cv(ends, as_numpy), ga.coefficients_of_variation(ends, values)
+    assert [g is None for g in got] == [w is None for w in want]
+    assert np.allclose([g for g in got if g is not None], [w for w in want if w is not None], rtol=1e-12)
+
+
+def test_study_cv_on_a_synthetic_table(lib):
+    from paper_1811_04165_gb300 import tune_study
+    nv, ko = [4, 1, 5], [0, 0, 1]
+    values = [[1, 2, 4, 8], [16], [32, 64, 128, 256, 512]]
+    table = {pt: float(1 + (pt[0] - 2) ** 2 + (pt[2] - 1) ** 2) for pt in np.ndindex(*nv)}
+    res = tune_study._cv_study(nv, ko, table, values, ["a.x", "a.fixed", "b.y"], range(6), 15, population=8)
+    assert set(res) == {"ga", "random"} and set(res["ga"]) == {"a.x", "b.y"}  # one-value gene left out
+    assert all(v >= 0 for r in res.values() for v in r.values())
