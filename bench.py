@@ -424,9 +424,11 @@ def main():
                 "peak_derivation": "152 SMs x 128 INT32 lanes/clk x 2070 MHz",
                 "peak_measured": int_peak_tadd, "frac_of_measured": achieved / int_peak_tadd,
                 "peak_measured_how": "sps_measure_int_add_rate: independent add chains on the ALU and FMA pipes",
-                "kernel_own_bound": ("shared-memory data path: the pass runs at 72 % of L1/shared throughput and "
-                                     "executes a quarter of the brute-force adds (ncu, " + summary + ")") if presum
-                else ("instruction issue: 82 % issue-active, 1.72 instructions per add (ncu, " + summary + ")")}
+                "kernel_own_bound": {
+                    2: "shared-memory data path: the pass runs at 72 % of L1/shared throughput and executes a "
+                       "quarter of the brute-force adds (ncu, " + summary + ")",
+                    1: "shared-memory data path (pairs: half the brute-force adds; no committed ncu capture)",
+                    0: "instruction issue: 82 % issue-active, 1.72 instructions per add (ncu, " + summary + ")"}[presum]}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
