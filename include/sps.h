@@ -45,7 +45,7 @@ typedef enum {
   SPS_ERR_UNSUPPORTED = 2,  /* valid request outside what the kernels implement   */
   SPS_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed                 */
   SPS_ERR_OOM = 4,          /* device or host allocation failed                     */
-  SPS_ERR_TIMEOUT = 5,      /* a tuning evaluation exceeded its time limit          */
+  SPS_ERR_TIMEOUT = 5,      /* a kernel's bounded wait ran out (sps_plan_status)    */
   SPS_ERR_NO_DEVICE = 6     /* no CUDA device is visible                            */
 } sps_status;
 
