@@ -182,6 +182,42 @@ def oracle_rows_threaded(x, d, rows, n_t, widths, threads):
         return list(ex.map(one, parts))
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, or implementer/part on Arm)."""
+    import platform
+    try:
+        fields = {}
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip(), v.strip())
+        if "model name" in fields:
+            return fields["model name"]
+        if "CPU part" in fields:
+            return f"{platform.machine()} implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def cpu_oracle_tiny():
+    """The oracle's whole search (dedispersion + S/N) on the tiny 64-channel
+    configuration, single thread: DM-trial samples/s and seconds."""
+    import oracle
+    from paper_1811_04165_gb300 import synth
+    wl = synth.tiny_brute()
+    d = oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms)
+    x = synth.filterbank(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, wl.n_t + int(d.max()), wl.seed, wl.pulses)
+    reps, t0 = 0, time.perf_counter()
+    while reps < 3 or time.perf_counter() - t0 < 1.0:
+        D = oracle.dedisperse(x, d, wl.n_t)
+        oracle.snr(D, wl.widths)
+        reps += 1
+    dt = (time.perf_counter() - t0) / reps
+    return wl.dms.size * wl.n_t / dt, dt
+
+
 def cpu_oracle_all_cores(wl, x, threads):
     """DM-trial samples/s of the oracle on every host core, over the whole batch."""
     import oracle
@@ -238,7 +274,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": workload_config(wl, "brute"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -497,7 +534,12 @@ def main():
                                           f"split over {threads} threads: {dt_all:.1f} s",
                                 "single_thread": {"value": rate, "unit": UNIT, "cores": 1,
                                                   "sample": f"{rows} of {wl.dms.size} DM trials, full batch, "
-                                                            f"{dt:.1f} s"}}
+                                                            f"{dt:.1f} s"},
+                                "cpu": cpu_model()}
+        tiny_rate, tiny_s = cpu_oracle_tiny()
+        line["cpu_baseline"]["tiny_single_thread"] = {
+            "value": tiny_rate, "unit": UNIT, "cores": 1,
+            "sample": f"the tiny 64-channel search (32 DM trials x 4096 samples, 4 widths), {1e3 * tiny_s:.1f} ms"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
