@@ -195,7 +195,9 @@ def cpu_model() -> str:
         if "model name" in fields:
             return fields["model name"]
         if "CPU part" in fields:
-            return f"{platform.machine()} implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+            names = {("0x41", "0xd4f"): "Arm Neoverse V2", ("0x41", "0xd40"): "Arm Neoverse V1"}
+            key = (fields.get("CPU implementer", "?"), fields["CPU part"])
+            return names.get(key, f"{platform.machine()} implementer {key[0]} part {key[1]}")
     except OSError:
         pass
     return platform.machine()
