@@ -71,7 +71,7 @@ typedef struct sps_plan sps_plan; /* opaque */
  *              j < N_t / f (the trailing N_t mod f samples are dropped); S/N is
  *              taken over the N_t / f downsampled samples (factor 1 = the
  *              series itself, Sec. 5) and peak_t is in input samples, f * j.
- * zap (Sec. 3, footnote: channels zapped for terrestrial RFI): zapped channels
+ * zap (Sec. 2, footnote: channels zapped for terrestrial RFI): zapped channels
  * contribute nothing to any sum; the search then reads a masked copy of x in
  * the workspace (sps_plan_workspace_bytes includes it). */
 typedef struct {

@@ -18,7 +18,7 @@ Sclocco, AMBER auto-tuning with genetic algorithms):
   boxcar             Sec. 2 "downsampling (smoothing)", as a sliding boxcar
   snr                Sec. 2 S/N step; (peak - mean) / population sigma
   detect             argmax over (DM, width) of the S/N table
-  zap_channels       Sec. 3, footnote: channels zapped for terrestrial RFI
+  zap_channels       Sec. 2, footnote: channels zapped for terrestrial RFI
   decimate           Table 2 DOWNSAMPLING / NRSAMPLES: decimating downsampling
   snr_decimated      Sec. 2 S/N, Sec. 5: on every downsampled series (factor 1 =
                      the series itself)

@@ -1,4 +1,4 @@
-// RFI channel zapping (Sec. 3, footnote: channels to zap because of
+// RFI channel zapping (Sec. 2, footnote: channels to zap because of
 // terrestrial interference): a copy of the input whose zapped rows are zero,
 // bytes at and beyond in_len zero too; the search then reads the copy.
 #include "sps_internal.h"

@@ -9,9 +9,8 @@
 2. On that table, the library's GA (population 32, tournament pools of 20 %,
    uniform crossover p_cross 0.8, mutation 0.1) and pure random search run with
    equal budgets of distinct evaluations over many seeds: best-of-run relative
-   to the optimum, the share of runs within 5 %, and the coefficient of
-   variation of the best fitness over runs (Sec. 5 reports it for repeated GA
-   runs).
+   to the optimum, the share of runs within 5 %, and the spread (coefficient
+   of variation) of the best fitness over runs.
 3. Sweeps of p_mut, p_cross, population, crossover kind and budget on the same
    table (Fig. 3), a histogram of the GA's best over seeds (Fig. 5), and the
    convergence diagnostic of Sec. 5 (Fig. 4): per gene, the coefficient of

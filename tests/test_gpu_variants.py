@@ -1,6 +1,6 @@
 """AMBER-style variants against the oracle: decimating downsampling with S/N on
 every downsampled series (Table 2 DOWNSAMPLING / NRSAMPLES, Sec. 5), and RFI
-channel zapping (Sec. 3 footnote)."""
+channel zapping (Sec. 2 footnote)."""
 import numpy as np
 import pytest
 

@@ -302,7 +302,7 @@ def test_detect_tie_break():
 # ----------------------------------------------------------------------------- RFI zapping, downsampling
 def test_zapping_is_linear_in_the_channel_set():
     """Zapped + zapped-only de-dispersions add up to the full one; zapping every
-    channel gives zeros (Sec. 3 footnote: zapped channels are left out)."""
+    channel gives zeros (Sec. 2 footnote: zapped channels are left out)."""
     rng = np.random.Generator(np.random.PCG64(41))
     C, n_t = 12, 40
     d = rng.integers(0, 9, size=(5, C)).astype(np.int32)

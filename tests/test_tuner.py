@@ -111,7 +111,7 @@ def test_mutation_always_moves_a_gene_when_forced():
 
 
 def test_ga_beats_random_search_on_average():
-    # Sec. 5: on average the GA finds better configurations than pure random
+    # Sec. 4: on average the GA finds better configurations than pure random
     # search with the same budget (separable landscape with a narrow optimum)
     nv = [8, 8, 8, 8, 8]
     rng = np.random.Generator(np.random.PCG64(11))
