@@ -97,6 +97,28 @@ def test_ga_without_operators_keeps_the_best_individual():
     assert r.generations == 5
 
 
+@pytest.mark.parametrize("seed", [2, 3])
+def test_end_configurations_are_the_last_population(seed):
+    """The oracle's end configurations (Sec. 5): the GA's last population has
+    N_pop valid, evaluated individuals and, by the elitist replacement, holds the
+    best one found; with pool = N_pop and no operators it is N_pop copies of the
+    fittest initial individual.  Random search's are its last N_pop draws."""
+    nv, ko = [4, 3, 5, 4], [0, 0, 1, 1]
+    fit, _ = _table_fitness(nv, seed)
+    valid, mask = _validity(nv, seed)
+    r = ga.genetic(ga.Space(nv, ko, valid), fit, n_pop=10, max_evaluations=60, max_generations=30, seed=seed)
+    evaluated = {p for p, _ in r.trace}
+    assert len(r.final_population) == 10
+    assert all(mask[p] and p in evaluated for p in r.final_population)
+    assert r.best_point in r.final_population
+    frozen = ga.genetic(ga.Space(nv, ko), fit, n_pop=6, p_cross=0.0, p_mut=0.0, pool_fraction=1.0,
+                        max_evaluations=100, max_generations=3, seed=seed)
+    first = min(frozen.trace[:6], key=lambda e: e[1])[0]
+    assert frozen.final_population == [first] * 6
+    rs = ga.random_search(ga.Space(nv, ko, valid), fit, max_evaluations=25, seed=seed, n_pop=10)
+    assert rs.final_population == [p for p, _ in rs.trace][-10:]
+
+
 def test_mutation_always_moves_a_gene_when_forced():
     nv = [3, 3]
     seen = []
