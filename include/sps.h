@@ -426,6 +426,20 @@ sps_status sps_plan_status(const sps_plan* plan, uint32_t* host_status, int32_t 
  * or polls out of range. */
 sps_status sps_plan_check_wait_timeout(const sps_plan* plan, int32_t polls, void* stream);
 
+/* Host-only check of the pre-summed kernels' tables (no device needed; the
+ * paper has no counterpart): builds the staging tables a plan would build for
+ * `delays` (host int32 [rows][channels]; groups of `per` channels: `channels`
+ * for brute force, channels / n_subbands for step one) and configuration
+ * `cfg` (presum 1 or 2), with series written for build_n_out outputs, then
+ * re-derives from the delays what each trial of each tile reads and checks it:
+ * its staged offset lies in a window of its chunk, the window holds its own
+ * series in the copy of its delay parity and starts where its delay says, the
+ * window fits the stage, and the series' written range covers the samples of
+ * read_n_out outputs.  OK when every check holds; INVALID_ARG naming the first
+ * failure; UNSUPPORTED when the configuration's stage would not fit. */
+sps_status sps_presum_tables_verify(const int32_t* delays, int32_t rows, int32_t channels, int32_t per,
+                                    int32_t build_n_out, int32_t read_n_out, const sps_dedisp_config* cfg);
+
 /* Measures the device's 32-bit integer add rate (adds/s over all SMs: independent
  * add chains split between the ALU pipe and multiply-adds by one on the FMA
  * pipe, best of three timed runs), the denominator against which the

@@ -523,6 +523,15 @@ def sps_plan_check_wait_timeout(plan, polls=1000, stream=None):
     check(_L.sps_plan_check_wait_timeout(plan.handle, int(polls), _stream(stream)), "sps_plan_check_wait_timeout")
 
 
+def sps_presum_tables_verify(delays, per, n_out, cfg: DedispConfig, read_n_out=None):
+    """Host-only check of the pre-summed kernels' staging tables for a delay table
+    (int32 [rows][channels]); raises SpsError naming the first violated invariant."""
+    d = np.ascontiguousarray(delays, np.int32)
+    check(_L.sps_presum_tables_verify(d.ctypes.data, d.shape[0], d.shape[1], int(per), int(n_out),
+                                      int(n_out if read_n_out is None else read_n_out), ctypes.byref(cfg)),
+          "sps_presum_tables_verify")
+
+
 def sps_measure_int_add_rate(stream=None) -> float:
     """The device's measured 32-bit integer add rate, adds/s."""
     v = ctypes.c_double()

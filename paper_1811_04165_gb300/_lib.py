@@ -34,6 +34,7 @@ SIGNATURES = {
     "sps_search_host": (_I32, [_P, _P, _I64, _P, _P, _P, _SZ, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "sps_plan_status": (_I32, [_P, _P, _I32]),
     "sps_plan_check_wait_timeout": (_I32, [_P, _I32, _P]),
+    "sps_presum_tables_verify": (_I32, [_P, _I32, _I32, _I32, _I32, _I32, _P]),
     "sps_batch_workspace_bytes": (_I32, [_P, _I32, _I32, _P]),
     "sps_batch_create": (_I32, [_P, _P, _I32, _I32, _P, _SZ, _P]),
     "sps_batch_launch": (_I32, [_P, _P]),

@@ -398,6 +398,21 @@ sps_status sps_search_host(const sps_plan* p, const uint8_t* x_host, int64_t pit
   return SPS_OK;
 }
 
+sps_status sps_presum_tables_verify(const int32_t* delays, int32_t rows, int32_t channels, int32_t per,
+                                    int32_t build_n_out, int32_t read_n_out, const sps_dedisp_config* cfg) {
+  clear_error();
+  if (!delays || !cfg) return fail(SPS_ERR_INVALID_ARG, "null argument");
+  if (rows < 1 || channels < 1 || per < 1 || channels % per || build_n_out < 1 || read_n_out < 1)
+    return fail(SPS_ERR_INVALID_ARG, "rows, channels, per (dividing channels) and n_out must be positive");
+  std::string why;
+  if (!presum_config_supported(*cfg, &why)) return fail(SPS_ERR_INVALID_ARG, why);
+  const std::vector<int32_t> d(delays, delays + (size_t)rows * channels);
+  PresumTables t;
+  if (sps_status s = build_presum_tables(d, rows, channels, per, build_n_out, *cfg, &t)) return s;
+  if (!verify_presum_tables(d, rows, channels, per, read_n_out, *cfg, t, &why)) return fail(SPS_ERR_INVALID_ARG, why);
+  return SPS_OK;
+}
+
 sps_status sps_plan_status(const sps_plan* p, uint32_t* host_status, int32_t clear) {
   clear_error();
   if (sps_status s = check_plan(p)) return s;

@@ -227,4 +227,64 @@ sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int3
   return SPS_OK;
 }
 
+// Checks, from the delay table alone, what the pass kernel will read through a
+// set of tables: for every trial of every (tile, group, unit), its staged
+// offset falls inside one window of its chunk's list, that window holds the
+// trial's own series (same unit, same relative delays) in the copy of the
+// trial's delay parity, the window's first sample plus the offset is the
+// trial's even-rounded reference delay d', the window lies inside the stage's
+// data, and the series' written range [lo, hi) covers d' .. d' + read_n_out - 1
+// (every sample a valid output reads).  The first failure is described in *why.
+bool verify_presum_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t read_n_out,
+                          const sps_dedisp_config& cfg, const PresumTables& t, std::string* why) {
+  const int32_t K = 1 << cfg.presum;
+  const int32_t G = C / per;
+  const int32_t U = (per + K - 1) / K;
+  const int32_t Di = cfg.warps_dm * cfg.dms_per_thread;
+  const int32_t Tt = cfg.warps_time * 32 * cfg.samples_per_thread;
+  const int32_t di_pad = presum_di_pad(cfg);
+  const int32_t cu = presum_chunk(cfg);
+  const int32_t n_chunks = (U + cu - 1) / cu;
+  const int32_t n_tiles = (rows + Di - 1) / Di;
+  auto say = [&](const char* what, int32_t tile, int32_t g, int32_t u, int32_t r) {
+    *why = std::string(what) + " (tile " + std::to_string(tile) + ", group " + std::to_string(g) + ", unit " +
+           std::to_string(u) + ", trial " + std::to_string(r) + ")";
+    return false;
+  };
+  for (int32_t tile = 0; tile < n_tiles; tile++)
+    for (int32_t g = 0; g < G; g++)
+      for (int32_t u = 0; u < U; u++) {
+        const int32_t c0 = g * per + K * u, n = std::min(K, per - K * u), e = c0 + n - 1;
+        const size_t row = ((size_t)tile * G + g) * n_chunks + u / cu;
+        const int4* list = &t.copies[row * (t.copies_max + 1)];
+        const int32_t count = list[t.copies_max].x;
+        for (int32_t r = 0; r < Di; r++) {
+          const int32_t i = tile * Di + r;
+          if (i >= rows) break;
+          const int32_t* di = &d[(size_t)i * C];
+          const int32_t de = di[e], dprime = de & ~1, parity = de & 1;
+          const int64_t off = 4 * (int64_t)t.offs[(((size_t)tile * G + g) * U + u) * di_pad + r];  // stage bytes
+          int32_t q = 0;
+          for (; q < count; q++) {
+            const int32_t dst = (list[q].z & 0xFFFF) * 16, bytes = ((uint32_t)list[q].z >> 16) * 16;
+            if (off >= dst && off + 2 * (int64_t)Tt <= (int64_t)dst + bytes) break;
+          }
+          if (q == count) return say("offset outside every window of the chunk", tile, g, u, r);
+          const int32_t dst = (list[q].z & 0xFFFF) * 16, bytes = ((uint32_t)list[q].z >> 16) * 16;
+          if (dst + bytes > t.data_bytes) return say("window beyond the stage data", tile, g, u, r);
+          const int32_t srow = list[q].x, s = srow / 2;
+          if (srow < 0 || s >= (int32_t)t.series.size()) return say("window row outside the series table", tile, g, u, r);
+          if (srow % 2 != parity) return say("window of the wrong alignment copy", tile, g, u, r);
+          const PresumSeries& ps = t.series[s];
+          if (ps.c0 != c0 || ps.n != n) return say("window of another unit's series", tile, g, u, r);
+          for (int32_t j = 0; j + 1 < n; j++)
+            if (ps.rel[j] != di[c0 + j] - de) return say("window of a series with other relative delays", tile, g, u, r);
+          if (list[q].y + (off - dst) / 2 != dprime) return say("offset does not land on the trial's delay", tile, g, u, r);
+          if (dprime < ps.lo || (int64_t)dprime + read_n_out > ps.hi)
+            return say("a valid output reads outside the series' written range", tile, g, u, r);
+        }
+      }
+  return true;
+}
+
 }  // namespace sps

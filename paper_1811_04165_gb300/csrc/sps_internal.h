@@ -172,6 +172,8 @@ int32_t presum_stage_data(const std::vector<int32_t>& d, int32_t rows, int32_t C
                           int32_t units_per_chunk, int32_t Tt);
 sps_status build_presum_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t n_out,
                                const sps_dedisp_config& cfg, PresumTables* out);
+bool verify_presum_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C, int32_t per, int32_t read_n_out,
+                          const sps_dedisp_config& cfg, const PresumTables& t, std::string* why);
 bool u8_config_supported(const sps_dedisp_config& cfg, std::string* why);
 bool step2_config_supported(const sps_dedisp_config& cfg, std::string* why);
 bool snr_config_supported(const sps_snr_config& cfg, std::string* why);
