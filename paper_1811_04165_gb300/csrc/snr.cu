@@ -347,11 +347,13 @@ detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
   __shared__ int si[32], sw[32];
   double bv = -1.0;
   int bi = 0x7fffffff, bw = 0x7fffffff;
-  const int64_t n = (int64_t)n_dms * n_widths;
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-    const int w = (int)(e / n_dms), i = (int)(e - (int64_t)w * n_dms);
-    const double v = snr[e];
-    if (better(v, i, w, bv, bi, bw)) { bv = v; bi = i; bw = w; }
+  // every (width, DM) entry once; the tie rules make the visiting order irrelevant
+  for (int w = 0; w < n_widths; w++) {
+    const double* row = snr + (int64_t)w * n_dms;
+    for (int i = threadIdx.x; i < n_dms; i += blockDim.x) {
+      const double v = __ldg(row + i);
+      if (better(v, i, w, bv, bi, bw)) { bv = v; bi = i; bw = w; }
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
