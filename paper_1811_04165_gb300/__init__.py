@@ -574,7 +574,11 @@ class SearchDesc(ctypes.Structure):
 
 def _with_final_population(desc, n_genes):
     """A copy of `desc` whose final_population points at a fresh [population][n_genes]
-    array (returned beside it); the caller's descriptor is left as it was."""
+    array (returned beside it); the caller's descriptor is left as it was.  Known
+    evaluations must have one value per gene (the engine reads n_genes per point)."""
+    known = getattr(desc, "_known_arrays", None)
+    if desc.n_known and (known is None or known[0].ndim != 2 or known[0].shape != (desc.n_known, n_genes)):
+        raise ValueError(f"known evaluations need {n_genes} gene values per point")
     d = SearchDesc.from_buffer_copy(desc)
     d._known_arrays = getattr(desc, "_known_arrays", None)
     fp = np.full((max(1, desc.population), n_genes), -1, np.int32)

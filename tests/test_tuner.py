@@ -277,8 +277,10 @@ def test_known_evaluations_are_checked(lib):
         lib.sps_optimize(nv, ko, lambda p: 1.0, None, lib.search_desc(known=[((3, 0), 1.0)]))  # out of the space
     d = lib.search_desc()
     d.n_known = 2  # arrays missing
-    with pytest.raises(lib.SpsError):
+    with pytest.raises(ValueError):
         lib.sps_optimize(nv, ko, lambda p: 1.0, None, d)
+    with pytest.raises(ValueError):  # points of the wrong length
+        lib.sps_optimize(nv, ko, lambda p: 1.0, None, lib.search_desc(known=[((1,), 1.0)]))
 
 
 def test_coefficients_of_variation_pins():
