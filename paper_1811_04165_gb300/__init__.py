@@ -127,6 +127,8 @@ def sps_plan_create(channels, f_lo_mhz, f_hi_mhz, t_samp_s, n_samples, dms, widt
                   None if zap is None else (np.asarray(zap) != 0).astype(np.uint8))
     if arr.zap is not None and arr.zap.size != int(channels):
         raise ValueError("zap needs one flag per channel")
+    if arr.coarse_of is not None and arr.coarse_of.size != arr.dms.size:
+        raise ValueError("coarse_of needs one coarse-DM index per DM trial")
     d = PlanDesc()
     d.channels, d.f_lo_mhz, d.f_hi_mhz, d.t_samp_s = int(channels), float(f_lo_mhz), float(f_hi_mhz), float(t_samp_s)
     d.n_samples = int(n_samples)

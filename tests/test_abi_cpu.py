@@ -94,3 +94,13 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(ImportError):
         _lib.lib()
+
+
+def test_binding_checks_host_array_lengths(lib):
+    """Arrays the library reads by count from the descriptor are checked for
+    length in the binding first (a short array would be read past its end)."""
+    with pytest.raises(ValueError):
+        lib.sps_plan_create(16, 1250.0, 1550.0, 81.92e-6, 100, [0.0, 1.0, 2.0, 3.0], [1], mode=lib.MODE_SUBBAND,
+                            n_subbands=4, coarse_dms=[0.0, 2.0], coarse_of=[0, 0, 1])
+    with pytest.raises(ValueError):
+        lib.sps_plan_create(16, 1250.0, 1550.0, 81.92e-6, 100, [0.0], [1], zap=[0] * 15)
