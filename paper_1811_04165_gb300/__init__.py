@@ -98,6 +98,15 @@ def _dev(t, dtype, name, shape=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _xdev(plan, x, name="x"):
+    """A filterbank on the device: uint8 [channels][pitch], one row per channel
+    (the library reads `channels` rows of the given pitch)."""
+    t = _torch()
+    if not isinstance(x, t.Tensor) or x.dim() != 2 or x.shape[0] != plan.channels:
+        raise ValueError(f"{name} must be a 2-D tensor with one row per channel ({plan.channels})")
+    return _dev(x, t.uint8, name)
+
+
 def _host(a, dtype, name, shape=None):
     import torch
     if isinstance(a, torch.Tensor):
@@ -155,7 +164,7 @@ def sps_dedisperse(plan, x, D, workspace=None, stream=None):
         workspace = plan.workspace()
     ws = _dev(workspace, workspace.dtype, "workspace") if workspace is not None else ctypes.c_void_p()
     wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
-    check(_L.sps_dedisperse(p, _dev(x, _torch().uint8, "x"), ctypes.c_int64(x.shape[1]),
+    check(_L.sps_dedisperse(p, _xdev(plan, x), ctypes.c_int64(x.shape[1]),
                             _dev(D, _torch().int32, "D", (plan.n_dms, plan.n_samples)), ws,
                             ctypes.c_size_t(wsb), _stream(stream)), "sps_dedisperse")
 
@@ -164,7 +173,7 @@ def sps_dedisperse_noalloc(plan, x, D, stream=None):
     """sps_dedisperse with the library's fixed static scratch instead of a workspace
     (for callers that cannot allocate device memory; see include/sps.h)."""
     t = _torch()
-    check(_L.sps_dedisperse_noalloc(plan.handle, _dev(x, t.uint8, "x"), ctypes.c_int64(x.shape[1]),
+    check(_L.sps_dedisperse_noalloc(plan.handle, _xdev(plan, x), ctypes.c_int64(x.shape[1]),
                                     _dev(D, t.int32, "D", (plan.n_dms, plan.n_samples)), _stream(stream)),
           "sps_dedisperse_noalloc")
 
@@ -172,7 +181,7 @@ def sps_dedisperse_noalloc(plan, x, D, stream=None):
 def sps_subband_step1(plan, x, Y, workspace=None, stream=None):
     if workspace is None:
         workspace = plan.workspace()
-    check(_L.sps_subband_step1(plan.handle, _dev(x, _torch().uint8, "x"), ctypes.c_int64(x.shape[1]),
+    check(_L.sps_subband_step1(plan.handle, _xdev(plan, x), ctypes.c_int64(x.shape[1]),
                                _dev(Y, _torch().uint16, "Y", plan.y_shape),
                                _dev(workspace, workspace.dtype, "workspace"),
                                ctypes.c_size_t(workspace.numel() * workspace.element_size()), _stream(stream)),
@@ -208,7 +217,7 @@ def sps_search(plan, x, D, snr, peak_t, peak_val, best=None, workspace=None, str
     shp = (plan.n_widths, plan.n_dms)
     ws = _dev(workspace, workspace.dtype, "workspace") if workspace is not None else ctypes.c_void_p()
     wsb = workspace.numel() * workspace.element_size() if workspace is not None else 0
-    check(_L.sps_search(plan.handle, _dev(x, t.uint8, "x"), ctypes.c_int64(x.shape[1]),
+    check(_L.sps_search(plan.handle, _xdev(plan, x), ctypes.c_int64(x.shape[1]),
                         _dev(D, t.int32, "D", (plan.n_dms, plan.n_samples)), ws, ctypes.c_size_t(wsb),
                         _dev(snr, t.float64, "snr", shp), _dev(peak_t, t.int32, "peak_t", shp),
                         _dev(peak_val, t.int32, "peak_val", shp),
@@ -228,7 +237,7 @@ def sps_search_host(plan, x_host, x_dev, D, snr_dev, peak_t_dev, peak_val_dev, b
         raise ValueError("x_host and x_dev must have the same shape")
     check(_L.sps_search_host(
         plan.handle, _host(x_host, t.uint8, "x_host"), ctypes.c_int64(x_dev.shape[1]),
-        _dev(x_dev, t.uint8, "x_dev"), _dev(D, t.int32, "D", (plan.n_dms, plan.n_samples)), ws,
+        _xdev(plan, x_dev, "x_dev"), _dev(D, t.int32, "D", (plan.n_dms, plan.n_samples)), ws,
         ctypes.c_size_t(wsb), _dev(snr_dev, t.float64, "snr_dev", shp),
         _dev(peak_t_dev, t.int32, "peak_t_dev", shp), _dev(peak_val_dev, t.int32, "peak_val_dev", shp),
         _dev(best_dev, t.int32, "best_dev", (4,)), _host(snr_host, t.float64, "snr_host", shp),
@@ -432,7 +441,7 @@ class Batch:
         bufs = (BeamBuffers * len(self.plans))()
         for b, (p, x, o) in enumerate(zip(self.plans, self.xs, self.outs)):
             shp = (p.n_widths, p.n_dms)
-            bufs[b] = BeamBuffers(_dev(x, t.uint8, "x").value, int(x.shape[1]),
+            bufs[b] = BeamBuffers(_xdev(p, x).value, int(x.shape[1]),
                                   _dev(o["D"], t.int32, "D", (p.n_dms, p.n_samples)).value,
                                   _dev(o["snr"], t.float64, "snr", shp).value,
                                   _dev(o["peak_t"], t.int32, "peak_t", shp).value,
@@ -485,6 +494,23 @@ class Server:
             if a is None:
                 return None
             return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        def dense(a, itemsize, name):
+            ok = a.is_contiguous() and a.element_size() == itemsize if hasattr(a, "is_contiguous") else \
+                a.flags["C_CONTIGUOUS"] and a.itemsize == itemsize
+            if not ok:
+                raise ValueError(f"{name} must be C-contiguous with {itemsize}-byte elements")
+
+        p = self.plans[int(beam)] if 0 <= int(beam) < len(self.plans) else None
+        if p is not None:  # (an unknown beam is refused by the library)
+            if len(x_host.shape) != 2 or x_host.shape[0] != p.channels:
+                raise ValueError(f"x_host must be 2-D with one row per channel ({p.channels})")
+            dense(x_host, 1, "x_host")
+            for a, shape, size, name in ((snr_host, (p.n_widths, p.n_dms), 8, "snr_host"),
+                                         (best_host, (4,), 4, "best_host")):
+                if a is not None:
+                    if tuple(a.shape) != shape:
+                        raise ValueError(f"{name} must have shape {shape}")
+                    dense(a, size, name)
         pitch = int(x_host.shape[1])
         self._keep[int(tag)] = (x_host, snr_host, best_host)
         check(_L.sps_server_submit(self.handle, int(beam), ptr(x_host), pitch, ptr(snr_host), ptr(best_host),
@@ -752,7 +778,7 @@ def sps_tune(plan, x, which=SPACE_FULL, desc: SearchDesc | None = None, reps=3, 
     shp = (plan.n_widths, plan.n_dms)
     desc = desc or search_desc()
     d, fp = _with_final_population(desc, n)
-    check(_L.sps_tune(plan.handle, int(which), ctypes.byref(d), _dev(x, t.uint8, "x"),
+    check(_L.sps_tune(plan.handle, int(which), ctypes.byref(d), _xdev(plan, x),
                       ctypes.c_int64(x.shape[1]), _dev(out["D"], t.int32, "D", (plan.n_dms, plan.n_samples)),
                       _dev(workspace, workspace.dtype, "workspace"),
                       ctypes.c_size_t(workspace.numel() * workspace.element_size()),

@@ -495,6 +495,8 @@ def test_argument_errors(lib):
     with pytest.raises(lib.SpsError) as e:
         lib.sps_dedisperse(p, x[:, : p.pitch - 16].contiguous(), D)
     assert e.value.status == 1
+    with pytest.raises(ValueError):  # one row short: refused before the library would read past it
+        lib.sps_dedisperse(p, x[:-1].contiguous(), D)
     xs = torch.zeros(wl.channels * p.pitch + 16, dtype=torch.uint8, device="cuda")[1:1 + wl.channels * p.pitch]
     with pytest.raises(lib.SpsError):
         lib.sps_dedisperse(p, xs.view(wl.channels, p.pitch), D)
