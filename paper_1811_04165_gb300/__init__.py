@@ -695,6 +695,8 @@ def sps_optimize(n_values, kernel_of, fitness, valid=None, desc: SearchDesc | No
     per distinct evaluation, in order; `log` names a JSON-lines tuning log to write."""
     nv = np.ascontiguousarray(n_values, np.int32)
     ko = np.ascontiguousarray(kernel_of, np.int32)
+    if nv.ndim != 1 or ko.shape != nv.shape:
+        raise ValueError("n_values and kernel_of need one entry per gene")
     sp = SpaceDesc(nv.size, nv.ctypes.data, ko.ctypes.data)
     desc = desc or search_desc()
     n = nv.size

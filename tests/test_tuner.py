@@ -207,6 +207,8 @@ def test_library_optimize_penalties_and_errors(lib):
     assert best == (1, 0) and res.best_fitness == 1.0
     with pytest.raises(lib.SpsError):
         lib.sps_optimize([4, 4], [1, 0], fit)  # kernel_of not non-decreasing
+    with pytest.raises(ValueError):
+        lib.sps_optimize([4, 4, 4], [0, 1], fit)  # kernel_of shorter than the gene list
     with pytest.raises(lib.SpsError):
         lib.sps_optimize([4, 4], [0, 1], fit, None, lib.search_desc(population=7))
     with pytest.raises(lib.SpsError):
