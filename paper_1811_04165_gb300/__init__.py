@@ -313,7 +313,9 @@ class Plan:
         return int(n.value)
 
     def workspace(self):
-        """A device workspace tensor of the required size (cached per plan)."""
+        """A device workspace tensor of the required size, cached per plan and used by
+        the calls that get no workspace argument: it serves one stream at a time;
+        searches on several streams at once need one workspace each."""
         import torch
         n = self.workspace_bytes
         ws = getattr(self, "_ws", None)
