@@ -28,6 +28,7 @@ from ._lib import SpsError, check, lib, lib_path  # noqa: F401
 
 MODE_BRUTE = 0
 MODE_SUBBAND = 1
+SPS_OK, SPS_ERR_INVALID_ARG, SPS_ERR_UNSUPPORTED, SPS_ERR_CUDA, SPS_ERR_OOM, SPS_ERR_TIMEOUT = 0, 1, 2, 3, 4, 5
 SMOOTH_SLIDING = 0
 SMOOTH_DECIMATE = 1
 
@@ -513,10 +514,15 @@ class Server:
                     if tuple(a.shape) != shape:
                         raise ValueError(f"{name} must have shape {shape}")
                     dense(a, size, name)
+        if int(tag) in self._keep:
+            raise ValueError(f"tag {int(tag)} is still in flight")  # its buffers must stay referenced
         pitch = int(x_host.shape[1])
         self._keep[int(tag)] = (x_host, snr_host, best_host)
-        check(_L.sps_server_submit(self.handle, int(beam), ptr(x_host), pitch, ptr(snr_host), ptr(best_host),
-                                   ctypes.c_uint64(int(tag))), "sps_server_submit")
+        st = _L.sps_server_submit(self.handle, int(beam), ptr(x_host), pitch, ptr(snr_host), ptr(best_host),
+                                  ctypes.c_uint64(int(tag)))
+        if st == SPS_ERR_INVALID_ARG:  # refused before anything was queued
+            self._keep.pop(int(tag), None)
+        check(st, "sps_server_submit")
 
     def poll(self, max_n=256):
         tags = (ctypes.c_uint64 * max_n)()

@@ -76,3 +76,29 @@ def test_admission_respects_the_budget(lib):
     assert e.value.status == 2 and "budget" in str(e.value)
     big = lib.Server(hbm_budget_bytes=8 << 30, max_inflight=2)
     assert [big.add_beam(p) for p in plans] == [0, 1]
+
+
+def test_submit_refuses_a_tag_in_flight_and_bad_buffers(lib):
+    wls = _beams()
+    p = lib.Plan.from_workload(wls[0])
+    srv = lib.Server(hbm_budget_bytes=8 << 30, max_inflight=2)
+    b = srv.add_beam(p)
+    x = np.zeros((wls[0].channels, wls[0].n_t), np.uint8)
+    snr = np.zeros((p.n_widths, p.n_dms))
+    srv.submit(b, x, snr, tag=7)
+    with pytest.raises(ValueError):  # tag 7 has not been polled yet: its buffers stay referenced
+        srv.submit(b, x, snr, tag=7)
+    with pytest.raises(ValueError):
+        srv.submit(b, x[:-1], tag=8)  # one channel row short
+    with pytest.raises(ValueError):
+        srv.submit(b, x, np.zeros((p.n_widths, p.n_dms), np.float32), tag=9)  # 4-byte S/N elements
+    with pytest.raises(lib.SpsError):
+        srv.submit(b, x[:, :10].copy(), tag=10)  # pitch below N_t: refused by the library
+    done = {}
+    t_end = srv.clock() + 30.0
+    while srv.pending() and srv.clock() < t_end:
+        done.update(srv.poll())
+    assert 7 in done and srv.pending() == 0
+    srv.submit(b, x, snr, tag=10)  # the refused tag is free again
+    while srv.pending() and srv.clock() < t_end:
+        srv.poll()
