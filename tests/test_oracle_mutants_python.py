@@ -118,3 +118,51 @@ def _run_pin(name, params):
 def test_variant_pin_fails(monkeypatch, attr, wrong, pin, params):
     monkeypatch.setattr(oracle, attr, wrong)
     assert _run_pin(pin, params), f"no pin caught the {attr} slip"
+
+
+# ----------------------------------------------------------------------------- the two-step path's index helpers
+_real_coarse_index, _real_subband_lengths = oracle.coarse_index, oracle.subband_lengths
+
+
+def _coarse_index_modulo(n_dms, n_coarse):  # trials dealt round-robin to the coarse DMs
+    return (np.arange(n_dms) % n_coarse).astype(np.int32)
+
+
+def _coarse_index_nearest(n_dms, n_coarse):  # the nearest block start instead of the one below
+    per = n_dms // n_coarse
+    return np.minimum(np.rint(np.arange(n_dms) / per), n_coarse - 1).astype(np.int32)
+
+
+def _coarse_index_off_by_one(n_dms, n_coarse):  # blocks shifted by one trial
+    per = n_dms // n_coarse
+    return np.minimum((np.arange(n_dms) + 1) // per, n_coarse - 1).astype(np.int32)
+
+
+def _lengths_swapped(n_t, d1, d2):  # step one's spread taken for step two's
+    n_1 = n_t + int(d1.max())
+    return n_1, n_1 + int(d2.max())
+
+
+def _lengths_step1_spread_twice(n_t, d1, d2):  # N_in from step two's spread again
+    n_1 = n_t + int(d2.max())
+    return n_1, n_1 + int(d2.max())
+
+
+def _lengths_one_short(n_t, d1, d2):  # the last sample of step two's reads dropped
+    n_1 = n_t + int(d2.max()) - 1
+    return n_1, n_1 + int(d1.max())
+
+
+@pytest.mark.parametrize("attr,wrong,pins_to_run", [
+    ("coarse_index", _coarse_index_modulo, ["test_coarse_index_hand_example", "test_coarse_index_apertif_grid"]),
+    ("coarse_index", _coarse_index_nearest, ["test_coarse_index_hand_example", "test_coarse_index_apertif_grid"]),
+    ("coarse_index", _coarse_index_off_by_one, ["test_coarse_index_hand_example", "test_coarse_index_apertif_grid"]),
+    ("subband_lengths", _lengths_swapped, ["test_subband_lengths_hand_example", "test_subband_apertif_lengths"]),
+    ("subband_lengths", _lengths_step1_spread_twice,
+     ["test_subband_lengths_hand_example", "test_subband_apertif_lengths"]),
+    ("subband_lengths", _lengths_one_short, ["test_subband_lengths_hand_example", "test_subband_apertif_lengths"]),
+])
+def test_subband_helper_pin_fails(monkeypatch, attr, wrong, pins_to_run):
+    monkeypatch.setattr(oracle, attr, wrong)
+    caught = [name for name in pins_to_run if _run_pin(name, [()])]
+    assert caught, f"no pin caught the {attr} slip"

@@ -220,13 +220,68 @@ def test_subband_composition_identity(S):
     assert np.array_equal(D_sub[0], x[:, :b["n_t"]].astype(np.int64).sum(axis=0))
 
 
-def test_subband_apertif_lengths():
+def test_coarse_index_hand_example():
+    # k(i) = floor(i / (n_dms / n_coarse)): each coarse DM serves the block of
+    # consecutive fine trials that starts at it (Sec. 2, first footnote: step one
+    # at the coarse DM, step two at the trial's own DM).  Worked by hand.
+    assert oracle.coarse_index(8, 2).tolist() == [0, 0, 0, 0, 1, 1, 1, 1]
+    assert oracle.coarse_index(6, 3).tolist() == [0, 0, 1, 1, 2, 2]
+    assert oracle.coarse_index(5, 5).tolist() == [0, 1, 2, 3, 4]
+    assert oracle.coarse_index(4, 1).tolist() == [0, 0, 0, 0]
+
+
+def test_coarse_index_apertif_grid():
+    # The beam's two-step grid: 64 coarse DMs 6.4 apart, each followed by 32
+    # fine trials 0.2 apart, so DM_i = 6.4 k + 0.2 j with i = 32 k + j; the
+    # coarse DM of trial i is 6.4 floor(i / 32) and the fine offset 0.2 (i mod 32).
     wl = synth.apertif_beam(subband=True)
-    d1, d2 = oracle.subband_tables(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, 32, wl.coarse_dms,
-                                   wl.dms)
+    k = oracle.coarse_index(wl.dms.size, wl.coarse_dms.size)
+    i = np.arange(2048)
+    assert np.allclose(wl.coarse_dms[k], 6.4 * (i // 32), rtol=0, atol=1e-9)
+    assert np.allclose(wl.dms - wl.coarse_dms[k], 0.2 * (i % 32), rtol=0, atol=1e-9)
+    # each coarse DM lies at or below every trial it serves, and serves 32 of them
+    assert np.all(wl.coarse_dms[k] <= wl.dms + 1e-12)
+    assert np.array_equal(np.bincount(k), np.full(64, 32))
+
+
+def _exact_k(f_lo, f_hi, channels, t_samp, c, c_ref):
+    """Exact rational delay per unit DM of channel c against channel c_ref."""
+    F = Fraction
+    df = (F(f_hi) - F(f_lo)) / channels
+    fc = F(f_lo) + (F(c) + F(1, 2)) * df
+    fr = F(f_lo) + (F(c_ref) + F(1, 2)) * df
+    return F(oracle.K_DM) * (1 / (fc * fc) - 1 / (fr * fr)) / F(t_samp)
+
+
+def test_subband_lengths_hand_example():
+    # Step two reads Y[k][s][t + d2] for t < N_t, so N_1 = N_t + max d2; step one
+    # reads x[c][t' + d1] for t' < N_1, so N_in = N_1 + max d1.  By hand:
+    # N_t = 10, max d2 = 5 -> N_1 = 15; max d1 = 3 -> N_in = 18.
+    d1 = np.array([[0, 3], [1, 0]], np.int32)
+    d2 = np.array([[2], [5]], np.int32)
+    assert oracle.subband_lengths(10, d1, d2) == (15, 18)
+    assert oracle.subband_lengths(7, np.zeros((1, 4), np.int32), np.array([[9]], np.int32)) == (16, 16)
+
+
+def test_subband_apertif_lengths():
+    # The beam's subband path from the delay law in exact rationals: the largest
+    # step-one delay is at the largest coarse DM (403.2), the largest step-two
+    # delay at the largest trial DM (409.4): 190 and 4444 samples, so
+    # N_1 = 12500 + 4444 = 16944 and N_in = 16944 + 190 = 17134.
+    wl = synth.apertif_beam(subband=True)
+    C, S = wl.channels, 32
+    per = C // S
+    d1, d2 = oracle.subband_tables(wl.f_lo, wl.f_hi, C, wl.t_samp, S, wl.coarse_dms, wl.dms)
     assert (d1.shape, d2.shape) == ((64, 1536), (2048, 32))
-    n_1, n_in = oracle.subband_lengths(wl.n_t, d1, d2)
-    assert n_1 - wl.n_t == d2.max() and n_in - n_1 == d1.max()
+    exact_d1 = max(_round_half_away(Fraction(float(wl.coarse_dms[-1])) *
+                                    _exact_k(wl.f_lo, wl.f_hi, C, wl.t_samp, c, (c // per + 1) * per - 1))
+                   for c in range(C))
+    exact_d2 = max(_round_half_away(Fraction(float(wl.dms[-1])) *
+                                    _exact_k(wl.f_lo, wl.f_hi, C, wl.t_samp, (s + 1) * per - 1, C - 1))
+                   for s in range(S))
+    assert (exact_d1, exact_d2) == (190, 4444)
+    assert (int(d1.max()), int(d2.max())) == (190, 4444)
+    assert oracle.subband_lengths(wl.n_t, d1, d2) == (16944, 17134)
 
 
 # --------------------------------------------------------------------------- boxcar
