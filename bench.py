@@ -221,14 +221,39 @@ def cpu_oracle_tiny():
 
 
 def cpu_oracle_all_cores(wl, x, threads):
-    """DM-trial samples/s of the oracle on every host core, over the whole batch."""
+    """DM-trial samples/s of the oracle on every host core, over the whole batch,
+    and its (snr, peak_t, peak_val) tables [n_widths, n_dms]."""
     import oracle
     d = oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms)
     rows = np.arange(wl.dms.size)
     t0 = time.perf_counter()
-    oracle_rows_threaded(x, d, rows, wl.n_t, wl.widths, threads)
+    parts = oracle_rows_threaded(x, d, rows, wl.n_t, wl.widths, threads)
     dt = time.perf_counter() - t0
-    return rows.size * wl.n_t / dt, dt
+    tables = tuple(np.concatenate([r[k] for r in parts], axis=1) for k in range(3))
+    return rows.size * wl.n_t / dt, dt, tables
+
+
+def check_outputs(wl, x, out, tables, n_rows=12):
+    """The pipelined run's outputs for input x against the oracle: the whole
+    S/N table (relative 1e-5), peak_t and peak_val (exact), the detection, and
+    `n_rows` rows of D (exact)."""
+    import oracle
+    s, pt, pv = tables
+    bi, bw = oracle.detect(s)
+    rows = np.unique(np.linspace(0, wl.dms.size - 1, n_rows).astype(np.int64))
+    d = oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms)
+    D_rows = oracle.dedisperse(x, d[rows], wl.n_t)
+    g_s = out["snr"].cpu().numpy()
+    err = np.abs(g_s - s)
+    res = {"snr_entries": int(s.size), "D_rows": int(rows.size),
+           "snr_ok": bool(np.all(err <= 1e-5 * np.abs(s) + 1e-9)),
+           "max_rel_err": float(np.max(err / np.maximum(np.abs(s), 1e-300))),
+           "peaks_ok": bool(np.array_equal(out["peak_t"].cpu().numpy(), pt) and
+                            np.array_equal(out["peak_val"].cpu().numpy(), pv)),
+           "best_ok": out["best"].cpu().numpy().tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])],
+           "D_ok": bool(np.array_equal(out["D"].cpu().numpy()[rows], D_rows))}
+    res["ok"] = res["snr_ok"] and res["peaks_ok"] and res["best_ok"] and res["D_ok"]
+    return res
 
 
 def cpu_oracle_rate(wl, x, target_s=12.0, max_rows=None):
@@ -296,7 +321,9 @@ def workload_config(wl, mode):
 def time_pipelined(torch, plan, xs, steps, warmup, n_streams=2):
     """Whole-job CUDA-event time (ms) of `steps` batches, each searched in full
     (sps_search) on the next of `n_streams` streams with its own workspace and
-    outputs, so consecutive batches overlap; inputs rotate through xs."""
+    outputs, so consecutive batches overlap; inputs rotate through xs.  Also
+    returns, per stream, the outputs its last timed batch left and that
+    batch's input index (checked against the oracle afterwards)."""
     import paper_1811_04165_gb300 as sps
     streams = [torch.cuda.Stream() for _ in range(n_streams)]
     outs = [plan.alloc_outputs() for _ in range(n_streams)]
@@ -323,7 +350,11 @@ def time_pipelined(torch, plan, xs, steps, warmup, n_streams=2):
         cur.wait_event(ev)
     e1.record(cur)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1)
+    held = []
+    for i in range(min(n_streams, steps)):
+        last = max(s for s in range(steps) if s % n_streams == i)
+        held.append((last, outs[i], (warmup + last) % len(xs)))
+    return e0.elapsed_time(e1), held
 
 
 def e2e_pipelined(torch, plan, xh, steps, warmup, device, n_workers=3):
@@ -432,7 +463,7 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        pipe_ms = time_pipelined(torch, plan, xs, args.steps, args.warmup)
+        pipe_ms, held = time_pipelined(torch, plan, xs, args.steps, args.warmup)
         times = time_path(torch, plan, xs, outs, args.steps, args.warmup, None, flush)
     barrier(world)
     dedisp_ms = [a for a, _ in times]
@@ -526,11 +557,18 @@ def main():
                           "every step copies its pinned batch in and its S/N tables and detection out",
                    "sequential_ms_per_step": 1e3 * e2e_seq / args.steps}
 
-    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1); its
+    # whole-batch run is on the input of the pipelined run's last batch, whose
+    # outputs are then checked against it
+    parity_ok = True
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, rows = cpu_oracle_rate(wl, xs_host[0])
+        _, held_out, held_b = max(held, key=lambda h: h[0])
+        rate, dt, rows = cpu_oracle_rate(wl, xs_host[held_b])
         threads = host_threads()
-        rate_all, dt_all = cpu_oracle_all_cores(wl, xs_host[0], threads)
+        rate_all, dt_all, tables = cpu_oracle_all_cores(wl, xs_host[held_b], threads)
+        line["parity"] = dict(check_outputs(wl, xs_host[held_b], held_out, tables), batch=held_b,
+                              what="the last timed batch of the pipelined run against the oracle")
+        parity_ok = line["parity"]["ok"]
         line["cpu_baseline"] = {"value": rate_all, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"the whole batch ({wl.dms.size} DM trials), dedispersion + S/N, DM rows "
                                           f"split over {threads} threads: {dt_all:.1f} s",
@@ -547,6 +585,8 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    if not parity_ok:
+        sys.exit("bench: the timed run's outputs differ from the oracle")
 
 
 if __name__ == "__main__":

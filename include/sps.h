@@ -184,9 +184,11 @@ sps_status sps_dedisperse(const sps_plan* plan, const uint8_t* x, int64_t x_pitc
  * Allocates nothing.  Every device that loads this entry point keeps the
  * array until the process exits.  All calls on a device share the array:
  * calls whose work overlaps on the GPU (other streams or threads) race and
- * corrupt each other's results.  The first call on each device looks up the
- * array's device address (with the plan's device current, which is required)
- * and should come before any stream capture. */
+ * corrupt each other's results.  Every call looks up the array's device
+ * address (with the plan's device current, which is required); the first call
+ * on each device loads the array there and should come before any stream
+ * capture.  Nothing is cached, so the entry point stays valid after a device
+ * reset. */
 sps_status sps_dedisperse_noalloc(const sps_plan* plan, const uint8_t* x, int64_t x_pitch, int32_t* D,
                                   void* stream);
 

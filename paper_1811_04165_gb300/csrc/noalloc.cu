@@ -16,12 +16,12 @@
 //     nothing in it needs to start at zero (the kernels overwrite all they
 //     read), but two calls whose work overlaps on the GPU (different streams,
 //     or different host threads) race on it and corrupt each other's results;
-//   * host code cannot use the array's name as a device address; the first
-//     call on each device looks the address up (cudaGetSymbolAddress) with
-//     that device current and caches it, so that first call should come before
-//     any stream capture.
-#include <mutex>
-
+//   * host code cannot use the array's name as a device address; every call
+//     looks the address up (cudaGetSymbolAddress) with the plan's device
+//     current.  The first call on a device loads the array there, so that first
+//     call should come before any stream capture.  Later lookups are cheap, and
+//     because none is cached, a device reset (which reloads the module,
+//     possibly at another address) never leaves a stale address behind.
 #include "sps_internal.h"
 
 namespace sps {
@@ -32,24 +32,15 @@ namespace {
 // 79 MB), not for the pre-summed pair or quad series (236 or 614 MB) nor for
 // the subband path.
 constexpr size_t kStaticScratchBytes = size_t(96) << 20;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_mutex;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on the current device (set up once per device).
-sps_status static_scratch(int device, void** out) {
-  if (device < 0 || device >= kMaxDevices) return fail(SPS_ERR_UNSUPPORTED, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[device]) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
-    g_scratch_ptr[device] = ptr;
-  }
-  *out = g_scratch_ptr[device];
+// Device address of g_static_scratch on the current device.
+sps_status static_scratch(void** out) {
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+  *out = ptr;
   return SPS_OK;
 }
 
@@ -71,6 +62,6 @@ extern "C" sps_status sps_dedisperse_noalloc(const sps_plan* plan, const uint8_t
   SPS_CUDA(cudaGetDevice(&device));
   if (device != plan->device) return fail(SPS_ERR_INVALID_ARG, "the plan's device must be the current device");
   void* scratch = nullptr;
-  if (sps_status s = static_scratch(device, &scratch)) return s;
+  if (sps_status s = static_scratch(&scratch)) return s;
   return dedisperse_into(plan, x, x_pitch, D, scratch, kStaticScratchBytes, (cudaStream_t)stream);
 }

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from paper_1811_04165_gb300 import synth
+from tests import oracle_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -232,40 +233,42 @@ def test_quads_with_long_relative_delays(lib):
     assert np.array_equal(_to_np(D), oracle.dedisperse(x, d, 100))
 
 
-@pytest.mark.parametrize("presum", [0, 1, 2])
-def test_apertif_brute_sampled_rows(lib, presum):
-    """Full Apertif-shaped beam in the launch configurations the benchmark times."""
-    torch = _torch()
+@pytest.fixture(scope="module")
+def apertif_brute_oracle():
+    """The beam's input and the oracle's whole-table results: D, S/N, peaks and
+    the detection over all 2048 DM trials (rows split over the host cores)."""
     wl = synth.apertif_beam()
+    d = oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms)
+    n_in = wl.n_t + int(d.max())
+    pitch = (n_in + 15) // 16 * 16
+    x = synth.filterbank(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, n_in, wl.seed, wl.pulses, pitch=pitch)
+    D = oracle_rows.dedisperse(x, d, wl.n_t)
+    s, pt, pv = oracle_rows.snr(D, wl.widths)
+    return wl, x, D, s, pt, pv, oracle.detect(s)
+
+
+@pytest.mark.parametrize("presum", [0, 1, 2])
+def test_apertif_brute_full_tables(lib, apertif_brute_oracle, presum):
+    """The full Apertif-shaped beam in the launch configurations the benchmark
+    times: every row of D, every (width, DM) entry of the S/N, peak_t and
+    peak_val tables, and the detection against the oracle's over the whole table."""
+    torch = _torch()
+    wl, x, Do, s, pt, pv, (bi, bw) = apertif_brute_oracle
     p = lib.Plan.from_workload(wl)
+    assert p.pitch == x.shape[1]
     c = p.config
     c.brute.presum = presum
     p.config = c
-    x = _x_for(p, wl)
     out = p.search(torch.from_numpy(x).cuda())
     torch.cuda.synchronize()
-    D = _to_np(out["D"])
-    d = oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms)
-    rng = np.random.Generator(np.random.PCG64(7))
-    rows = np.unique(np.concatenate([[0, 1, 31, 32, 2047], rng.integers(0, 2048, 11)]))
-    want = oracle.dedisperse(x, d[rows], wl.n_t)
-    assert np.array_equal(D[rows], want)
-    # DM 0 is the plain channel sum at any size
-    assert np.array_equal(D[0], x[:, :wl.n_t].astype(np.int64).sum(axis=0))
-    s, pt, pv = oracle.snr(want, wl.widths)
-    _check_snr(_to_np(out["snr"])[:, rows], _to_np(out["peak_t"])[:, rows], _to_np(out["peak_val"])[:, rows],
-               s, pt, pv)
-    # the strongest injected pulse is the detection
-    best = _to_np(out["best"])
+    assert np.array_equal(_to_np(out["D"]), Do)
+    _check_snr(_to_np(out["snr"]), _to_np(out["peak_t"]), _to_np(out["peak_val"]), s, pt, pv)
+    assert _to_np(out["best"]).tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])]
+    # the detection is the strongest injected pulse
     strongest = max(wl.pulses, key=lambda q: q.amp * np.sqrt(q.width))
-    assert abs(wl.dms[best[0]] - strongest.dm) <= 0.2 + 1e-9
-    assert abs(best[2] - strongest.t0) <= strongest.width
-    # the detection agrees with the oracle over a window of trials around it
-    lo, hi = max(best[0] - 8, 0), min(best[0] + 9, 2048)
-    wd = oracle.dedisperse(x, d[lo:hi], wl.n_t)
-    ws, wpt, wpv = oracle.snr(wd, wl.widths)
-    oi, ow = oracle.detect(ws)
-    assert (best[0], best[1]) == (lo + oi, ow)
+    assert abs(wl.dms[bi] - strongest.dm) <= 0.2 + 1e-9
+    assert abs(int(pt[bw, bi]) - strongest.t0) <= strongest.width
+    assert p.status() == 0
 
 
 # ----------------------------------------------------------------------------- subband
@@ -357,33 +360,45 @@ def test_subband_presum_ignores_stale_workspace(lib, presum):
     assert np.array_equal(_to_np(D), Do)
 
 
-@pytest.mark.parametrize("presum", [0, 1, 2])
-def test_apertif_subband_sampled(lib, presum):
-    torch = _torch()
+@pytest.fixture(scope="module")
+def apertif_subband_oracle():
+    """The beam's two-step path in the oracle: Y over all 64 coarse DMs, D over
+    all 2048 trials, the S/N tables and the detection."""
     wl = synth.apertif_beam(subband=True)
+    d1, d2 = oracle.subband_tables(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.n_subbands, wl.coarse_dms,
+                                   wl.dms)
+    n_1, n_in = oracle.subband_lengths(wl.n_t, d1, d2)
+    pitch = (n_in + 15) // 16 * 16
+    x = synth.filterbank(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, n_in, wl.seed, wl.pulses, pitch=pitch)
+    k = oracle.coarse_index(wl.dms.size, wl.coarse_dms.size)
+    Y = oracle_rows.subband_step1(x, d1, wl.n_subbands, n_1)
+    D = oracle_rows.subband_step2(Y, d2, k, wl.n_t)
+    s, pt, pv = oracle_rows.snr(D, wl.widths)
+    return wl, x, n_1, Y, D, s, pt, pv, oracle.detect(s)
+
+
+@pytest.mark.parametrize("presum", [0, 1, 2])
+def test_apertif_subband_full_tables(lib, apertif_subband_oracle, presum):
+    """Every element of Y and D, the S/N tables and the detection of the beam's
+    two-step path against the oracle."""
+    torch = _torch()
+    wl, x, n_1, Yo, Do, s, pt, pv, (bi, bw) = apertif_subband_oracle
     p = lib.Plan.from_workload(wl)
+    assert p.pitch == x.shape[1] and p.step1_samples == n_1
     c = p.config
     # quads on the widely spaced coarse trials: smaller DM tiles keep a chunk's tuples in shared memory
     c.step1 = lib.DedispConfig(1, 16, 8, 1, 8, 2) if presum == 2 else lib.DedispConfig(4, 16, 8, 1, 16, presum)
     p.config = c
-    x = _x_for(p, wl)
     xd = torch.from_numpy(x).cuda()
     Y = torch.empty(p.y_shape, dtype=torch.uint16, device="cuda")
     lib.sps_subband_step1(p, xd, Y)
     out = p.search(xd)
     torch.cuda.synchronize()
-    d1, d2 = oracle.subband_tables(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, 32, wl.coarse_dms, wl.dms)
-    n_1, _ = oracle.subband_lengths(wl.n_t, d1, d2)
-    ks = [0, 17, 63]
-    Yo = oracle.subband_step1(x, d1[ks], 32, n_1)
-    assert np.array_equal(_to_np(Y)[ks, :, :n_1].astype(np.int32), Yo)
-    rows = np.array([0, 5, 31, 32, 1000, 2016, 2047])
-    k = oracle.coarse_index(2048, 64)
-    Yfull = np.zeros((64, 32, n_1), np.int32)
-    need = np.unique(k[rows])
-    Yfull[need] = oracle.subband_step1(x, d1[need], 32, n_1)
-    Do = oracle.subband_step2(Yfull, d2[rows], k[rows], wl.n_t)
-    assert np.array_equal(_to_np(out["D"])[rows], Do)
+    assert np.array_equal(_to_np(Y)[:, :, :n_1].astype(np.int32), Yo)
+    assert np.array_equal(_to_np(out["D"]), Do)
+    _check_snr(_to_np(out["snr"]), _to_np(out["peak_t"]), _to_np(out["peak_val"]), s, pt, pv)
+    assert _to_np(out["best"]).tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])]
+    assert p.status() == 0
 
 
 # ----------------------------------------------------------------------------- boxcar, S/N

@@ -1,8 +1,11 @@
 """Real-time serving through the C ABI (`sps_server_*`): streamed batches with
 device-resident overlap tails must give exactly what an offline search of the
-same overlap-save window gives; admission respects the HBM budget."""
+same overlap-save window gives, and what the oracle gives on that window;
+admission respects the HBM budget."""
 import numpy as np
 import pytest
+
+import oracle
 
 from paper_1811_04165_gb300 import synth
 
@@ -61,6 +64,11 @@ def test_streamed_batches_equal_offline_windows(lib, inflight):
         torch.cuda.synchronize()
         assert np.array_equal(snr, o["snr"].cpu().numpy()), (b, k)
         assert np.array_equal(best, o["best"].cpu().numpy()), (b, k)
+        # and what the oracle computes on that window
+        _, so, pto, pvo, (bi, bw) = oracle.search_brute(np.ascontiguousarray(window), wl.f_lo, wl.f_hi, wl.t_samp,
+                                                        wl.dms, wl.widths, wl.n_t)
+        assert np.all(np.abs(snr - so) <= 1e-5 * np.abs(so) + 1e-9), (b, k)
+        assert best.tolist() == [bi, bw, int(pto[bw, bi]), int(pvo[bw, bi])], (b, k)
     # completion times are on the server clock and ordered per beam
     for b in range(len(plans)):
         ts = [done[t] for t, bb, *_ in subs if bb == b]

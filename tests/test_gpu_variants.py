@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 from paper_1811_04165_gb300 import synth
+from tests import oracle_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -93,7 +94,8 @@ def test_zapping_in_subband_mode(lib):
 
 def test_apertif_beam_decimated_and_zapped(lib):
     """The full beam with the paper's downsampling range (Table 2: 10 .. 3200)
-    plus the raw series, and an RFI mask: sampled rows against the oracle."""
+    plus the raw series, and an RFI mask: every row of D and every S/N, peak and
+    the detection against the oracle."""
     import torch
     base = synth.apertif_beam()
     rng = np.random.Generator(np.random.PCG64(99))
@@ -106,12 +108,13 @@ def test_apertif_beam_decimated_and_zapped(lib):
     x = _x(p, wl)
     out = p.search(torch.from_numpy(x).cuda(), workspace=p.workspace())
     torch.cuda.synchronize()
-    rows = np.array([0, 1, 700, 1500, 2047])
-    d = oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms)[rows]
-    want = oracle.dedisperse(oracle.zap_channels(x, zap), d, wl.n_t)
-    assert np.array_equal(out["D"].cpu().numpy()[rows], want)
-    s, pt, pv = oracle.snr_decimated(want, factors)
-    assert np.allclose(out["snr"].cpu().numpy()[:, rows], s, rtol=1e-5, atol=1e-9)
-    assert np.array_equal(out["peak_t"].cpu().numpy()[:, rows], pt)
-    assert np.array_equal(out["peak_val"].cpu().numpy()[:, rows], pv)
+    d = oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms)
+    want = oracle_rows.dedisperse(oracle.zap_channels(x, zap), d, wl.n_t)
+    assert np.array_equal(out["D"].cpu().numpy(), want)
+    s, pt, pv = oracle_rows.snr_decimated(want, factors)
+    assert np.allclose(out["snr"].cpu().numpy(), s, rtol=1e-5, atol=1e-9)
+    assert np.array_equal(out["peak_t"].cpu().numpy(), pt)
+    assert np.array_equal(out["peak_val"].cpu().numpy(), pv)
+    bi, bw = oracle.detect(s)
+    assert out["best"].cpu().numpy().tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])]
     assert p.status() == 0
