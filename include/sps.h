@@ -374,42 +374,74 @@ sps_status sps_batch_destroy(sps_batch* batch);
  * ALERT searches every beam's 1.024 s of data within 1.024 s).  Not in the
  * paper; a library runtime.  Single-threaded: one host thread calls every
  * entry point of a server.
- *   - Admission: a beam is admitted when its device footprint (two input
- *     buffers, D, the S/N tables, and, if it needs a larger one, its share of
- *     the workspace slots) fits `hbm_budget_bytes`; otherwise UNSUPPORTED.
- *   - Overlap tails: each beam keeps its input device-resident in two buffers
- *     used alternately; a batch's buffer starts with the previous batch's last
- *     N_in - N_t samples (zeros before the first batch), so every batch is
- *     searched over N_t new samples plus the delay tail.
- *   - sps_server_submit and sps_server_poll dispatch queued batches in
- *     arrival order onto `max_inflight` concurrent slots (stream + workspace),
- *     a beam's batches one at a time and in order; each runs the tail copy, the
- *     host-to-device copy of the new samples, sps_search and the copies of the
- *     S/N table and best back to the host pointers given at submission, which
- *     must stay valid until the batch is reported complete.
+ *   - Memory: the server allocates one device arena of `hbm_budget_bytes` at
+ *     creation and nothing afterwards.  Each beam keeps only its overlap tail
+ *     there between batches ([channels][N_in - N_t] bytes).  A batch takes its
+ *     input buffer, D, S/N tables and workspace from the arena when it is
+ *     dispatched and returns them when it completes.
+ *   - Admission: sps_server_add_beam admits a beam when its tail, plus one
+ *     batch of it, fits beside the tails already resident (UNSUPPORTED
+ *     otherwise).  Queued batches are admitted at dispatch time, in arrival
+ *     order and each beam's in order, as slots and arena memory free up; a
+ *     batch that does not fit yet waits, and later batches of other beams
+ *     that fit may pass it.
+ *   - Overlap tails: a batch is searched over its beam's tail (zeros before the
+ *     first batch) followed by its N_t new samples; its window's last
+ *     N_in - N_t samples become the tail of the beam's next batch.
+ *   - Each batch runs on one of `max_inflight` concurrent slots (streams): the
+ *     tail copy, the host-to-device copy of the new samples, sps_search and
+ *     the copies of the S/N table and best back to the host pointers given at
+ *     submission, which must stay valid until poll reports the batch.
  *   - Times are seconds on the host's steady clock; a completion time is the
  *     GPU-timeline end of the batch's last copy, mapped to that clock. */
 typedef struct sps_server sps_server;
 typedef struct {
-  size_t hbm_budget_bytes;  /* device bytes the server may allocate            */
+  size_t hbm_budget_bytes;  /* the arena: every device byte the server uses     */
   int32_t max_inflight;     /* concurrent batches (1 = one batch at a time)    */
 } sps_server_desc;
+typedef struct {
+  size_t budget_bytes;      /* arena size                                      */
+  size_t used_bytes;        /* tails + batches in flight                       */
+  size_t resident_bytes;    /* overlap tails                                   */
+  size_t batch_bytes;       /* blocks of the batches in flight                 */
+  int32_t inflight;         /* batches on the GPU                              */
+  int32_t queued;           /* batches waiting for their beam, a slot or memory */
+  int64_t admitted;         /* batches dispatched so far                       */
+  int64_t waits_for_memory; /* dispatch attempts that found the arena too full */
+  int64_t failed;           /* batches reported with an error status           */
+} sps_server_stats;
+/* Creates a server on the current device; OOM when the arena cannot be
+ * allocated. */
 sps_status sps_server_create(const sps_server_desc* desc, sps_server** out);
 /* Admits a beam searched with `plan` (which must outlive the server and keep
- * its configuration); beam ids count from 0. */
+ * its configuration); beam ids count from 0 and are never reused. */
 sps_status sps_server_add_beam(sps_server* server, const sps_plan* plan, int32_t* beam_id);
+/* Removes a beam: further submissions are refused (INVALID_ARG); batches
+ * already queued or in flight still run and are reported; its tail returns
+ * to the arena once none is left. */
+sps_status sps_server_remove_beam(sps_server* server, int32_t beam_id);
 /* Queues one batch of a beam: host uint8 [channels][host_pitch], N_t new
  * samples per channel (pinned memory keeps the copy asynchronous).  snr_host:
- * double [n_widths][n_dms]; best_host: int32[4] (either may be NULL). */
+ * double [n_widths][n_dms]; best_host: int32[4] (either may be NULL).
+ * Every check happens before the batch is queued: a non-OK status means it
+ * was refused and nothing of it remains.  OK means it is queued, and its
+ * outcome -- completion, or an error when it was dispatched -- is reported
+ * by sps_server_poll under `tag`.  Then dispatches what it can. */
 sps_status sps_server_submit(sps_server* server, int32_t beam_id, const uint8_t* host_x, int64_t host_pitch,
                              double* snr_host, int32_t* best_host, uint64_t tag);
-/* Dispatches what it can, then reports up to `max` completed batches (tags
- * and completion times) in completion-check order; *n = how many. */
-sps_status sps_server_poll(sps_server* server, uint64_t* tags, double* done_s, int32_t max, int32_t* n);
-/* Batches queued or in flight. */
+/* Collects completed batches, dispatches what it can, then reports up to
+ * `max` finished batches (oldest first): tags, completion times and, if
+ * `status` is not NULL, each batch's status (OK, or the error that stopped
+ * it).  *n = how many; batches beyond `max` stay for the next call. */
+sps_status sps_server_poll(sps_server* server, uint64_t* tags, double* done_s, sps_status* status, int32_t max,
+                           int32_t* n);
+/* Batches queued, in flight, or finished and not yet reported. */
 sps_status sps_server_pending(const sps_server* server, int32_t* n);
+/* Arena occupancy and counters. */
+sps_status sps_server_get_stats(const sps_server* server, sps_server_stats* out);
 /* The host steady clock in seconds (the clock of submission and completion times). */
 double sps_server_clock(void);
+/* Waits for the batches in flight, then frees the arena; queued batches are dropped. */
 sps_status sps_server_destroy(sps_server* server);
 
 /* ---------------------------------------------------------------- misc */

@@ -473,9 +473,29 @@ class ServerDesc(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t),
+                ("resident_bytes", ctypes.c_size_t), ("batch_bytes", ctypes.c_size_t),
+                ("inflight", ctypes.c_int32), ("queued", ctypes.c_int32), ("admitted", ctypes.c_int64),
+                ("waits_for_memory", ctypes.c_int64), ("failed", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+@dataclass
+class Completion:
+    """One finished batch as sps_server_poll reports it: its tag, its completion
+    time on the server clock, and its status (SPS_OK, or the error that
+    stopped it when it was dispatched)."""
+    tag: int
+    done_s: float
+    status: int
+
+
 class Server:
     """Real-time serving of streaming beams (`sps_server_*`).  Host buffers
-    handed to submit() must stay alive until poll() reports their tag."""
+    handed to submit() stay referenced here until poll() reports their tag."""
 
     def __init__(self, hbm_budget_bytes, max_inflight=4):
         h = ctypes.c_void_p()
@@ -490,6 +510,11 @@ class Server:
         check(_L.sps_server_add_beam(self.handle, plan.handle, ctypes.byref(b)), "sps_server_add_beam")
         self.plans.append(plan)
         return b.value
+
+    def remove_beam(self, beam):
+        """No further batches for this beam; its queued and in-flight batches
+        still run; its overlap tail returns to the arena once they are done."""
+        check(_L.sps_server_remove_beam(self.handle, int(beam)), "sps_server_remove_beam")
 
     def submit(self, beam, x_host, snr_host=None, best_host=None, tag=0):
         """x_host: uint8 array [channels][pitch >= N_t] (pinned torch tensor or numpy)."""
@@ -520,24 +545,33 @@ class Server:
         self._keep[int(tag)] = (x_host, snr_host, best_host)
         st = _L.sps_server_submit(self.handle, int(beam), ptr(x_host), pitch, ptr(snr_host), ptr(best_host),
                                   ctypes.c_uint64(int(tag)))
-        if st == SPS_ERR_INVALID_ARG:  # refused before anything was queued
+        if st != SPS_OK:  # refused before it was queued: nothing of it remains in the library
             self._keep.pop(int(tag), None)
         check(st, "sps_server_submit")
 
     def poll(self, max_n=256):
+        """Finished batches as a list of Completion (oldest first).  A batch
+        whose dispatch failed is reported with its error status, not raised:
+        every submitted tag is reported exactly once."""
         tags = (ctypes.c_uint64 * max_n)()
         done = (ctypes.c_double * max_n)()
+        status = (ctypes.c_int32 * max_n)()
         n = ctypes.c_int32()
-        check(_L.sps_server_poll(self.handle, tags, done, int(max_n), ctypes.byref(n)), "sps_server_poll")
-        out = [(int(tags[i]), float(done[i])) for i in range(n.value)]
-        for t, _ in out:
-            self._keep.pop(t, None)
+        check(_L.sps_server_poll(self.handle, tags, done, status, int(max_n), ctypes.byref(n)), "sps_server_poll")
+        out = [Completion(int(tags[i]), float(done[i]), int(status[i])) for i in range(n.value)]
+        for c in out:
+            self._keep.pop(c.tag, None)
         return out
 
     def pending(self) -> int:
         n = ctypes.c_int32()
         check(_L.sps_server_pending(self.handle, ctypes.byref(n)), "sps_server_pending")
         return n.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        check(_L.sps_server_get_stats(self.handle, ctypes.byref(st)), "sps_server_get_stats")
+        return st.as_dict()
 
     @staticmethod
     def clock() -> float:

@@ -42,7 +42,9 @@ SIGNATURES = {
     "sps_server_create": (_I32, [_P, _P]),
     "sps_server_add_beam": (_I32, [_P, _P, _P]),
     "sps_server_submit": (_I32, [_P, _I32, _P, _I64, _P, _P, ctypes.c_uint64]),
-    "sps_server_poll": (_I32, [_P, _P, _P, _I32, _P]),
+    "sps_server_remove_beam": (_I32, [_P, _I32]),
+    "sps_server_poll": (_I32, [_P, _P, _P, _P, _I32, _P]),
+    "sps_server_get_stats": (_I32, [_P, _P]),
     "sps_server_pending": (_I32, [_P, _P]),
     "sps_server_clock": (ctypes.c_double, []),
     "sps_server_destroy": (_I32, [_P]),

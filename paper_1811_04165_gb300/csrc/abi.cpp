@@ -437,6 +437,6 @@ const char* sps_status_string(sps_status s) {
 
 const char* sps_last_error(void) { return g_last_error.c_str(); }
 
-int32_t sps_abi_version(void) { return 103; }
+int32_t sps_abi_version(void) { return 104; }
 
 }  // extern "C"

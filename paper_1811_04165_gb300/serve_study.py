@@ -71,16 +71,16 @@ def run(plans, host_x, period, duration, inflight, seed, budget):
     for k, (t, b) in enumerate(ev):
         due = t0 + t
         while Server.clock() < due:
-            for tag, s in srv.poll():
-                done[tag] = s
+            for c in srv.poll():
+                done[c.tag] = c.done_s
         tag = 1_000_000 + k
         arrive[tag] = due
         srv.submit(ids[b], host_x[plans[b].channels], snr[b], best[b], tag=tag)
     while srv.pending():
-        for tag, s in srv.poll():
-            done[tag] = s
-    for tag, s in srv.poll():
-        done[tag] = s
+        for c in srv.poll():
+            done[c.tag] = c.done_s
+    for c in srv.poll():
+        done[c.tag] = c.done_s
     lat = np.array([done[t] - arrive[t] for t in arrive])
     span = max(done.values()) - t0
     return {"batches": int(lat.size), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
