@@ -405,6 +405,14 @@ def e2e_pipelined(torch, plan, xh, steps, warmup, device, n_workers=3):
     return time.perf_counter() - t0
 
 
+def launches_per_step(plan):
+    """Kernels of one brute-force search: the pre-pass (pre-summed series, or the
+    shifted copies) and the pass, then the S/N kernel -- with the detection
+    folded in for power-of-two widths, else followed by the detection kernel."""
+    pow2 = list(plan.widths) == [1 << k for k in range(plan.n_widths)] and plan.n_widths <= 7
+    return 2 + (1 if pow2 and plan.smoothing == 0 else 2)
+
+
 def time_path(torch, plan, xs, outs, steps, warmup, ws, flush, with_events=True):
     """Per-step CUDA-event times (ms) of [dedisperse, snr+detect] on the current stream."""
     import paper_1811_04165_gb300 as sps
@@ -510,7 +518,7 @@ def main():
             "sequential_step_ms": {"median": statistics.median(step_ms),
                                    "p10": float(np.percentile(step_ms, 10)),
                                    "p90": float(np.percentile(step_ms, 90))},
-            "real_time_beams": 1024.0 / ms_per_step, "gpu_launches": 4 * args.steps,
+            "real_time_beams": 1024.0 / ms_per_step, "gpu_launches": launches_per_step(plan) * args.steps,
             "roofline": roofline, "clocks": clk.summary()}
 
     # ---- the two-step subband path on the same batch

@@ -205,9 +205,12 @@ sps_status run_snr(const sps_plan* p, const int32_t* D, double* snr, int32_t* pe
   a.peak_t = peak_t;
   a.peak_val = peak_val;
   a.decimate = p->smoothing == SPS_SMOOTH_DECIMATE ? 1 : 0;
-  sps_status s = launch_snr(a, p->cfg.snr, st);
-  if (s || !best) return s;
-  return launch_detect(snr, peak_t, peak_val, a.n_dms, a.n_widths, best, st);
+  a.pow2_widths = 0;
+  bool pow2 = p->widths.size() <= 30;
+  for (size_t k = 0; k < p->widths.size() && pow2; k++) pow2 = p->widths[k] == (1 << k);
+  if (pow2) a.pow2_widths = (int32_t)p->widths.size();
+  a.best = best;
+  return launch_snr(a, p->cfg.snr, st);
 }
 
 }  // namespace

@@ -340,9 +340,12 @@ __device__ __forceinline__ bool better(double v, int i, int w, double bv, int bi
   return w < bw;
 }
 
-__global__ void __launch_bounds__(1024, 1)
-detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val, int n_dms, int n_widths,
-              int32_t* best) {
+// The detection over the whole S/N table by one block (any multiple of 32
+// threads); `ld` reads through L2 when other blocks of the same launch wrote
+// the table.
+template <bool L2>
+__device__ void detect_block(const double* snr, const int32_t* peak_t, const int32_t* peak_val, int n_dms,
+                             int n_widths, int32_t* best) {
   __shared__ double sv[32];
   __shared__ int si[32], sw[32];
   double bv = -1.0;
@@ -351,7 +354,7 @@ detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
   for (int w = 0; w < n_widths; w++) {
     const double* row = snr + (int64_t)w * n_dms;
     for (int i = threadIdx.x; i < n_dms; i += blockDim.x) {
-      const double v = __ldg(row + i);
+      const double v = L2 ? __ldcg(row + i) : __ldg(row + i);
       if (better(v, i, w, bv, bi, bw)) { bv = v; bi = i; bw = w; }
     }
   }
@@ -378,9 +381,170 @@ detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
       const int64_t o = (int64_t)bw * n_dms + bi;
       best[0] = bi;
       best[1] = bw;
-      best[2] = peak_t[o];
-      best[3] = peak_val[o];
+      best[2] = L2 ? __ldcg(peak_t + o) : peak_t[o];
+      best[3] = L2 ? __ldcg(peak_val + o) : peak_val[o];
     }
+  }
+}
+
+__global__ void __launch_bounds__(1024, 1)
+detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val, int n_dms, int n_widths,
+              int32_t* best) {
+  detect_block<false>(snr, peak_t, peak_val, n_dms, n_widths, best);
+}
+
+// ---------------------------------------------------------------------------
+// Register-window form for width sets {1, 2, 4, ..., 2^(NW-1)} (the
+// smoothing widths of the search; AMBER's are powers of two as well).
+//
+// The row is staged and scanned into prefix sums as above (P[k] at buf[3 + k]).
+// Then each thread takes segments of S consecutive outputs t = t0 .. t0 + S - 1
+// (t0 = seg * S - 3, so the window's first word is 16-byte aligned) and loads
+// the window P[t0 .. t0 + S + 2^(NW-1)) into registers with 16-byte shared
+// loads (S / 4 odd: conflict-free).  With the widths known at compile time,
+// every boxcar is one register subtraction B = P[t + w] - P[t], and each
+// (sample, width) costs a subtract and a maximum on the integer ALU and one
+// 32 x 32 -> 64-bit multiply-add on the FMA pipe -- no shared-memory access.
+// Outputs outside [0, N_t - w] contribute B = 0 (neither the sum of squares
+// nor the maximum changes).  S1 comes in closed form as in snr_kernel.
+//
+// Detection is folded in: `best` (int32[4]) is zeroed before the launch; each
+// block, once its outputs are written, counts itself in best[3]; the block
+// that counts last reads the whole table (through L2) and writes the
+// detection over the counter.
+constexpr int kWinThreads = 128;
+constexpr int kWinS = 52;  // outputs per segment (S / 4 odd)
+
+__host__ __device__ constexpr int win_words(int NW) { return kWinS + (1 << (NW - 1)); }
+
+template <int NW>
+__global__ void __launch_bounds__(kWinThreads, 3) snr_window_kernel(SnrArgs a, int use_tma, int32_t* best) {
+  constexpr int WMAX = 1 << (NW - 1);
+  constexpr int WIN = (win_words(NW) + 3) / 4 * 4;
+  extern __shared__ __align__(16) uint32_t buf[];
+  __shared__ uint32_t scratch[32];
+  __shared__ uint64_t bar;
+  __shared__ unsigned long long ps1[kWinThreads / 32][NW], ps2[kWinThreads / 32][NW];
+  __shared__ uint32_t pmx[kWinThreads / 32][NW];
+  __shared__ int gmax[NW], first[NW];
+  __shared__ int is_last;
+  const int row = blockIdx.x;
+  const int n_t = a.n_t;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t segsum = 0;
+  if (!load_prefix(a.D + (int64_t)row * n_t, n_t, buf, scratch, &bar, use_tma != 0, a.status, &segsum)) return;
+
+  const int n_seg = (n_t + 3 + kWinS - 1) / kWinS;
+  uint32_t mx[NW];
+  unsigned long long s2[NW];
+#pragma unroll
+  for (int k = 0; k < NW; k++) { mx[k] = 0u; s2[k] = 0ull; }
+  if (threadIdx.x < NW) first[threadIdx.x] = 0x7fffffff;
+  for (int seg = threadIdx.x; seg < n_seg; seg += blockDim.x) {
+    const int t0 = seg * kWinS - 3;
+    uint32_t p[WIN];
+    const uint4* src = reinterpret_cast<const uint4*>(buf + seg * kWinS);
+#pragma unroll
+    for (int j = 0; j < WIN / 4; j++) {
+      const uint4 v = src[j];
+      p[4 * j] = v.x; p[4 * j + 1] = v.y; p[4 * j + 2] = v.z; p[4 * j + 3] = v.w;
+    }
+    if (t0 >= 0 && t0 + kWinS - 1 + WMAX <= n_t) {
+#pragma unroll
+      for (int k = 0; k < NW; k++)
+#pragma unroll
+        for (int i = 0; i < kWinS; i++) {
+          const uint32_t B = p[i + (1 << k)] - p[i];
+          s2[k] += (unsigned long long)B * B;
+          mx[k] = max(mx[k], B);
+        }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NW; k++)
+#pragma unroll
+        for (int i = 0; i < kWinS; i++) {
+          const bool ok = t0 + i >= 0 && t0 + i + (1 << k) <= n_t;
+          const uint32_t B = ok ? p[i + (1 << k)] - p[i] : 0u;
+          s2[k] += (unsigned long long)B * B;
+          mx[k] = max(mx[k], B);
+        }
+    }
+  }
+  const uint32_t* P = buf + 3;  // P[k], k = 0 .. n_t
+  // this thread's share of S1 (closed form; wrap-around 64-bit terms, exact block total)
+  unsigned long long s1t[NW];
+#pragma unroll
+  for (int k = 0; k < NW; k++) s1t[k] = (unsigned long long)(1u << k) * segsum;
+  for (int j = (int)threadIdx.x + 1; j < WMAX; j += blockDim.x) {
+    const unsigned long long v = (unsigned long long)P[j] + (unsigned long long)(P[n_t] - P[n_t - j]);
+#pragma unroll
+    for (int k = 0; k < NW; k++)
+      if (j < (1 << k)) s1t[k] -= v;
+  }
+#pragma unroll
+  for (int k = 0; k < NW; k++) {
+    unsigned long long v1 = s1t[k], v2 = s2[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+      v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+    }
+    const uint32_t m = __reduce_max_sync(0xffffffffu, mx[k]);
+    if (lane == 0) { ps1[warp][k] = v1; ps2[warp][k] = v2; pmx[warp][k] = m; }
+  }
+  __syncthreads();
+  if (threadIdx.x < NW) {
+    const int k = threadIdx.x;
+    uint32_t m = pmx[0][k];
+    for (int q = 1; q < nw; q++) m = max(m, pmx[q][k]);
+    gmax[k] = (int)m;
+  }
+  __syncthreads();
+  // first position of each maximum: the warp of each thread holding it searches
+  // that thread's segments, in order, 32 outputs at a time
+#pragma unroll
+  for (int k = 0; k < NW; k++) {
+    const int w = 1 << k;
+    unsigned owners = __ballot_sync(0xffffffffu, (int)mx[k] == gmax[k]);
+    while (owners) {
+      const int o = __ffs(owners) - 1;
+      owners &= owners - 1;
+      bool found = false;
+      for (int seg = warp * 32 + o; seg < n_seg && !found; seg += blockDim.x) {
+        const int t0 = seg * kWinS - 3;
+        for (int i0 = 0; i0 < kWinS && !found; i0 += 32) {
+          const int t = t0 + i0 + lane;
+          const bool hit = i0 + lane < kWinS && t >= 0 && t + w <= n_t && (int)(P[t + w] - P[t]) == gmax[k];
+          const unsigned h = __ballot_sync(0xffffffffu, hit);
+          if (h) {
+            if (lane == 0) atomicMin(&first[k], t0 + i0 + __ffs(h) - 1);
+            found = true;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NW) {
+    const int k = threadIdx.x;
+    Moments r{ps1[0][k], ps2[0][k], 0ull, gmax[k], 0};
+    for (int q = 1; q < nw; q++) {
+      r.s1 += ps1[q][k];
+      r.s2lo += ps2[q][k];
+    }
+    const int64_t o = (int64_t)k * a.n_dms + row;
+    a.snr[o] = snr_from_moments(n_t - (1 << k) + 1, r);
+    a.peak_t[o] = first[k];
+    a.peak_val[o] = gmax[k];
+    if (best) __threadfence();
+  }
+  if (!best) return;
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(reinterpret_cast<unsigned*>(best + 3), 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (is_last) {
+    __threadfence();
+    detect_block<true>(a.snr, a.peak_t, a.peak_val, a.n_dms, NW, best);
   }
 }
 
@@ -423,9 +587,51 @@ SnrKernel snr_variant(int nwp) {
   }
 }
 
+typedef void (*WindowKernel)(SnrArgs, int, int32_t*);
+
+WindowKernel window_variant(int nw) {
+  switch (nw) {
+    case 1: return snr_window_kernel<1>;
+    case 2: return snr_window_kernel<2>;
+    case 3: return snr_window_kernel<3>;
+    case 4: return snr_window_kernel<4>;
+    case 5: return snr_window_kernel<5>;
+    case 6: return snr_window_kernel<6>;
+    default: return snr_window_kernel<7>;
+  }
+}
+
+// The register-window kernel serves sliding boxcars of widths 1, 2, ..., 2^(NW-1)
+// (NW <= 7) whose sums of squares fit 64 bits per row; it has no decimating
+// form.  Its block is min(threads, 128) threads.
+bool window_form(const SnrArgs& a, const sps_snr_config& c, int* threads) {
+  if (a.decimate || a.pow2_widths < 1 || a.pow2_widths > 7 || !tma_ok(a.D, a.n_t)) return false;
+  const long double bmax = (long double)std::max<int64_t>(1, a.max_boxcar);
+  // the block total of S2 (at most N_t squares) is kept in 64 bits
+  if ((long double)a.n_t * bmax * bmax >= 1.8e19L) return false;
+  *threads = std::min(c.threads, kWinThreads);
+  return true;
+}
+
+size_t window_smem(int n_t, int nw) {
+  const int n_seg = (n_t + 3 + kWinS - 1) / kWinS;
+  return ((size_t)n_seg * kWinS + (size_t)(win_words(nw) + 3) / 4 * 4) * sizeof(uint32_t);
+}
+
 sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st) {
   std::string why;
   if (!snr_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
+  int wthreads = 0;
+  if (window_form(a, c, &wthreads)) {
+    const size_t smem = window_smem(a.n_t, a.pow2_widths);
+    if (sps_status s = check_row_fits(a.n_t, smem - prefix_smem(a.n_t) + 4096)) return s;
+    WindowKernel fn = window_variant(a.pow2_widths);
+    SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (a.best) SPS_CUDA(cudaMemsetAsync(a.best, 0, 4 * sizeof(int32_t), st));
+    fn<<<a.n_dms, wthreads, smem, st>>>(a, 1, a.best);
+    SPS_CUDA(cudaGetLastError());
+    return SPS_OK;
+  }
   if (sps_status s = check_row_fits(a.n_t, sizeof(Moments) * (kMaxThreads / 32) * kWidthsPerPass + 512)) return s;
   // largest boxcar value: 255 * channels * widest width (< 2^31, checked by the plan);
   // a thread's 64-bit S2 partial takes `flush` squares before it must be flushed
@@ -447,6 +653,10 @@ sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st
     fn<<<a.n_dms, c.threads, smem, st>>>(a, w0, flush, tma_ok(a.D, a.n_t) ? 1 : 0, narrow);
     SPS_CUDA(cudaGetLastError());
   }
+  if (a.best) {
+    detect_kernel<<<1, 1024, 0, st>>>(a.snr, a.peak_t, a.peak_val, a.n_dms, a.n_widths, a.best);
+    SPS_CUDA(cudaGetLastError());
+  }
   return SPS_OK;
 }
 
@@ -457,13 +667,6 @@ sps_status launch_integrate(const int32_t* D, int32_t n_dms, int32_t n_t, const 
   SPS_CUDA(cudaFuncSetAttribute(integrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   integrate_kernel<<<n_dms, 256, smem, st>>>(D, n_dms, n_t, widths, n_widths, B, tma_ok(D, n_t) ? 1 : 0, decimate,
                                              status);
-  SPS_CUDA(cudaGetLastError());
-  return SPS_OK;
-}
-
-sps_status launch_detect(const double* snr, const int32_t* peak_t, const int32_t* peak_val, int32_t n_dms,
-                         int32_t n_widths, int32_t* best, cudaStream_t st) {
-  detect_kernel<<<1, 1024, 0, st>>>(snr, peak_t, peak_val, n_dms, n_widths, best);
   SPS_CUDA(cudaGetLastError());
   return SPS_OK;
 }

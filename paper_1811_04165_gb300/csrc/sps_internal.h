@@ -139,10 +139,13 @@ struct SnrArgs {
   int32_t* peak_val;
   uint32_t* status;
   int32_t decimate;        // 1: widths are downsampling factors
+  int32_t pow2_widths;     // NW when the widths are exactly 1, 2, ..., 2^(NW-1); else 0
+  int32_t* best;           // device int32[4] for the detection, or null
 };
 
 // Kernel launchers (dedisperse_u8.cu, dedisperse_presum.cu, dedisperse_step2.cu,
-// snr.cu, zap.cu).  They validate the configuration
+// snr.cu, zap.cu).  launch_snr also writes the detection when SnrArgs::best is
+// set.  They validate the configuration
 // against the kernel's compiled variants and return UNSUPPORTED otherwise.
 sps_status launch_u8_pass(const U8PassArgs& a, const sps_dedisp_config& cfg, cudaStream_t st);
 sps_status launch_step2(const Step2Args& a, const sps_dedisp_config& cfg, cudaStream_t st);
@@ -151,8 +154,6 @@ sps_status launch_integrate(const int32_t* D, int32_t n_dms, int32_t n_t, const 
                             int32_t n_widths, int32_t decimate, int32_t* B, uint32_t* status, cudaStream_t st);
 sps_status launch_expand(const uint8_t* x, int64_t pitch, int32_t in_len, int32_t channels, uint8_t* x4,
                          int64_t pitch4, cudaStream_t st);
-sps_status launch_detect(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
-                         int32_t n_dms, int32_t n_widths, int32_t* best, cudaStream_t st);
 sps_status launch_presum_series(const uint8_t* x, int64_t pitch, int32_t in_len, const PresumUnit* units,
                                 int32_t n_units, int32_t unit_channels, int32_t max_rel, const PresumSeries* series,
                                 int32_t n_series, uint16_t* q, int32_t q_pitch, cudaStream_t st);

@@ -563,3 +563,47 @@ def test_int_add_rate_is_plausible(lib):
     between 1e12 adds/s and 2.5 x the 152 SM x 128 lane x 2.07 GHz unit count."""
     r = lib.sps_measure_int_add_rate()
     assert 1e12 < r < 2.5 * 152 * 128 * 2.07e9
+
+
+@pytest.mark.parametrize("n_t", [64, 100, 1000, 4096, 12500])
+@pytest.mark.parametrize("n_w", [1, 3, 7])
+@pytest.mark.parametrize("threads", [32, 128])
+def test_snr_power_of_two_widths_edges(lib, n_t, n_w, threads):
+    """Widths 1, 2, ..., 2^(n_w - 1) take the register-window form with the
+    detection folded in: rows whose maximum sits at the first or last valid
+    sample of a width, a maximum repeated in many segments (the first must
+    win), constant and zero rows, the largest value the plan allows, and two
+    identical rows (the detection takes the smaller DM index)."""
+    torch = _torch()
+    widths = [1 << k for k in range(n_w)]
+    if widths[-1] > n_t:
+        pytest.skip("widest boxcar longer than the row")
+    rng = np.random.Generator(np.random.PCG64(n_t * 10 + n_w))
+    C = 1536
+    n_dms = 12
+    p = lib.Plan(C, 1250.0, 1550.0, 81.92e-6, n_t, synth.dm_grid(n_dms, 1.0), widths)
+    c = p.config
+    c.snr = lib.SnrConfig(threads)
+    p.config = c
+    D = rng.integers(180000, 220000, (n_dms, n_t)).astype(np.int32)
+    D[0] = 7                          # constant: S/N 0 everywhere, peak at t = 0
+    D[1] = 0
+    D[1, 0] = 255 * C                 # spike at the first sample
+    D[2] = 0
+    D[2, n_t - 1] = 255 * C           # spike at the last sample: only width 1 sees it at t = n_t - 1
+    D[3] = 0
+    D[3, ::37] = 1000                 # the same maximum in many segments
+    D[4] = 255 * C                    # the largest value everywhere
+    D[5, :] = np.arange(n_t) % 251    # a ramp
+    D[6] = D[7]                       # identical rows: a detection tie goes to the smaller index
+    D[7, n_t // 2] = 255 * C
+    D[6] = D[7]
+    out = p.alloc_outputs()
+    out["best"].fill_(-5)
+    lib.sps_snr(p, torch.from_numpy(D).cuda(), out["snr"], out["peak_t"], out["peak_val"], out["best"])
+    torch.cuda.synchronize()
+    s, pt, pv = oracle.snr(D, widths)
+    _check_snr(_to_np(out["snr"]), _to_np(out["peak_t"]), _to_np(out["peak_val"]), s, pt, pv)
+    bi, bw = oracle.detect(s)
+    assert _to_np(out["best"]).tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])]
+    assert p.status() == 0
