@@ -253,8 +253,9 @@ sps_status sps_search_host(const sps_plan* plan, const uint8_t* x_host, int64_t 
  * partners, per-kernel crossover with p_cross (uniform coin-toss or one-point,
  * undone when it breaks validity), per-kernel mutation with p_mut to a
  * different valid value, next population = fitter half of parents + fitter
- * half of offspring.  The evaluation budget counts distinct individuals;
- * repeats are served from a cache.
+ * half of offspring (an offspring left unevaluated because the budget ran
+ * out takes no place; further parents fill it).  The evaluation budget counts
+ * distinct individuals; repeats are served from a cache.
  * Resume (checkpoint of the best per generation, Sec. 4): `known_points` /
  * `known_fitness` hold n_known earlier evaluations (a tuning log); a point
  * found there takes the logged fitness instead of being measured, and
@@ -290,6 +291,13 @@ typedef struct {
                                    population; random search's last `population`
                                    distinct individuals (rows past the evaluation
                                    count set to -1); untouched by exhaustive search */
+  int32_t renew;                /* GA renewal tries (>= 0; 0 = none): an offspring that
+                                   repeats an evaluated individual or an earlier
+                                   offspring of its generation is mutated again (a
+                                   kernel, then one of its genes, drawn uniformly) up
+                                   to this many times -- Sec. 3.2 forms pairs so that
+                                   crossover yields new offspring, and a repeat is no
+                                   new offspring */
 } sps_search_desc;
 
 typedef struct {

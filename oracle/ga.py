@@ -28,8 +28,16 @@ Readings of the paper taken here (the text does not fix them):
     condition the next values in cyclic order are tried, and the old value is
     kept if none is valid;
   * replacement: parents and offspring are ranked by (fitness, index) and the
-    best ceil(N_pop/2) parents followed by the best floor(N_pop/2) offspring
-    form the next population;
+    best N_pop/2 parents followed by the best N_pop/2 offspring form the next
+    population; offspring left unevaluated because the budget ran out are not
+    ranked, and further parents take their places;
+  * renewal (Sec. 3.2 pairs individuals so that crossover yields new
+    offspring; an offspring identical to an individual already evaluated is no
+    new offspring either): after mutation, each offspring that repeats an
+    evaluated individual or an earlier offspring of the same generation is
+    mutated again -- a kernel drawn uniformly, then one of its genes, to a
+    different valid value as in mutation -- up to `renew` times; renew = 0
+    keeps every offspring as crossover and mutation left it;
   * the evaluation budget counts distinct evaluated individuals; repeats come
     from a cache; once the budget is spent further individuals score +inf;
   * pure random search draws valid individuals until the budget of distinct
@@ -139,10 +147,34 @@ def tournament_pool_size(n_pop: int, pool_fraction: float) -> int:
     return min(n_pop, max(2, int(math.floor(pool_fraction * n_pop + 0.5))))
 
 
+def _mutate_gene(space: Space, child, g, rng: SplitMix64):
+    """One gene to a different value drawn uniformly; if that breaks a boundary
+    condition the next values in cyclic order are tried, and the old value is
+    kept if none is valid."""
+    nv = space.n_values[g]
+    if nv < 2:
+        return
+    old = child[g]
+    v = rng.below(nv - 1)
+    if v >= old:
+        v += 1
+    chosen = old
+    for s in range(nv):
+        cand = (v + s) % nv
+        if cand == old:
+            continue
+        child[g] = cand
+        if space.is_valid(child):
+            chosen = cand
+            break
+    child[g] = chosen
+
+
 def genetic(space: Space, fitness, n_pop=32, p_cross=0.8, p_mut=0.1, pool_fraction=0.2,
-            crossover="uniform", max_evaluations=500, max_generations=1000, seed=1) -> Result:
+            crossover="uniform", max_evaluations=500, max_generations=1000, seed=1, renew=8) -> Result:
     """Sec. 3.2: initialise, evaluate, then select -> pair -> cross -> mutate ->
-    evaluate -> replace, until the evaluation budget or generation limit."""
+    (renew repeats) -> evaluate -> replace, until the evaluation budget or the
+    generation limit."""
     if n_pop < 2 or n_pop % 2:
         raise ValueError("N_pop must be even and >= 2")
     rng = SplitMix64(seed)
@@ -200,28 +232,22 @@ def genetic(space: Space, fitness, n_pop=32, p_cross=0.8, p_mut=0.1, pool_fracti
         for child in offspring:
             for genes in kernels:
                 if rng.unit() < p_mut:
-                    g = genes[rng.below(len(genes))]
-                    nv = space.n_values[g]
-                    if nv < 2:
-                        continue
-                    old = child[g]
-                    v = rng.below(nv - 1)
-                    if v >= old:
-                        v += 1
-                    chosen = old
-                    for s in range(nv):
-                        cand = (v + s) % nv
-                        if cand == old:
-                            continue
-                        child[g] = cand
-                        if space.is_valid(child):
-                            chosen = cand
-                            break
-                    child[g] = chosen
+                    _mutate_gene(space, child, genes[rng.below(len(genes))], rng)
+        # renewal: offspring that repeat an evaluated individual or an earlier
+        # offspring of this generation mutate again, up to `renew` times each
+        for j, child in enumerate(offspring):
+            tries = 0
+            while tries < renew and (tuple(child) in ev.cache or child in offspring[:j]):
+                genes = kernels[rng.below(len(kernels))]
+                _mutate_gene(space, child, genes[rng.below(len(genes))], rng)
+                tries += 1
         off_fit = [ev(c) for c in offspring]
-        # replacement: the fitter half of the parents and of the offspring
-        par_rank = sorted(range(n_pop), key=lambda j: (fit[j], j))[: (n_pop + 1) // 2]
-        off_rank = sorted(range(n_pop), key=lambda j: (off_fit[j], j))[: n_pop // 2]
+        # replacement: the fitter half of the parents and of the offspring; an
+        # offspring left unevaluated because the budget ran out takes no place,
+        # and the next-fittest parents fill the population instead
+        evaluated = [j for j in range(n_pop) if tuple(offspring[j]) in ev.cache]
+        off_rank = sorted(evaluated, key=lambda j: (off_fit[j], j))[: n_pop // 2]
+        par_rank = sorted(range(n_pop), key=lambda j: (fit[j], j))[: n_pop - len(off_rank)]
         population = [population[j] for j in par_rank] + [offspring[j] for j in off_rank]
         fit = [fit[j] for j in par_rank] + [off_fit[j] for j in off_rank]
         history.append((gen, ev.evaluations, ev.best))

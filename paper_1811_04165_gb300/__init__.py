@@ -639,7 +639,7 @@ class SearchDesc(ctypes.Structure):
                 ("max_generations", ctypes.c_int32), ("p_cross", ctypes.c_double), ("p_mut", ctypes.c_double),
                 ("pool_fraction", ctypes.c_double), ("max_evaluations", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("known_points", ctypes.c_void_p), ("known_fitness", ctypes.c_void_p), ("n_known", ctypes.c_int64),
-                ("final_population", ctypes.c_void_p)]
+                ("final_population", ctypes.c_void_p), ("renew", ctypes.c_int32)]
 
 
 def _with_final_population(desc, n_genes):
@@ -670,12 +670,14 @@ class SearchResult(ctypes.Structure):
 
 def search_desc(algorithm=TUNE_GA, population=32, p_cross=0.8, p_mut=0.1, pool_fraction=0.2,
                 crossover=CROSS_UNIFORM, max_evaluations=500, max_generations=1000, seed=1,
-                known=None) -> SearchDesc:
+                known=None, renew=8) -> SearchDesc:
     """Search descriptor.  `known`: earlier evaluations [(point, fitness), ...]
     (e.g. read_tuning_log) served instead of measuring them: a search re-run
-    with the same settings replays its log and continues (resume)."""
+    with the same settings replays its log and continues (resume).  `renew`:
+    GA renewal tries for offspring that repeat an evaluated individual (0: none)."""
     d = SearchDesc(int(algorithm), int(crossover), int(population), int(max_generations), float(p_cross),
                    float(p_mut), float(pool_fraction), int(max_evaluations), int(seed) & ((1 << 64) - 1))
+    d.renew = int(renew)
     if known:
         pts = np.ascontiguousarray([list(p) for p, _ in known], np.int32)
         fit = np.ascontiguousarray([float(f) for _, f in known], np.float64)

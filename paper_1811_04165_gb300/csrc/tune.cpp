@@ -22,7 +22,10 @@
 //              coin (> 0.5 swaps) for uniform crossover, or one cut in
 //              [0, n_genes_of_kernel) for one-point crossover;
 //   mutation:  per offspring and kernel, one draw against p_mut; then the gene
-//              index and a new value among the other values.
+//              index and a new value among the other values;
+//   renewal:   per offspring that repeats an evaluated individual or an
+//              earlier offspring, per try: the kernel, the gene index and a new
+//              value among the other values.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -115,10 +118,33 @@ bool random_valid(const Problem& pr, SplitMix64& rng, Point* out) {
   return false;
 }
 
+// One gene to a different value drawn uniformly; if that breaks a boundary
+// condition the next values in cyclic order are tried, and the old value is
+// kept if none is valid.
+void mutate_gene(const Problem& pr, Point& c, int32_t g, SplitMix64& rng) {
+  const int32_t nv = pr.n_values[g];
+  if (nv < 2) return;
+  const int32_t old = c[g];
+  int32_t v = rng.below(nv - 1);
+  if (v >= old) v++;
+  int32_t chosen = old;
+  for (int32_t s = 0; s < nv; s++) {
+    const int32_t cand = (v + s) % nv;
+    if (cand == old) continue;
+    c[g] = cand;
+    if (pr.valid(c)) {
+      chosen = cand;
+      break;
+    }
+  }
+  c[g] = chosen;
+}
+
 sps_status run_genetic(const Problem& pr, const sps_search_desc& d, Point* best, sps_search_result* res) {
   const int32_t n = d.population;
   if (n < 2 || n % 2) return fail(SPS_ERR_INVALID_ARG, "population must be even and >= 2");
   if (!(d.pool_fraction > 0.0)) return fail(SPS_ERR_INVALID_ARG, "pool_fraction must be > 0");
+  if (d.renew < 0) return fail(SPS_ERR_INVALID_ARG, "renew must be >= 0");
   SplitMix64 rng(d.seed);
   Evaluator ev(pr, d.max_evaluations);
   const int32_t n_pool = std::min(n, std::max<int32_t>(2, (int32_t)std::floor(d.pool_fraction * n + 0.5)));
@@ -181,36 +207,38 @@ sps_status run_genetic(const Problem& pr, const sps_search_desc& d, Point* best,
     for (Point& c : off) {
       for (const auto& genes : pr.kernels) {
         if (!(rng.unit() < d.p_mut)) continue;
-        const int32_t g = genes[rng.below((int64_t)genes.size())];
-        const int32_t nv = pr.n_values[g];
-        if (nv < 2) continue;
-        const int32_t old = c[g];
-        int32_t v = rng.below(nv - 1);
-        if (v >= old) v++;
-        int32_t chosen = old;
-        for (int32_t s = 0; s < nv; s++) {
-          const int32_t cand = (v + s) % nv;
-          if (cand == old) continue;
-          c[g] = cand;
-          if (pr.valid(c)) {
-            chosen = cand;
-            break;
-          }
-        }
-        c[g] = chosen;
+        mutate_gene(pr, c, genes[rng.below((int64_t)genes.size())], rng);
+      }
+    }
+    // renewal: an offspring that repeats an evaluated individual or an earlier
+    // offspring of this generation mutates again (a kernel, then one of its
+    // genes), up to `renew` times
+    for (int32_t j = 0; j < n; j++) {
+      Point& c = off[j];
+      for (int32_t tries = 0; tries < d.renew; tries++) {
+        bool repeat = ev.seen(c);
+        for (int32_t q = 0; q < j && !repeat; q++) repeat = off[q] == c;
+        if (!repeat) break;
+        const auto& genes = pr.kernels[rng.below((int64_t)pr.kernels.size())];
+        mutate_gene(pr, c, genes[rng.below((int64_t)genes.size())], rng);
       }
     }
     std::vector<double> off_fit(n);
     for (int32_t j = 0; j < n; j++) off_fit[j] = ev(off[j]);
-    // replacement: fitter half of parents, then fitter half of offspring
-    auto ranked = [&](const std::vector<double>& f, int32_t keep) {
-      std::vector<int32_t> r(n);
-      std::iota(r.begin(), r.end(), 0);
+    // replacement: fitter half of parents, then fitter half of offspring; an
+    // offspring left unevaluated because the budget ran out takes no place and
+    // the next-fittest parents fill the population instead
+    auto ranked = [&](const std::vector<double>& f, std::vector<int32_t> r, int32_t keep) {
       std::stable_sort(r.begin(), r.end(), [&](int32_t x, int32_t y) { return f[x] < f[y]; });
-      r.resize(keep);
+      r.resize(std::min<size_t>(r.size(), (size_t)keep));
       return r;
     };
-    const std::vector<int32_t> rp = ranked(fit, (n + 1) / 2), ro = ranked(off_fit, n / 2);
+    std::vector<int32_t> all(n), evaluated;
+    std::iota(all.begin(), all.end(), 0);
+    for (int32_t j = 0; j < n; j++)
+      if (ev.seen(off[j])) evaluated.push_back(j);
+    const std::vector<int32_t> ro = ranked(off_fit, evaluated, n / 2);
+    const std::vector<int32_t> rp = ranked(fit, all, n - (int32_t)ro.size());
     std::vector<Point> np;
     std::vector<double> nf;
     for (int32_t j : rp) { np.push_back(pop[j]); nf.push_back(fit[j]); }

@@ -591,6 +591,8 @@ def test_snr_power_of_two_widths_edges(lib, n_t, n_w, threads):
     D[1, 0] = 255 * C                 # spike at the first sample
     D[2] = 0
     D[2, n_t - 1] = 255 * C           # spike at the last sample: only width 1 sees it at t = n_t - 1
+    D[2, n_t // 3] = 3                # (and a small one: no exact S/N tie with row 1, which FP64
+                                      # rounding in the oracle's two-pass sigma could break either way)
     D[3] = 0
     D[3, ::37] = 1000                 # the same maximum in many segments
     D[4] = 255 * C                    # the largest value everywhere

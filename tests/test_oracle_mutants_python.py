@@ -39,6 +39,26 @@ def _ga_initial_population(space, fitness, **kw):
 _real_random, _real_genetic, _real_cv = ga.random_search, ga.genetic, ga.coefficients_of_variation
 
 
+def _ga_no_renewal(space, fitness, **kw):  # renewal tries ignored
+    kw["renew"] = 0
+    return _real_genetic(space, fitness, **kw)
+
+
+def _planted(fn, old, new):
+    """A copy of an oracle function with one slip planted in its source."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(fn))
+    assert src.count(old) == 1, old
+    ns = dict(vars(ga))
+    exec(compile(src.replace(old, new), f"<planted {fn.__name__}>", "exec"), ns)
+    return ns[fn.__name__]
+
+
+# renewal that checks the cache but not the generation's earlier offspring
+_ga_renewal_against_the_cache_only = _planted(ga.genetic, " or child in offspring[:j]", "")
+
+
 @pytest.mark.parametrize("name,attr,wrong,pins", [
     ("c_v with the sample sigma", "coefficients_of_variation", _cv_sample_sigma,
      ["test_coefficients_of_variation_pins"]),
@@ -48,6 +68,9 @@ _real_random, _real_genetic, _real_cv = ga.random_search, ga.genetic, ga.coeffic
      ["test_end_configurations_are_the_last_population"]),
     ("the GA's initial population as its end configurations", "genetic", _ga_initial_population,
      ["test_end_configurations_are_the_last_population"]),
+    ("a GA without renewal", "genetic", _ga_no_renewal, ["test_renewal_keeps_a_converged_population_exploring"]),
+    ("renewal that checks the cache but not the generation's other offspring", "genetic",
+     _ga_renewal_against_the_cache_only, ["test_renewal_keeps_a_converged_population_exploring"]),
 ])
 def test_a_pin_fails(monkeypatch, name, attr, wrong, pins):
     monkeypatch.setattr(ga, attr, wrong)

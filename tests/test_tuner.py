@@ -92,9 +92,34 @@ def test_ga_without_operators_keeps_the_best_individual():
     nv = [5, 5, 5]
     fit, _ = _table_fitness(nv, 5)
     r = ga.genetic(ga.Space(nv, [0, 1, 2]), fit, n_pop=8, p_cross=0.0, p_mut=0.0, pool_fraction=1.0,
-                   max_evaluations=100, max_generations=5, seed=6)
+                   max_evaluations=100, max_generations=5, seed=6, renew=0)
     assert r.evaluations == len({p for p, _ in r.trace}) <= 8
     assert r.generations == 5
+
+
+def test_renewal_keeps_a_converged_population_exploring():
+    """Renewal (Sec. 3.2: pairs are formed so that crossover yields new
+    offspring; a repeat of an evaluated individual is no new offspring): with
+    the same frozen operators as above, offspring that repeat an evaluated
+    individual mutate again, so every generation evaluates new individuals
+    until the budget is spent; each offspring is new unless its tries ran out."""
+    nv = [5, 5, 5]
+    fit, _ = _table_fitness(nv, 5)
+    r = ga.genetic(ga.Space(nv, [0, 1, 2]), fit, n_pop=8, p_cross=0.0, p_mut=0.0, pool_fraction=1.0,
+                   max_evaluations=100, max_generations=50, seed=6, renew=8)
+    assert r.evaluations == 100 and r.generations < 50
+    assert len({p for p, _ in r.trace}) == 100
+    # early generations: all N_pop offspring are new and distinct from each other
+    steps = [b - a for (_, a, _), (_, b, _) in zip(r.history[:4], r.history[1:5])]
+    assert steps == [8, 8, 8, 8]
+    # one try per offspring reaches the single-gene neighbours of the selected
+    # individuals: more than the frozen run's initial population, fewer than the budget
+    r1 = ga.genetic(ga.Space(nv, [0, 1, 2]), fit, n_pop=8, p_cross=0.0, p_mut=0.0, pool_fraction=1.0,
+                    max_evaluations=60, max_generations=100, seed=6, renew=1)
+    assert 8 < r1.evaluations <= 60
+    # the fittest individual survives renewal: elitist replacement never loses it
+    best = min(fit(p) for p, _ in r.trace)
+    assert r.best_fitness == best
 
 
 @pytest.mark.parametrize("seed", [2, 3])
@@ -112,7 +137,7 @@ def test_end_configurations_are_the_last_population(seed):
     assert all(mask[p] and p in evaluated for p in r.final_population)
     assert r.best_point in r.final_population
     frozen = ga.genetic(ga.Space(nv, ko), fit, n_pop=6, p_cross=0.0, p_mut=0.0, pool_fraction=1.0,
-                        max_evaluations=100, max_generations=3, seed=seed)
+                        max_evaluations=100, max_generations=3, seed=seed, renew=0)
     first = min(frozen.trace[:6], key=lambda e: e[1])[0]
     assert frozen.final_population == [first] * 6
     rs = ga.random_search(ga.Space(nv, ko, valid), fit, max_evaluations=25, seed=seed, n_pop=10)
@@ -154,21 +179,22 @@ CASES = list(itertools.product(
     ["uniform", "one-point"],     # crossover
     [(0.8, 0.1), (1.0, 1.0), (0.3, 0.5)],  # (p_cross, p_mut)
     [False, True],                # validity constraints
+    [0, 2, 8],                    # renewal tries
 ))
 
 
-@pytest.mark.parametrize("seed,crossover,rates,constrained", CASES)
-def test_library_ga_matches_oracle_draw_for_draw(lib, seed, crossover, rates, constrained):
+@pytest.mark.parametrize("seed,crossover,rates,constrained,renew", CASES)
+def test_library_ga_matches_oracle_draw_for_draw(lib, seed, crossover, rates, constrained, renew):
     nv = [4, 3, 5, 2, 6, 3, 4]
     kernels = [0, 0, 0, 1, 1, 2, 2]
     fit, _ = _table_fitness(nv, seed, ties=(seed == 2))
     valid = _validity(nv, seed)[0] if constrained else None
     kw = dict(n_pop=12, p_cross=rates[0], p_mut=rates[1], pool_fraction=0.2, max_evaluations=120,
-              max_generations=60, seed=seed)
+              max_generations=60, seed=seed, renew=renew)
     want = ga.genetic(ga.Space(nv, kernels, valid), fit, crossover=crossover, **kw)
     desc = lib.search_desc(algorithm=lib.TUNE_GA, population=12, p_cross=rates[0], p_mut=rates[1],
                            pool_fraction=0.2, crossover=lib.CROSS_UNIFORM if crossover == "uniform" else
-                           lib.CROSS_ONE_POINT, max_evaluations=120, max_generations=60, seed=seed)
+                           lib.CROSS_ONE_POINT, max_evaluations=120, max_generations=60, seed=seed, renew=renew)
     best, res, trace = lib.sps_optimize(nv, kernels, fit, valid, desc)
     assert trace == [(tuple(p), f) for p, f in want.trace]
     assert best == want.best_point and res.best_fitness == want.best_fitness
@@ -309,7 +335,7 @@ def test_ga_converges_more_than_random_search_in_cv(lib):
         for seed in range(10):
             _, res, _ = lib.sps_optimize(nv, ko, lambda p: t[tuple(p)], None,
                                          lib.search_desc(algorithm=alg, population=20, max_evaluations=150,
-                                                         seed=seed))
+                                                         seed=seed, renew=0))
             runs.append(ga.coefficients_of_variation(res.final_population, values))
         cv[name] = np.mean([[c for c in r if c is not None] for r in runs], axis=0)
     assert np.all(cv["ga"] < cv["random"])
