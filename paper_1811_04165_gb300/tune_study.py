@@ -52,10 +52,10 @@ def _input(plan, wl):
     return torch.from_numpy(x).cuda()
 
 
-def _runs(nv, ko, table, algorithm, seeds, budget, **kw):
+def _runs(nv, ko, table, algorithm, seeds, budget, valid=None, **kw):
     best = []
     for s in seeds:
-        _, res, _ = sps_optimize(nv, ko, table.__getitem__, None,
+        _, res, _ = sps_optimize(nv, ko, table.__getitem__, valid,
                                  search_desc(algorithm=algorithm, max_evaluations=budget, seed=s, **kw))
         best.append(res.best_fitness)
     return best
@@ -193,6 +193,57 @@ def study_beam(evals, reps, seed):
             "ga_ms": t_best, "speedup": t_default / t_best}
 
 
+def study_beam_table(seeds, budget_frac, reps, table_out=None):
+    """The bench's workload (the Apertif beam, brute force) over its reduced
+    joint space: every valid point timed live (exhaustive search), then GA and
+    random search on that table at `budget_frac` of its valid points over
+    `seeds`, and the library's default configuration placed in the table."""
+    import torch
+    wl = synth.apertif_beam()
+    plan = Plan.from_workload(wl)
+    x = _input(plan, wl)
+    default = plan.config
+    nv, ko, values = sps_tune_space(plan, SPACE_REDUCED)
+    t0 = time.perf_counter()
+    _, res, trace = sps_tune(plan, x, which=SPACE_REDUCED, desc=search_desc(algorithm=TUNE_EXHAUSTIVE), reps=reps)
+    torch.cuda.synchronize()
+    t_exh = time.perf_counter() - t0
+    plan.config = default
+    table = {tuple(int(v) for v in pt): float(f) for pt, f in trace}
+    finite = {pt: f for pt, f in table.items() if np.isfinite(f)}
+    opt_pt = min(finite, key=finite.get)
+    opt = finite[opt_pt]
+    # the default configuration's point in the space (None if it lies outside)
+    default_pt = None
+    for pt in finite:
+        if sps_tune_config(plan, SPACE_REDUCED, pt).as_dict() == default.as_dict():
+            default_pt = pt
+            break
+    budget = max(1, int(budget_frac * len(finite)))
+    seeds = list(seeds)
+    # the searches see the plan's boundary conditions: the points the exhaustive search visited
+    valid = table.__contains__
+    ga = _runs(nv, ko, table, TUNE_GA, seeds, budget, valid)
+    rnd = _runs(nv, ko, table, TUNE_RANDOM, seeds, budget, valid)
+    ga0 = _runs(nv, ko, table, TUNE_GA, seeds, budget, valid, renew=0)
+    out = {"workload": wl.name, "space": "reduced brute force", "genes": [list(map(int, v)) for v in values],
+           "points": int(np.prod(nv)), "valid": len(finite), "exhaustive_s": t_exh, "reps": reps,
+           "optimum_ms": opt, "optimum_config": sps_tune_config(plan, SPACE_REDUCED, opt_pt).as_dict(),
+           "median_ms": statistics.median(finite.values()), "worst_ms": max(finite.values()), "budget": budget,
+           "default_ms": finite.get(default_pt) if default_pt is not None else None,
+           "default_ratio": finite[default_pt] / opt if default_pt is not None else None,
+           "ga": _summary(ga, opt), "random": _summary(rnd, opt), "ga_without_renewal": _summary(ga0, opt)}
+    if table_out:
+        with open(table_out, "w") as f:
+            json.dump({"how": "python -m paper_1811_04165_gb300.tune_study --beam-table (sps_tune, exhaustive "
+                              f"search of the reduced space, reps={reps}, median of three trials per point)",
+                       "gpu": torch.cuda.get_device_name(), "workload": wl.name, "n_values": [int(v) for v in nv],
+                       "kernel_of": [int(k) for k in ko], "values": out["genes"],
+                       "default_point": list(default_pt) if default_pt is not None else None,
+                       "points": [[list(pt), (f if np.isfinite(f) else None)] for pt, f in table.items()]}, f)
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--seeds", type=int, default=50)
@@ -200,7 +251,17 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--beam-evals", type=int, default=200, help="0 skips the live run on the beam")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--beam-table", default=None, metavar="FILE",
+                    help="only the beam's reduced-space study; writes its fitness table to FILE")
     a = ap.parse_args(argv)
+    if a.beam_table:
+        res = {"apertif_beam_table": study_beam_table(range(a.seeds), 0.1, a.reps, a.beam_table)}
+        text = json.dumps(res, indent=1, default=lambda v: v.item() if hasattr(v, "item") else str(v))
+        if a.out:
+            with open(a.out, "w") as f:
+                f.write(text + "\n")
+        print(text)
+        return 0
     res = {"tiny_subband": study_table(range(a.seeds), a.budget, a.reps)}
     if a.beam_evals:
         res["apertif_beam"] = study_beam(a.beam_evals, a.reps, seed=1)
