@@ -111,7 +111,11 @@ typedef struct {
 
 /* Launch parameters of the fused boxcar + S/N kernel. */
 typedef struct {
-  int32_t threads;            /* threads per block (one block per DM row)           */
+  int32_t threads;            /* threads per block (one block per DM row); the
+                                 register-window form used for widths 1, 2, 4, ...
+                                 runs min(threads, 128)                            */
+  int32_t samples;            /* register-window form: outputs per thread segment,
+                                 0 (default, 28) or one of 20, 28, 36, 44, 52      */
 } sps_snr_config;
 
 typedef struct {
@@ -345,17 +349,22 @@ sps_status sps_tune(sps_plan* plan, int32_t which, const sps_search_desc* desc, 
 
 /* Batched beams.  A fixed set of beams (one plan each, in any mix of shapes
  * and configurations) searched by ONE launch: sps_batch_create captures every
- * beam's sps_search into a CUDA graph whose beams run on `branches`
- * concurrent branches (beams spread over the branches by work, largest
- * first); sps_batch_launch replays the graph on a stream.  The ALERT setting
+ * beam's search into a CUDA graph whose beams run on `branches` concurrent
+ * branches (beams spread over the branches by work, largest first);
+ * sps_batch_launch replays the graph on a stream.  Beams on the pre-summed
+ * brute-force kernel share their pass: the graph runs their pre-passes, then
+ * one pass launch per kernel configuration over a device work list of (beam,
+ * DM tile, time tile) descriptors of all those beams, then their S/N kernels;
+ * other beams run their whole search on a branch.  Results are those of each
+ * beam's own sps_search.  The ALERT setting
  * searches hundreds of beams at once (Sec. 1: beams spread over a GPU
  * cluster); the paper has no batched entry point, this is a library one.
  * buffers[b]: the device buffers of beam b as for sps_search (x with its
  * pitch, D, snr, peak_t, peak_val; best may be NULL); they stay owned by the
  * caller and must outlive the batch.  workspace: device, >=
  * sps_batch_workspace_bytes for the same plans and branch count, 256-byte
- * aligned; each branch uses its own region, so beams on different branches run
- * concurrently.  The graph holds the plans' current configurations:
+ * aligned; each branch uses its own region, and each beam of a shared pass
+ * its own, so beams run concurrently.  The graph holds the plans' current configurations:
  * sps_batch_launch returns INVALID_ARG, launching nothing, once a plan has been
  * reconfigured since the capture; plans must outlive the batch.  Launches of
  * one batch on different streams must not overlap (they share the workspace). */
@@ -374,6 +383,8 @@ sps_status sps_batch_workspace_bytes(const sps_plan* const* plans, int32_t n_bea
 sps_status sps_batch_create(const sps_plan* const* plans, const sps_beam_buffers* buffers, int32_t n_beams,
                             int32_t branches, void* workspace, size_t workspace_bytes, sps_batch** out);
 sps_status sps_batch_launch(sps_batch* batch, void* stream);
+/* How many shared-pass launches (one per kernel configuration) the graph holds. */
+sps_status sps_batch_list_launches(const sps_batch* batch, int32_t* n);
 sps_status sps_batch_destroy(sps_batch* batch);
 
 /* ------------------------------------------------------- real-time serving */

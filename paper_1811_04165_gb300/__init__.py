@@ -43,10 +43,10 @@ class DedispConfig(ctypes.Structure):
 
 
 class SnrConfig(ctypes.Structure):
-    _fields_ = [("threads", ctypes.c_int32)]
+    _fields_ = [("threads", ctypes.c_int32), ("samples", ctypes.c_int32)]
 
     def as_tuple(self):
-        return (self.threads,)
+        return (self.threads, self.samples)
 
 
 class KernelConfig(ctypes.Structure):
@@ -458,6 +458,14 @@ class Batch:
 
     def launch(self, stream=None):
         check(_L.sps_batch_launch(self.handle, _stream(stream)), "sps_batch_launch")
+
+    @property
+    def list_launches(self) -> int:
+        """Shared-pass launches in the graph (one per kernel configuration of
+        the beams on the pre-summed brute-force kernel)."""
+        n = ctypes.c_int32()
+        check(_L.sps_batch_list_launches(self.handle, ctypes.byref(n)), "sps_batch_list_launches")
+        return n.value
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -39,6 +39,7 @@ SIGNATURES = {
     "sps_batch_create": (_I32, [_P, _P, _I32, _I32, _P, _SZ, _P]),
     "sps_batch_launch": (_I32, [_P, _P]),
     "sps_batch_destroy": (_I32, [_P]),
+    "sps_batch_list_launches": (_I32, [_P, _P]),
     "sps_server_create": (_I32, [_P, _P]),
     "sps_server_add_beam": (_I32, [_P, _P, _P]),
     "sps_server_submit": (_I32, [_P, _I32, _P, _I64, _P, _P, ctypes.c_uint64]),

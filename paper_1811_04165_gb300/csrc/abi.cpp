@@ -99,35 +99,48 @@ U8PassArgs u8_args(const sps_plan* p, const uint8_t* x, int64_t pitch, const uin
   return a;
 }
 
+// The pre-summed series of one uint8 pass (the pre-pass), and the arguments of
+// the pass that reads them.
+sps_status presum_prepass(const sps_plan* p, const sps_dedisp_config& cfg, const uint8_t* x, int64_t pitch,
+                          uint8_t* ws, int32_t rows, int32_t per, int32_t n_out, int64_t out_pitch, int32_t dmax,
+                          void* out, int32_t out_u16, cudaStream_t st, PresumPassArgs* args) {
+  uint16_t* q = reinterpret_cast<uint16_t*>(ws);
+  const int32_t K = 1 << cfg.presum;
+  sps_status s = launch_presum_series(x, pitch, (int32_t)p->n_in, p->d_presum_units, p->n_presum_units, K,
+                                      p->presum_max_rel, p->d_presum_series, p->n_presum_series, q, p->q_pitch, st);
+  if (s) return s;
+  PresumPassArgs& a = *args;
+  a = PresumPassArgs{};
+  a.q = q;
+  a.q_pitch = p->q_pitch;
+  a.copies = p->d_presum_copies;
+  a.copies_max = p->presum_copies_max;
+  a.data_bytes = p->presum_data_bytes;
+  a.offs = p->d_presum_offs;
+  a.di_pad = presum_di_pad(cfg);
+  a.n_dm = rows;
+  a.n_groups = p->channels / per;
+  a.group_units = (per + K - 1) / K;
+  a.fold_units = 65535 / (255 * K);
+  a.max_start = (int32_t)(p->n_in - p->n_t);
+  a.n_out = n_out;
+  a.out_pitch = out_pitch;
+  a.dmax_tile = dmax;
+  a.out = out;
+  a.out_u16 = out_u16;
+  a.status = p->d_status;
+  a.window_bytes = presum_window_bytes(cfg, dmax);
+  return SPS_OK;
+}
+
 // One uint8 pass (brute force or step one) with the configured kernel.
 sps_status run_u8_pass(const sps_plan* p, const sps_dedisp_config& cfg, const uint8_t* x, int64_t pitch,
                        uint8_t* ws, int32_t rows, int32_t per, int32_t n_out, int64_t out_pitch, int32_t dmax,
                        void* out, int32_t out_u16, cudaStream_t st) {
   if (cfg.presum) {
-    uint16_t* q = reinterpret_cast<uint16_t*>(ws);
-    const int32_t K = 1 << cfg.presum;
-    sps_status s = launch_presum_series(x, pitch, (int32_t)p->n_in, p->d_presum_units, p->n_presum_units, K,
-                                        p->presum_max_rel, p->d_presum_series, p->n_presum_series, q, p->q_pitch, st);
-    if (s) return s;
     PresumPassArgs a{};
-    a.q = q;
-    a.q_pitch = p->q_pitch;
-    a.copies = p->d_presum_copies;
-    a.copies_max = p->presum_copies_max;
-    a.data_bytes = p->presum_data_bytes;
-    a.offs = p->d_presum_offs;
-    a.di_pad = presum_di_pad(cfg);
-    a.n_dm = rows;
-    a.n_groups = p->channels / per;
-    a.group_units = (per + K - 1) / K;
-    a.fold_units = 65535 / (255 * K);
-    a.max_start = (int32_t)(p->n_in - p->n_t);
-    a.n_out = n_out;
-    a.out_pitch = out_pitch;
-    a.dmax_tile = dmax;
-    a.out = out;
-    a.out_u16 = out_u16;
-    a.status = p->d_status;
+    sps_status s = presum_prepass(p, cfg, x, pitch, ws, rows, per, n_out, out_pitch, dmax, out, out_u16, st, &a);
+    if (s) return s;
     return launch_presum_pass(a, cfg, st);
   }
   sps_status s = launch_expand(x, pitch, (int32_t)p->n_in, p->channels, ws, p->pitch4, st);
@@ -227,6 +240,26 @@ sps_status run_search(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_
 sps_status dedisperse_into(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
                            size_t ws_bytes, cudaStream_t st) {
   return run_dedisperse(p, x, pitch, D, ws, ws_bytes, st);
+}
+
+bool batched_pass_form(const sps_plan* p) { return p->mode == SPS_MODE_BRUTE && p->cfg.brute.presum > 0; }
+
+sps_status brute_prepass(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
+                         size_t ws_bytes, cudaStream_t st, PresumPassArgs* args) {
+  if (!batched_pass_form(p)) return fail(SPS_ERR_INVALID_ARG, "not a pre-summed brute-force plan");
+  sps_status s = check_x(p, x, pitch);
+  if (s) return s;
+  if (!D || !aligned16(D)) return fail(SPS_ERR_INVALID_ARG, "D must be non-null and 16-byte aligned");
+  if ((s = check_workspace(p, ws, ws_bytes))) return s;
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  if ((s = prepare_input(p, &x, &pitch, &w, st))) return s;
+  return presum_prepass(p, p->cfg.brute, x, pitch, w, (int32_t)p->dms.size(), p->channels, p->n_t, p->n_t,
+                        p->dmax_brute, D, 0, st, args);
+}
+
+sps_status snr_into(const sps_plan* p, const int32_t* D, double* snr, int32_t* peak_t, int32_t* peak_val,
+                    int32_t* best, cudaStream_t st) {
+  return run_snr(p, D, snr, peak_t, peak_val, best, st);
 }
 
 }  // namespace sps

@@ -66,9 +66,10 @@ __device__ __forceinline__ void load_offs(const uint16_t* p, uint32_t (&o)[ND]) 
   }
 }
 
+// One block's tile: DM tile `tile`, time tile `ty`, group `g` of the pass `a`.
 template <int ND, int NW>
-__global__ void __launch_bounds__(kMaxThreads, 1)
-presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb) {
+__device__ __forceinline__ void presum_pass_block(const PresumPassArgs& a, int tile, int ty, int g, int wd,
+                                                  int cp_max, int wb) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int wt = (int)(blockDim.x >> 5) / wd;
   const int Tt = wt * 64 * NW;
@@ -83,10 +84,8 @@ presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = (int)(blockDim.x >> 5);
   const int dm_sub = warp % wd, t_sub = warp / wd;
-  const int tile = blockIdx.x;
   const int i0 = tile * Di;
-  const int t0 = blockIdx.y * Tt;
-  const int g = blockIdx.z;
+  const int t0 = ty * Tt;
   const int P = a.group_units;
   const int n_chunks = (P + cp_max - 1) / cp_max;
   const uint32_t toff = (uint32_t)(t_sub * 128 * NW + lane * 4);  // bytes
@@ -288,6 +287,24 @@ presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb) {
       }
     }
   }
+}
+
+template <int ND, int NW>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+presum_pass_kernel(PresumPassArgs a, int wd, int cp_max, int wb) {
+  presum_pass_block<ND, NW>(a, blockIdx.x, blockIdx.y, blockIdx.z, wd, cp_max, wb);
+}
+
+// Batched form: one launch over a work list of tiles from several passes of
+// the same configuration (several beams).  work[b] = {pass, DM tile, time
+// tile, group}; each pass's arguments (and its window bytes) live in `passes`.
+template <int ND, int NW>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+presum_pass_list_kernel(const PresumPassArgs* __restrict__ passes, const int4* __restrict__ work, int wd,
+                        int cp_max) {
+  const int4 w = work[blockIdx.x];
+  const PresumPassArgs& a = passes[w.x];
+  presum_pass_block<ND, NW>(a, w.y, w.z, w.w, wd, cp_max, a.window_bytes);
 }
 
 // Adds bytes o + j .. o + j + 15 of W (24 bytes, o in 0 .. 7), for j = 0 and
@@ -497,22 +514,32 @@ __global__ void __launch_bounds__(256) presum_series_direct_kernel(const uint8_t
 }
 
 typedef void (*PresumKernel)(PresumPassArgs, int, int, int);
+typedef void (*PresumListKernel)(const PresumPassArgs*, const int4*, int, int);
 
 template <int ND, int NW>
 constexpr PresumKernel k() { return presum_pass_kernel<ND, NW>; }
+template <int ND, int NW>
+constexpr PresumListKernel kl() { return presum_pass_list_kernel<ND, NW>; }
 
-struct Variant { int nd, nw; PresumKernel fn; };
+struct Variant { int nd, nw; PresumKernel fn; PresumListKernel list; };
+#define SPS_PRESUM_VARIANT(ND, NW) {ND, NW, k<ND, NW>(), kl<ND, NW>()}
 const Variant kVariants[] = {
-    {1, 2, k<1, 2>()}, {1, 4, k<1, 4>()}, {1, 8, k<1, 8>()}, {1, 16, k<1, 16>()},
-    {2, 2, k<2, 2>()}, {2, 4, k<2, 4>()}, {2, 8, k<2, 8>()}, {2, 16, k<2, 16>()},
-    {4, 2, k<4, 2>()}, {4, 4, k<4, 4>()}, {4, 8, k<4, 8>()},
-    {8, 2, k<8, 2>()}, {8, 4, k<8, 4>()},
+    SPS_PRESUM_VARIANT(1, 2), SPS_PRESUM_VARIANT(1, 4), SPS_PRESUM_VARIANT(1, 8), SPS_PRESUM_VARIANT(1, 16),
+    SPS_PRESUM_VARIANT(2, 2), SPS_PRESUM_VARIANT(2, 4), SPS_PRESUM_VARIANT(2, 8), SPS_PRESUM_VARIANT(2, 16),
+    SPS_PRESUM_VARIANT(4, 2), SPS_PRESUM_VARIANT(4, 4), SPS_PRESUM_VARIANT(4, 8),
+    SPS_PRESUM_VARIANT(8, 2), SPS_PRESUM_VARIANT(8, 4),
 };
+#undef SPS_PRESUM_VARIANT
+
+const Variant* find_variant(int nd, int nw) {
+  for (const Variant& v : kVariants)
+    if (v.nd == nd && v.nw == nw) return &v;
+  return nullptr;
+}
 
 PresumKernel find(int nd, int nw) {
-  for (const Variant& v : kVariants)
-    if (v.nd == nd && v.nw == nw) return v.fn;
-  return nullptr;
+  const Variant* v = find_variant(nd, nw);
+  return v ? v->fn : nullptr;
 }
 
 }  // namespace
@@ -586,6 +613,35 @@ sps_status launch_presum_pass(const PresumPassArgs& a, const sps_dedisp_config& 
   SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   fn<<<grid, 32 * c.warps_dm * c.warps_time, smem, st>>>(a, c.warps_dm, presum_chunk(c),
                                                         presum_window_bytes(c, a.dmax_tile));
+  SPS_CUDA(cudaGetLastError());
+  return SPS_OK;
+}
+
+int64_t presum_pass_blocks(const PresumPassArgs& a, const sps_dedisp_config& c) {
+  const int Di = c.warps_dm * c.dms_per_thread;
+  const int Tt = c.warps_time * 32 * c.samples_per_thread;
+  return (int64_t)((a.n_dm + Di - 1) / Di) * ((a.n_out + Tt - 1) / Tt) * a.n_groups;
+}
+
+void presum_pass_work(const PresumPassArgs& a, const sps_dedisp_config& c, int32_t pass, std::vector<int4>* work) {
+  const int Di = c.warps_dm * c.dms_per_thread;
+  const int Tt = c.warps_time * 32 * c.samples_per_thread;
+  const int tiles = (a.n_dm + Di - 1) / Di, ty = (a.n_out + Tt - 1) / Tt;
+  for (int g = 0; g < a.n_groups; g++)
+    for (int y = 0; y < ty; y++)
+      for (int t = 0; t < tiles; t++) work->push_back(make_int4(pass, t, y, g));
+}
+
+sps_status launch_presum_pass_list(const PresumPassArgs* d_passes, const int4* d_work, int64_t n_work,
+                                   const sps_dedisp_config& c, int32_t max_data_bytes, cudaStream_t st) {
+  std::string why;
+  if (!presum_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
+  if (n_work < 1 || n_work > 0x7fffffff) return fail(SPS_ERR_UNSUPPORTED, "work list size out of range");
+  const Variant* v = find_variant(c.dms_per_thread, c.samples_per_thread / 2);
+  const size_t smem = presum_smem_bytes(c, max_data_bytes);
+  SPS_CUDA(cudaFuncSetAttribute(v->list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  v->list<<<(unsigned)n_work, 32 * c.warps_dm * c.warps_time, smem, st>>>(d_passes, d_work, c.warps_dm,
+                                                                         presum_chunk(c));
   SPS_CUDA(cudaGetLastError());
   return SPS_OK;
 }

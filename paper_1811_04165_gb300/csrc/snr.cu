@@ -397,30 +397,83 @@ detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
 // Register-window form for width sets {1, 2, 4, ..., 2^(NW-1)} (the
 // smoothing widths of the search; AMBER's are powers of two as well).
 //
-// The row is staged and scanned into prefix sums as above (P[k] at buf[3 + k]).
-// Then each thread takes segments of S consecutive outputs t = t0 .. t0 + S - 1
-// (t0 = seg * S - 3, so the window's first word is 16-byte aligned) and loads
-// the window P[t0 .. t0 + S + 2^(NW-1)) into registers with 16-byte shared
-// loads (S / 4 odd: conflict-free).  With the widths known at compile time,
-// every boxcar is one register subtraction B = P[t + w] - P[t], and each
-// (sample, width) costs a subtract and a maximum on the integer ALU and one
-// 32 x 32 -> 64-bit multiply-add on the FMA pipe -- no shared-memory access.
-// Outputs outside [0, N_t - w] contribute B = 0 (neither the sum of squares
-// nor the maximum changes).  S1 comes in closed form as in snr_kernel.
+// The row is staged and scanned into prefix sums as above (P[k] at buf[3 + k]),
+// here with 16-byte shared accesses.  Then each thread takes segments of S
+// consecutive outputs t = t0 .. t0 + S - 1 (t0 = seg * S - 3, so the window's
+// first word is 16-byte aligned) and loads the window P[t0 .. t0 + S +
+// 2^(NW-1)) into registers with 16-byte shared loads (S / 4 odd:
+// conflict-free).  With the widths known at compile time, every boxcar is one
+// register subtraction B = P[t + w] - P[t], and each (sample, width) costs a
+// subtract and a maximum on the integer ALU and one 32 x 32 -> 64-bit
+// multiply-add on the FMA pipe -- no shared-memory access.  The first and last
+// segments, where some outputs fall outside [0, N_t - w], take a compact loop
+// over P in shared memory instead (the unrolled body stays small enough for
+// the instruction cache).  S1 comes in closed form as in snr_kernel.
 //
 // Detection is folded in: `best` (int32[4]) is zeroed before the launch; each
 // block, once its outputs are written, counts itself in best[3]; the block
 // that counts last reads the whole table (through L2) and writes the
 // detection over the counter.
 constexpr int kWinThreads = 128;
-constexpr int kWinS = 52;  // outputs per segment (S / 4 odd)
+// Segment lengths with a compiled register-window kernel (a multiple of 4 with S / 4 odd).
+constexpr int kWinSegments[] = {20, 28, 36, 44, 52};
+constexpr int kWinDefaultS = 28;
 
-__host__ __device__ constexpr int win_words(int NW) { return kWinS + (1 << (NW - 1)); }
+__host__ __device__ constexpr int win_words(int NW, int S) { return (S + (1 << (NW - 1)) + 3) / 4 * 4; }
 
-template <int NW>
-__global__ void __launch_bounds__(kWinThreads, 3) snr_window_kernel(SnrArgs a, int use_tma, int32_t* best) {
+// Row i into buf[4 .. 4 + n_t), scanned in place into P[k] = buf[3 + k]
+// (k = 0 .. n_t); *seg = the sum of the samples this thread scanned.  Each
+// thread scans a run of `per` samples (a multiple of 4 with per / 4 odd, so the
+// 16-byte accesses of a warp are conflict-free).
+__device__ bool load_prefix_v4(const int32_t* row, int n_t, uint32_t* buf, uint32_t* scratch, uint64_t* bar,
+                               uint32_t* status, uint32_t* seg) {
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(bar, (uint32_t)n_t * 4u);
+    bulk_g2s(buf + 4, row, (uint32_t)n_t * 4u, bar);
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(bar, 0, status);
+  if (__syncthreads_or(ok ? 0 : 1)) {
+    if (threadIdx.x == 0) mbar_wait(bar, 0, status);
+    return false;
+  }
+  if (threadIdx.x == 0) buf[3] = 0u;
+  int per = ((n_t + blockDim.x - 1) / blockDim.x + 3) / 4 * 4;
+  if ((per / 4) % 2 == 0) per += 4;
+  const int b = min(n_t, (int)threadIdx.x * per), e = min(n_t, b + per);
+  const int ev = b + (e - b) / 4 * 4;  // vector part [b, ev)
+  uint32_t s = 0;
+  for (int t = b; t < ev; t += 4) {
+    const uint4 v = *reinterpret_cast<const uint4*>(buf + 4 + t);
+    s += v.x + v.y + v.z + v.w;
+  }
+  for (int t = ev; t < e; t++) s += buf[4 + t];
+  *seg = s;
+  uint32_t run = block_exclusive_scan(s, scratch);
+  for (int t = b; t < ev; t += 4) {
+    uint4 v = *reinterpret_cast<const uint4*>(buf + 4 + t);
+    v.x += run;
+    v.y += v.x;
+    v.z += v.y;
+    v.w += v.z;
+    run = v.w;
+    *reinterpret_cast<uint4*>(buf + 4 + t) = v;
+  }
+  for (int t = ev; t < e; t++) {
+    run += buf[4 + t];
+    buf[4 + t] = run;
+  }
+  __syncthreads();
+  return true;
+}
+
+template <int NW, int S>
+__global__ void __launch_bounds__(kWinThreads, S <= 28 ? 4 : 3) snr_window_kernel(SnrArgs a, int32_t* best) {
+  static_assert(S % 4 == 0 && (S / 4) % 2 == 1, "segment length: a multiple of 4 with S / 4 odd");
   constexpr int WMAX = 1 << (NW - 1);
-  constexpr int WIN = (win_words(NW) + 3) / 4 * 4;
+  constexpr int WIN = win_words(NW, S);
   extern __shared__ __align__(16) uint32_t buf[];
   __shared__ uint32_t scratch[32];
   __shared__ uint64_t bar;
@@ -432,45 +485,46 @@ __global__ void __launch_bounds__(kWinThreads, 3) snr_window_kernel(SnrArgs a, i
   const int n_t = a.n_t;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t segsum = 0;
-  if (!load_prefix(a.D + (int64_t)row * n_t, n_t, buf, scratch, &bar, use_tma != 0, a.status, &segsum)) return;
+  if (!load_prefix_v4(a.D + (int64_t)row * n_t, n_t, buf, scratch, &bar, a.status, &segsum)) return;
+  const uint32_t* P = buf + 3;  // P[k], k = 0 .. n_t
 
-  const int n_seg = (n_t + 3 + kWinS - 1) / kWinS;
+  const int n_seg = (n_t + 3 + S - 1) / S;
   uint32_t mx[NW];
   unsigned long long s2[NW];
 #pragma unroll
   for (int k = 0; k < NW; k++) { mx[k] = 0u; s2[k] = 0ull; }
   if (threadIdx.x < NW) first[threadIdx.x] = 0x7fffffff;
   for (int seg = threadIdx.x; seg < n_seg; seg += blockDim.x) {
-    const int t0 = seg * kWinS - 3;
-    uint32_t p[WIN];
-    const uint4* src = reinterpret_cast<const uint4*>(buf + seg * kWinS);
+    const int t0 = seg * S - 3;
+    if (t0 >= 0 && t0 + S - 1 + WMAX <= n_t) {
+      uint32_t p[WIN];
+      const uint4* src = reinterpret_cast<const uint4*>(buf + seg * S);
 #pragma unroll
-    for (int j = 0; j < WIN / 4; j++) {
-      const uint4 v = src[j];
-      p[4 * j] = v.x; p[4 * j + 1] = v.y; p[4 * j + 2] = v.z; p[4 * j + 3] = v.w;
-    }
-    if (t0 >= 0 && t0 + kWinS - 1 + WMAX <= n_t) {
+      for (int j = 0; j < WIN / 4; j++) {
+        const uint4 v = src[j];
+        p[4 * j] = v.x; p[4 * j + 1] = v.y; p[4 * j + 2] = v.z; p[4 * j + 3] = v.w;
+      }
 #pragma unroll
       for (int k = 0; k < NW; k++)
 #pragma unroll
-        for (int i = 0; i < kWinS; i++) {
+        for (int i = 0; i < S; i++) {
           const uint32_t B = p[i + (1 << k)] - p[i];
           s2[k] += (unsigned long long)B * B;
           mx[k] = max(mx[k], B);
         }
     } else {
 #pragma unroll
-      for (int k = 0; k < NW; k++)
-#pragma unroll
-        for (int i = 0; i < kWinS; i++) {
-          const bool ok = t0 + i >= 0 && t0 + i + (1 << k) <= n_t;
-          const uint32_t B = ok ? p[i + (1 << k)] - p[i] : 0u;
+      for (int k = 0; k < NW; k++) {
+        const int lo = max(t0, 0), hi = min(t0 + S, n_t - (1 << k) + 1);
+#pragma unroll 1
+        for (int t = lo; t < hi; t++) {
+          const uint32_t B = P[t + (1 << k)] - P[t];
           s2[k] += (unsigned long long)B * B;
           mx[k] = max(mx[k], B);
         }
+      }
     }
   }
-  const uint32_t* P = buf + 3;  // P[k], k = 0 .. n_t
   // this thread's share of S1 (closed form; wrap-around 64-bit terms, exact block total)
   unsigned long long s1t[NW];
 #pragma unroll
@@ -511,10 +565,10 @@ __global__ void __launch_bounds__(kWinThreads, 3) snr_window_kernel(SnrArgs a, i
       owners &= owners - 1;
       bool found = false;
       for (int seg = warp * 32 + o; seg < n_seg && !found; seg += blockDim.x) {
-        const int t0 = seg * kWinS - 3;
-        for (int i0 = 0; i0 < kWinS && !found; i0 += 32) {
+        const int t0 = seg * S - 3;
+        for (int i0 = 0; i0 < S && !found; i0 += 32) {
           const int t = t0 + i0 + lane;
-          const bool hit = i0 + lane < kWinS && t >= 0 && t + w <= n_t && (int)(P[t + w] - P[t]) == gmax[k];
+          const bool hit = i0 + lane < S && t >= 0 && t + w <= n_t && (int)(P[t + w] - P[t]) == gmax[k];
           const unsigned h = __ballot_sync(0xffffffffu, hit);
           if (h) {
             if (lane == 0) atomicMin(&first[k], t0 + i0 + __ffs(h) - 1);
@@ -568,6 +622,11 @@ bool snr_config_supported(const sps_snr_config& c, std::string* why) {
     *why = "threads must be a multiple of 32 in [32, 512]";
     return false;
   }
+  if (c.samples != 0 && std::find(std::begin(kWinSegments), std::end(kWinSegments), c.samples) ==
+                            std::end(kWinSegments)) {
+    *why = "samples must be 0 (default) or one of 20, 28, 36, 44, 52";
+    return false;
+  }
   return true;
 }
 
@@ -587,19 +646,32 @@ SnrKernel snr_variant(int nwp) {
   }
 }
 
-typedef void (*WindowKernel)(SnrArgs, int, int32_t*);
+typedef void (*WindowKernel)(SnrArgs, int32_t*);
 
-WindowKernel window_variant(int nw) {
+template <int S>
+WindowKernel window_variant_s(int nw) {
   switch (nw) {
-    case 1: return snr_window_kernel<1>;
-    case 2: return snr_window_kernel<2>;
-    case 3: return snr_window_kernel<3>;
-    case 4: return snr_window_kernel<4>;
-    case 5: return snr_window_kernel<5>;
-    case 6: return snr_window_kernel<6>;
-    default: return snr_window_kernel<7>;
+    case 1: return snr_window_kernel<1, S>;
+    case 2: return snr_window_kernel<2, S>;
+    case 3: return snr_window_kernel<3, S>;
+    case 4: return snr_window_kernel<4, S>;
+    case 5: return snr_window_kernel<5, S>;
+    case 6: return snr_window_kernel<6, S>;
+    default: return snr_window_kernel<7, S>;
   }
 }
+
+WindowKernel window_variant(int nw, int S) {
+  switch (S) {
+    case 20: return window_variant_s<20>(nw);
+    case 36: return window_variant_s<36>(nw);
+    case 44: return window_variant_s<44>(nw);
+    case 52: return window_variant_s<52>(nw);
+    default: return window_variant_s<28>(nw);
+  }
+}
+
+int window_segment(const sps_snr_config& c) { return c.samples ? c.samples : kWinDefaultS; }
 
 // The register-window kernel serves sliding boxcars of widths 1, 2, ..., 2^(NW-1)
 // (NW <= 7) whose sums of squares fit 64 bits per row; it has no decimating
@@ -613,9 +685,9 @@ bool window_form(const SnrArgs& a, const sps_snr_config& c, int* threads) {
   return true;
 }
 
-size_t window_smem(int n_t, int nw) {
-  const int n_seg = (n_t + 3 + kWinS - 1) / kWinS;
-  return ((size_t)n_seg * kWinS + (size_t)(win_words(nw) + 3) / 4 * 4) * sizeof(uint32_t);
+size_t window_smem(int n_t, int nw, int S) {
+  const int n_seg = (n_t + 3 + S - 1) / S;
+  return ((size_t)n_seg * S + (size_t)win_words(nw, S)) * sizeof(uint32_t);
 }
 
 sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st) {
@@ -623,12 +695,13 @@ sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st
   if (!snr_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
   int wthreads = 0;
   if (window_form(a, c, &wthreads)) {
-    const size_t smem = window_smem(a.n_t, a.pow2_widths);
+    const int S = window_segment(c);
+    const size_t smem = window_smem(a.n_t, a.pow2_widths, S);
     if (sps_status s = check_row_fits(a.n_t, smem - prefix_smem(a.n_t) + 4096)) return s;
-    WindowKernel fn = window_variant(a.pow2_widths);
+    WindowKernel fn = window_variant(a.pow2_widths, S);
     SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (a.best) SPS_CUDA(cudaMemsetAsync(a.best, 0, 4 * sizeof(int32_t), st));
-    fn<<<a.n_dms, wthreads, smem, st>>>(a, 1, a.best);
+    fn<<<a.n_dms, wthreads, smem, st>>>(a, a.best);
     SPS_CUDA(cudaGetLastError());
     return SPS_OK;
   }

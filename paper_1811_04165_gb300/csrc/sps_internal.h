@@ -83,6 +83,7 @@ struct PresumPassArgs {
   void* out;
   int32_t out_u16;
   uint32_t* status;
+  int32_t window_bytes;    // staged bytes of one series window (the batched form reads it here)
 };
 
 // One pre-summed series: channels c0 .. c0 + n - 1, channel c0 + j (j < n - 1)
@@ -158,6 +159,14 @@ sps_status launch_presum_series(const uint8_t* x, int64_t pitch, int32_t in_len,
                                 int32_t n_units, int32_t unit_channels, int32_t max_rel, const PresumSeries* series,
                                 int32_t n_series, uint16_t* q, int32_t q_pitch, cudaStream_t st);
 sps_status launch_presum_pass(const PresumPassArgs& a, const sps_dedisp_config& cfg, cudaStream_t st);
+// Batched pre-summed pass: one launch over the work list of several passes of
+// configuration `cfg` (d_passes / d_work in device memory; max_data_bytes =
+// the largest data_bytes of the passes).  presum_pass_work appends the work
+// items of pass index `pass`; presum_pass_blocks counts them.
+sps_status launch_presum_pass_list(const PresumPassArgs* d_passes, const int4* d_work, int64_t n_work,
+                                   const sps_dedisp_config& cfg, int32_t max_data_bytes, cudaStream_t st);
+void presum_pass_work(const PresumPassArgs& a, const sps_dedisp_config& cfg, int32_t pass, std::vector<int4>* work);
+int64_t presum_pass_blocks(const PresumPassArgs& a, const sps_dedisp_config& cfg);
 sps_status launch_zap_copy(const uint8_t* x, int64_t pitch, int32_t in_len, const uint8_t* zap, int32_t channels,
                            uint8_t* out, int64_t out_pitch, cudaStream_t st);
 bool presum_config_supported(const sps_dedisp_config& cfg, std::string* why);
@@ -198,6 +207,15 @@ sps_status run_search(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_
                       double* snr, int32_t* peak_t, int32_t* peak_val, int32_t* best, cudaStream_t st);
 sps_status dedisperse_into(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
                            size_t ws_bytes, cudaStream_t st);
+// The batched brute-force form (batch.cpp): plans whose brute-force kernel is
+// the pre-summed one run their pre-pass here (checks, zapping, the series into
+// the workspace) and return the arguments of their pass, which a batched list
+// launch then runs; snr_into is the S/N step of sps_search on its own.
+bool batched_pass_form(const sps_plan* p);
+sps_status brute_prepass(const sps_plan* p, const uint8_t* x, int64_t pitch, int32_t* D, void* ws,
+                         size_t ws_bytes, cudaStream_t st, PresumPassArgs* args);
+sps_status snr_into(const sps_plan* p, const int32_t* D, double* snr, int32_t* peak_t, int32_t* peak_val,
+                    int32_t* best, cudaStream_t st);
 
 }  // namespace sps
 

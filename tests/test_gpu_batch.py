@@ -47,6 +47,9 @@ def test_batch_matches_each_beam_alone(lib, branches):
     plans[1].config = c
     ref = _alone(plans, xs)
     batch = lib.Batch(plans, xs, branches=branches)
+    # the pre-summed beams share their pass: one launch per kernel configuration
+    keys = {plans[b].config.brute.as_tuple() for b in range(len(plans)) if plans[b].config.brute.presum}
+    assert batch.list_launches == len(keys) >= 1
     for _ in range(2):  # a replay finds the previous launch's contents everywhere
         for o in batch.outs:
             o["D"].fill_(-1)
