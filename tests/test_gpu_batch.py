@@ -37,19 +37,39 @@ def _alone(plans, xs):
     return ref
 
 
+def _mixed_beams(lib):
+    """Beams of several shapes on several kernels: two pre-summed configurations
+    shared by beams of different channel counts, DM counts and lengths (fine DM
+    grids keep the pre-summed tables small on these wide channels), one on
+    pairs, and beams on the single-channel kernel."""
+    specs = [  # channels, DM trials, DM step, samples, brute-force configuration (None: single channels)
+        (96, 96, 0.10, 2000, (4, 16, 8, 1, 8, 2)), (64, 160, 0.08, 1777, (4, 16, 8, 1, 8, 2)),
+        (96, 64, 0.12, 1531, (2, 16, 4, 2, 8, 2)), (64, 40, 0.10, 2000, (2, 16, 4, 2, 8, 2)),
+        (96, 72, 0.10, 1900, (4, 16, 8, 1, 8, 1)), (96, 200, 1.00, 2000, None), (48, 64, 2.00, 1200, None)]
+    wls, cfgs = [], []
+    for b, (ch, n_dm, step, n_t, cfg) in enumerate(specs):
+        dms = synth.dm_grid(n_dm, step)
+        wls.append(synth.Workload(f"mix{b}", ch, 1250.0, 1550.0, 81.92e-6, n_t, dms,
+                                  np.array([1, 2, 4, 8][: 1 + b % 4], np.int32), seed=60 + b,
+                                  pulses=[synth.Pulse(float(dms[n_dm // 2]), 2.0, 30.0, n_t / 3.0)]))
+        cfgs.append(cfg)
+    plans, xs = _setup(lib, wls)
+    for p, cfg in zip(plans, cfgs):
+        c = p.config
+        c.brute = lib.DedispConfig(*cfg) if cfg else lib.DedispConfig(4, 16, 8, 1, 16, 0)
+        p.config = c
+    return wls, plans, xs
+
+
 @pytest.mark.parametrize("branches", [1, 3, 8])
 def test_batch_matches_each_beam_alone(lib, branches):
     import torch
-    wls = _beams()
-    plans, xs = _setup(lib, wls)
-    c = plans[1].config  # one beam on the single-channel kernel, the rest on their defaults
-    c.brute.presum = 0
-    plans[1].config = c
+    wls, plans, xs = _mixed_beams(lib)
     ref = _alone(plans, xs)
     batch = lib.Batch(plans, xs, branches=branches)
     # the pre-summed beams share their pass: one launch per kernel configuration
-    keys = {plans[b].config.brute.as_tuple() for b in range(len(plans)) if plans[b].config.brute.presum}
-    assert batch.list_launches == len(keys) >= 1
+    keys = {p.config.brute.as_tuple() for p in plans if p.config.brute.presum}
+    assert batch.list_launches == len(keys) == 3
     for _ in range(2):  # a replay finds the previous launch's contents everywhere
         for o in batch.outs:
             o["D"].fill_(-1)
@@ -90,14 +110,15 @@ def test_batch_mixes_smoothing_modes_and_zapping(lib):
     assert np.array_equal(batch.outs[1]["peak_t"].cpu().numpy(), pt)
 
 
-def test_batch_beam_against_the_oracle(lib):
+@pytest.mark.parametrize("b", [1, 2, 5])
+def test_batch_beam_against_the_oracle(lib, b):
+    """Beams of the two shared pre-summed passes and an unbatched beam, each
+    against the oracle outright."""
     import torch
-    wls = _beams()
-    plans, xs = _setup(lib, wls)
+    wls, plans, xs = _mixed_beams(lib)
     batch = lib.Batch(plans, xs, branches=2)
     batch.launch()
     torch.cuda.synchronize()
-    b = 2
     wl, x = wls[b], xs[b].cpu().numpy()
     D = batch.outs[b]["D"].cpu().numpy()
     want = oracle.dedisperse(x, oracle.delay_table(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, wl.dms), wl.n_t)
