@@ -56,6 +56,9 @@ def parse():
                     help="DM trials (fewer only for small profiling cases; bench lines use 2048)")
     ap.add_argument("--presum", type=int, choices=[0, 1, 2], default=None,
                     help="brute-force kernel: 0 single channels, 1 pairs, 2 quads (default: the plan's default)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-beam leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the real-time serving leg")
+    ap.add_argument("--no-tuning", action="store_true", help="skip the tuning leg")
     return ap.parse_args()
 
 
@@ -413,6 +416,124 @@ def launches_per_step(plan):
     return 2 + (1 if pow2 and plan.smoothing == 0 else 2)
 
 
+def device_noise(torch, shape, seed, dev):
+    """uint8 Gaussian-like noise (mean 128, sd 16) drawn on the device: inputs for
+    the legs whose timing and exactness checks do not depend on the values."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    x = torch.randn(shape, generator=g, device=dev).mul_(16).add_(128).round_().clamp_(0, 255)
+    return x.to(torch.uint8)
+
+
+def events_ms(torch, fn, reps, warm=2):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def leg_batched(torch, dev, reps=5):
+    """The batched-beam workload: 40 beams (alternately 1536 and 384 channels,
+    512-4096 DM trials with steps 0.1-0.5, 1-7 widths) per 1.024 s batch, as one
+    graph launch (sps_batch_*) against plain per-beam sps_search launches on one
+    stream; every beam's batched outputs must equal its own search's."""
+    import paper_1811_04165_gb300 as sps
+    from paper_1811_04165_gb300 import synth
+    wls = synth.batch_beams(40)
+    t0 = time.perf_counter()
+    plans = [sps.Plan.from_workload(wl) for wl in wls]
+    plan_s = time.perf_counter() - t0
+    xs = [device_noise(torch, (p.channels, p.pitch), 1000 + b, dev) for b, p in enumerate(plans)]
+    ws = torch.empty(max(sps.batch_workspace_bytes([p], 1) for p in plans), dtype=torch.uint8, device=dev)
+    outs = [p.alloc_outputs() for p in plans]
+
+    def per_beam():
+        for p, x, o in zip(plans, xs, outs):
+            p.search(x, out=o, workspace=ws)
+
+    t_beam = events_ms(torch, per_beam, reps)
+    del ws
+    batch = sps.Batch(plans, xs, branches=8)
+    t_batch = events_ms(torch, batch.launch, reps)
+    exact = all(torch.equal(o[k], r[k]) for o, r in zip(batch.outs, outs) for k in ("D", "snr", "peak_t",
+                                                                                    "peak_val", "best"))
+    samples = sum(wl.dm_trial_samples for wl in wls)
+    res = {"workload": "40 beams, 1536/384 channels, 512-4096 DM trials, 1-7 widths, 12500 samples each",
+           "value": samples / (t_batch * 1e-3), "unit": UNIT, "ms_per_batch": t_batch,
+           "per_beam_ms_per_batch": t_beam, "speedup_vs_per_beam": t_beam / t_batch,
+           "real_time_beams": len(wls) * 1024.0 / t_batch, "exact_vs_per_beam": exact,
+           "shared_pass_launches": batch.list_launches, "kernel_configs": "library defaults",
+           "plan_s": plan_s, "inputs": "device-drawn noise (timing and exactness do not depend on values)"}
+    del batch
+    torch.cuda.empty_cache()
+    return res
+
+
+def leg_serving(torch, dev, seconds=3.0):
+    """The real-time serving workload (sps_server_*): beams alternately 1536 and
+    384 channels, 1024-4096 DM trials, widths 1..64, 1.024 s batches arriving
+    as per-beam Poisson processes with +-50 ms jitter.  p50/p99 batch latency
+    (GPU completion on the host clock minus arrival) against the 1.024 s
+    deadline, for the server (8 slots, continuous batching) and for one batch
+    at a time (plain per-beam processing): 48 beams in real time, then 96
+    beams with the arrival period compressed to 96 ms, which emulates 1024
+    beams."""
+    import numpy as np
+    import paper_1811_04165_gb300 as sps
+    from paper_1811_04165_gb300 import serve_study
+    wls = serve_study.serve_beams(96)
+    t0 = time.perf_counter()
+    plans = [sps.Plan.from_workload(wl) for wl in wls]
+    plan_s = time.perf_counter() - t0
+    rng = np.random.Generator(np.random.PCG64(1))
+    host_x = {ch: torch.from_numpy(np.clip(np.rint(128 + 16 * rng.standard_normal((ch, 12500))), 0, 255)
+                                   .astype(np.uint8)).pin_memory() for ch in (384, 1536)}
+    budget = 32 << 30
+    out = {"deadline_s": serve_study.DEADLINE_S, "plan_s": plan_s, "hbm_budget_bytes": budget}
+    for name, n, period, dur in (("real_time_48_beams", 48, serve_study.DEADLINE_S, seconds),
+                                 ("emulated_1024_beams", 96, 0.096, seconds * 0.096 / serve_study.DEADLINE_S * 4)):
+        for mode, inflight in (("served", 8), ("per_beam", 1)):
+            r = serve_study.run(plans[:n], host_x, period, dur, inflight, seed=n, budget=budget)
+            r["period_s"] = period
+            r["within_period"] = r["p99_s"] <= period
+            out[f"{name}/{mode}"] = r
+    return out
+
+
+def leg_tuning(torch, dev):
+    """The tuner against exhaustive search on this workload: the committed
+    live-measured table of the beam's reduced brute-force space replayed with
+    the GA and random search at 10 % of its valid points over 20 seeds each,
+    and the table's optimum and the default configuration re-timed live."""
+    import paper_1811_04165_gb300 as sps
+    from paper_1811_04165_gb300 import synth, tune_study
+    tab = tune_study.load_table(tune_study.BEAM_TABLE)
+    res = tune_study.replay(tab, seeds=range(20), budget_frac=0.1)
+    wl = synth.apertif_beam()
+    plan = sps.Plan.from_workload(wl)
+    default = plan.config
+    x = device_noise(torch, (plan.channels, plan.pitch), 7, dev)
+    o = plan.alloc_outputs()
+    ws = plan.workspace()
+    live = {}
+    for name, point in (("optimum", tab["optimum_point"]), ("default", tab["default_point"])):
+        if point is None:
+            continue
+        plan.config = sps.sps_tune_config(plan, sps.SPACE_REDUCED, point)
+        live[name] = events_ms(torch, lambda: plan.search(x, out=o, workspace=ws), 20, warm=3)
+    plan.config = default
+    res["live_ms"] = live
+    if "optimum" in live and "default" in live:
+        res["live_default_over_optimum"] = live["default"] / live["optimum"]
+    return res
+
+
 def time_path(torch, plan, xs, outs, steps, warmup, ws, flush, with_events=True):
     """Per-step CUDA-event times (ms) of [dedisperse, snr+detect] on the current stream."""
     import paper_1811_04165_gb300 as sps
@@ -533,6 +654,15 @@ def main():
                            "dedisperse_ms": statistics.mean(a for a, _ in ts),
                            "snr_detect_ms": statistics.mean(b for _, b in ts),
                            "subbands": 32, "coarse_dms": 64}
+
+    # ---- the batched-beam, serving and tuning workloads (rank 0 of a single-GPU run)
+    if world == 1 and args.dms == 2048:
+        if not args.no_batched:
+            line["batched"] = leg_batched(torch, dev)
+        if not args.no_serving:
+            line["serving"] = leg_serving(torch, dev)
+        if not args.no_tuning:
+            line["tuning"] = leg_tuning(torch, dev)
 
     # ---- end to end through the host entry point
     if args.no_e2e:

@@ -111,11 +111,7 @@ typedef struct {
 
 /* Launch parameters of the fused boxcar + S/N kernel. */
 typedef struct {
-  int32_t threads;            /* threads per block (one block per DM row); the
-                                 register-window form used for widths 1, 2, 4, ...
-                                 runs min(threads, 128)                            */
-  int32_t samples;            /* register-window form: outputs per thread segment,
-                                 0 (default, 28) or one of 20, 28, 36, 44, 52      */
+  int32_t threads;            /* threads per block (one block per DM row)           */
 } sps_snr_config;
 
 typedef struct {
@@ -353,7 +349,7 @@ sps_status sps_tune(sps_plan* plan, int32_t which, const sps_search_desc* desc, 
  * branches (beams spread over the branches by work, largest first);
  * sps_batch_launch replays the graph on a stream.  Beams on the pre-summed
  * brute-force kernel share their pass: the graph runs their pre-passes, then
- * one pass launch per kernel configuration over a device work list of (beam,
+ * one pass launch per kernel configuration (and occupancy class) over a device work list of (beam,
  * DM tile, time tile) descriptors of all those beams, then their S/N kernels;
  * other beams run their whole search on a branch.  Results are those of each
  * beam's own sps_search.  The ALERT setting
@@ -383,7 +379,9 @@ sps_status sps_batch_workspace_bytes(const sps_plan* const* plans, int32_t n_bea
 sps_status sps_batch_create(const sps_plan* const* plans, const sps_beam_buffers* buffers, int32_t n_beams,
                             int32_t branches, void* workspace, size_t workspace_bytes, sps_batch** out);
 sps_status sps_batch_launch(sps_batch* batch, void* stream);
-/* How many shared-pass launches (one per kernel configuration) the graph holds. */
+/* How many shared-pass launches the graph holds (one per kernel configuration
+ * and occupancy class: beams whose stages allow the same number of resident
+ * blocks per SM share a launch). */
 sps_status sps_batch_list_launches(const sps_batch* batch, int32_t* n);
 sps_status sps_batch_destroy(sps_batch* batch);
 

@@ -43,10 +43,10 @@ class DedispConfig(ctypes.Structure):
 
 
 class SnrConfig(ctypes.Structure):
-    _fields_ = [("threads", ctypes.c_int32), ("samples", ctypes.c_int32)]
+    _fields_ = [("threads", ctypes.c_int32)]
 
     def as_tuple(self):
-        return (self.threads, self.samples)
+        return (self.threads,)
 
 
 class KernelConfig(ctypes.Structure):

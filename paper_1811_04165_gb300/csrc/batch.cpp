@@ -42,10 +42,16 @@ size_t round_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 double beam_work(const sps_plan* p) { return (double)p->dms.size() * p->n_t * p->channels; }
 
-using ConfigKey = std::tuple<int32_t, int32_t, int32_t, int32_t, int32_t, int32_t>;
+// Beams share a pass launch when they have the same kernel configuration and
+// the same number of resident blocks per SM: the launch gives every block the
+// largest stage of its beams, which must not cost the others occupancy.
+using ConfigKey = std::tuple<int32_t, int32_t, int32_t, int32_t, int32_t, int32_t, int32_t>;
 
-ConfigKey key_of(const sps_dedisp_config& c) {
-  return ConfigKey{c.dms_per_thread, c.samples_per_thread, c.warps_dm, c.warps_time, c.chunk, c.presum};
+ConfigKey key_of(const sps_plan* p, int32_t smem_per_sm) {
+  const sps_dedisp_config& c = p->cfg.brute;
+  const size_t per_block = presum_smem_bytes(c, p->presum_data_bytes) + 1024;  // + the block's reserved share
+  const int32_t resident = (int32_t)std::max<size_t>(1, (size_t)smem_per_sm / per_block);
+  return ConfigKey{c.dms_per_thread, c.samples_per_thread, c.warps_dm, c.warps_time, c.chunk, c.presum, resident};
 }
 
 // The batch's layout: each beam's branch, whether its pass is batched, and
@@ -132,10 +138,12 @@ sps_status sps_batch_create(const sps_plan* const* plans, const sps_beam_buffers
   if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace % kAlign))
     return fail(SPS_ERR_INVALID_ARG, "workspace missing, smaller than sps_batch_workspace_bytes or not 256-byte aligned");
 
-  // batched passes grouped by kernel configuration, beams in order
+  // batched passes grouped by kernel configuration and occupancy, beams in order
+  int32_t smem_per_sm = 0;
+  SPS_CUDA(cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
   std::map<ConfigKey, std::vector<int32_t>> groups;
   for (int32_t b = 0; b < n_beams; b++)
-    if (L.batched[b]) groups[key_of(plans[b]->cfg.brute)].push_back(b);
+    if (L.batched[b]) groups[key_of(plans[b], smem_per_sm)].push_back(b);
   std::vector<int32_t> pass_of(n_beams, -1);  // index into the passes array
   int32_t n_passes = 0;
   for (auto& g : groups)

@@ -111,7 +111,7 @@ std::vector<sps_kernel_config> default_configs() {
   c.brute = {4, 16, 8, 1, 16, 2};
   c.step1 = u8[0];
   c.step2 = s2[0];
-  c.snr = {256, 0};
+  c.snr = {256};
   out.push_back(c);
   for (int k = 0; k < 3; k++) {
     c.brute = u8[k];

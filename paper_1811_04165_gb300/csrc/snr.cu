@@ -350,12 +350,24 @@ __device__ void detect_block(const double* snr, const int32_t* peak_t, const int
   __shared__ int si[32], sw[32];
   double bv = -1.0;
   int bi = 0x7fffffff, bw = 0x7fffffff;
-  // every (width, DM) entry once; the tie rules make the visiting order irrelevant
+  // every (width, DM) entry once; the tie rules make the visiting order
+  // irrelevant.  Eight loads are issued before any is compared, so that one
+  // thread has eight table reads in flight.
+  constexpr int kBatch = 8;
   for (int w = 0; w < n_widths; w++) {
     const double* row = snr + (int64_t)w * n_dms;
-    for (int i = threadIdx.x; i < n_dms; i += blockDim.x) {
-      const double v = L2 ? __ldcg(row + i) : __ldg(row + i);
-      if (better(v, i, w, bv, bi, bw)) { bv = v; bi = i; bw = w; }
+    for (int i0 = threadIdx.x; i0 < n_dms; i0 += kBatch * blockDim.x) {
+      double v[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; u++) {
+        const int i = i0 + u * blockDim.x;
+        v[u] = i < n_dms ? (L2 ? __ldcg(row + i) : __ldg(row + i)) : -1.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; u++) {
+        const int i = i0 + u * blockDim.x;
+        if (i < n_dms && better(v[u], i, w, bv, bi, bw)) { bv = v[u]; bi = i; bw = w; }
+      }
     }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -394,32 +406,26 @@ detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
 }
 
 // ---------------------------------------------------------------------------
-// Register-window form for width sets {1, 2, 4, ..., 2^(NW-1)} (the
-// smoothing widths of the search; AMBER's are powers of two as well).
+// Vector form for width sets {1, 2, 4, ..., 2^(NW-1)} (the smoothing widths of
+// the search; AMBER's are powers of two as well).
 //
 // The row is staged and scanned into prefix sums as above (P[k] at buf[3 + k]),
-// here with 16-byte shared accesses.  Then each thread takes segments of S
-// consecutive outputs t = t0 .. t0 + S - 1 (t0 = seg * S - 3, so the window's
-// first word is 16-byte aligned) and loads the window P[t0 .. t0 + S +
-// 2^(NW-1)) into registers with 16-byte shared loads (S / 4 odd:
-// conflict-free).  With the widths known at compile time, every boxcar is one
-// register subtraction B = P[t + w] - P[t], and each (sample, width) costs a
-// subtract and a maximum on the integer ALU and one 32 x 32 -> 64-bit
-// multiply-add on the FMA pipe -- no shared-memory access.  The first and last
-// segments, where some outputs fall outside [0, N_t - w], take a compact loop
-// over P in shared memory instead (the unrolled body stays small enough for
-// the instruction cache).  S1 comes in closed form as in snr_kernel.
+// here with 16-byte shared accesses.  Then the outputs are taken four at a
+// time: group j holds t = 4j - 3 .. 4j, whose P[t] are the aligned word
+// quadruple buf[4j .. 4j + 3].  With the widths known at compile time every
+// P[t + w] is a 16-byte load too: buf[4j + 4] serves w = 1, 2 and 4, and
+// buf[4j + w] (w a multiple of 4) the wider ones; consecutive lanes read
+// consecutive quadruples (no bank conflicts).  So a group costs NW - 1 shared
+// loads for 4 NW boxcars, each boxcar a subtract, a maximum (integer ALU) and
+// one 32 x 32 -> 64-bit multiply-add (FMA pipe).  Outputs outside [0, N_t - w]
+// contribute B = 0 (neither the sum of squares nor the maximum changes); only
+// the first and last groups need that test.  S1 comes in closed form as in
+// snr_kernel.
 //
 // Detection is folded in: `best` (int32[4]) is zeroed before the launch; each
 // block, once its outputs are written, counts itself in best[3]; the block
 // that counts last reads the whole table (through L2) and writes the
 // detection over the counter.
-constexpr int kWinThreads = 128;
-// Segment lengths with a compiled register-window kernel (a multiple of 4 with S / 4 odd).
-constexpr int kWinSegments[] = {20, 28, 36, 44, 52};
-constexpr int kWinDefaultS = 28;
-
-__host__ __device__ constexpr int win_words(int NW, int S) { return (S + (1 << (NW - 1)) + 3) / 4 * 4; }
 
 // Row i into buf[4 .. 4 + n_t), scanned in place into P[k] = buf[3 + k]
 // (k = 0 .. n_t); *seg = the sum of the samples this thread scanned.  Each
@@ -469,16 +475,18 @@ __device__ bool load_prefix_v4(const int32_t* row, int n_t, uint32_t* buf, uint3
   return true;
 }
 
-template <int NW, int S>
-__global__ void __launch_bounds__(kWinThreads, S <= 28 ? 4 : 3) snr_window_kernel(SnrArgs a, int32_t* best) {
-  static_assert(S % 4 == 0 && (S / 4) % 2 == 1, "segment length: a multiple of 4 with S / 4 odd");
+__device__ __forceinline__ uint32_t quad(const uint4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+template <int NW>
+__global__ void __launch_bounds__(kMaxThreads, 2) snr_vec4_kernel(SnrArgs a, int32_t* best) {
   constexpr int WMAX = 1 << (NW - 1);
-  constexpr int WIN = win_words(NW, S);
   extern __shared__ __align__(16) uint32_t buf[];
   __shared__ uint32_t scratch[32];
   __shared__ uint64_t bar;
-  __shared__ unsigned long long ps1[kWinThreads / 32][NW], ps2[kWinThreads / 32][NW];
-  __shared__ uint32_t pmx[kWinThreads / 32][NW];
+  __shared__ unsigned long long ps1[kMaxThreads / 32][NW], ps2[kMaxThreads / 32][NW];
+  __shared__ uint32_t pmx[kMaxThreads / 32][NW];
   __shared__ int gmax[NW], first[NW];
   __shared__ int is_last;
   const int row = blockIdx.x;
@@ -488,40 +496,35 @@ __global__ void __launch_bounds__(kWinThreads, S <= 28 ? 4 : 3) snr_window_kerne
   if (!load_prefix_v4(a.D + (int64_t)row * n_t, n_t, buf, scratch, &bar, a.status, &segsum)) return;
   const uint32_t* P = buf + 3;  // P[k], k = 0 .. n_t
 
-  const int n_seg = (n_t + 3 + S - 1) / S;
+  const int n_grp = (n_t + 3 + 3) / 4;  // groups of t = 4j - 3 .. 4j covering 0 .. n_t - 1
   uint32_t mx[NW];
   unsigned long long s2[NW];
 #pragma unroll
   for (int k = 0; k < NW; k++) { mx[k] = 0u; s2[k] = 0ull; }
   if (threadIdx.x < NW) first[threadIdx.x] = 0x7fffffff;
-  for (int seg = threadIdx.x; seg < n_seg; seg += blockDim.x) {
-    const int t0 = seg * S - 3;
-    if (t0 >= 0 && t0 + S - 1 + WMAX <= n_t) {
-      uint32_t p[WIN];
-      const uint4* src = reinterpret_cast<const uint4*>(buf + seg * S);
+  for (int j = threadIdx.x; j < n_grp; j += blockDim.x) {
+    const int t0 = 4 * j - 3;
+    const uint4 A = *reinterpret_cast<const uint4*>(buf + 4 * j);        // P[t0 .. t0 + 3]
+    const uint4 N = *reinterpret_cast<const uint4*>(buf + 4 * j + 4);    // P[t0 + 4 .. t0 + 7]
+    const bool full = t0 >= 0 && t0 + 3 + WMAX <= n_t;
 #pragma unroll
-      for (int j = 0; j < WIN / 4; j++) {
-        const uint4 v = src[j];
-        p[4 * j] = v.x; p[4 * j + 1] = v.y; p[4 * j + 2] = v.z; p[4 * j + 3] = v.w;
-      }
+    for (int k = 0; k < NW; k++) {
+      constexpr int dummy = 0;
+      (void)dummy;
+      const int w = 1 << k;
+      uint4 Q;
+      if (w >= 8) Q = *reinterpret_cast<const uint4*>(buf + 4 * j + w);  // P[t0 + w .. t0 + w + 3]
 #pragma unroll
-      for (int k = 0; k < NW; k++)
-#pragma unroll
-        for (int i = 0; i < S; i++) {
-          const uint32_t B = p[i + (1 << k)] - p[i];
-          s2[k] += (unsigned long long)B * B;
-          mx[k] = max(mx[k], B);
+      for (int i = 0; i < 4; i++) {
+        // P[t0 + i + w]
+        const uint32_t hi = w >= 8 ? quad(Q, i) : (i + w < 4 ? quad(A, i + w) : quad(N, i + w - 4));
+        uint32_t B = hi - quad(A, i);
+        if (!full) {
+          const int t = t0 + i;
+          B = (t >= 0 && t + w <= n_t) ? B : 0u;
         }
-    } else {
-#pragma unroll
-      for (int k = 0; k < NW; k++) {
-        const int lo = max(t0, 0), hi = min(t0 + S, n_t - (1 << k) + 1);
-#pragma unroll 1
-        for (int t = lo; t < hi; t++) {
-          const uint32_t B = P[t + (1 << k)] - P[t];
-          s2[k] += (unsigned long long)B * B;
-          mx[k] = max(mx[k], B);
-        }
+        s2[k] += (unsigned long long)B * B;
+        mx[k] = max(mx[k], B);
       }
     }
   }
@@ -555,7 +558,7 @@ __global__ void __launch_bounds__(kWinThreads, S <= 28 ? 4 : 3) snr_window_kerne
   }
   __syncthreads();
   // first position of each maximum: the warp of each thread holding it searches
-  // that thread's segments, in order, 32 outputs at a time
+  // that thread's groups, 8 groups (32 outputs) at a time, in order
 #pragma unroll
   for (int k = 0; k < NW; k++) {
     const int w = 1 << k;
@@ -563,17 +566,17 @@ __global__ void __launch_bounds__(kWinThreads, S <= 28 ? 4 : 3) snr_window_kerne
     while (owners) {
       const int o = __ffs(owners) - 1;
       owners &= owners - 1;
-      bool found = false;
-      for (int seg = warp * 32 + o; seg < n_seg && !found; seg += blockDim.x) {
-        const int t0 = seg * S - 3;
-        for (int i0 = 0; i0 < S && !found; i0 += 32) {
-          const int t = t0 + i0 + lane;
-          const bool hit = i0 + lane < S && t >= 0 && t + w <= n_t && (int)(P[t + w] - P[t]) == gmax[k];
-          const unsigned h = __ballot_sync(0xffffffffu, hit);
-          if (h) {
-            if (lane == 0) atomicMin(&first[k], t0 + i0 + __ffs(h) - 1);
-            found = true;
-          }
+      const int owner = warp * 32 + o;
+      for (int m0 = 0; owner + m0 * (int)blockDim.x < n_grp; m0 += 8) {
+        // lane -> group owner + (m0 + lane / 4) * blockDim, output lane % 4 of it
+        const int j = owner + (m0 + (lane >> 2)) * (int)blockDim.x;
+        const int t = 4 * j - 3 + (lane & 3);
+        const bool hit = j < n_grp && t >= 0 && t + w <= n_t && (int)(P[t + w] - P[t]) == gmax[k];
+        const unsigned h = __ballot_sync(0xffffffffu, hit);
+        if (h) {
+          const int l = __ffs(h) - 1;
+          if (lane == 0) atomicMin(&first[k], 4 * (owner + (m0 + (l >> 2)) * (int)blockDim.x) - 3 + (l & 3));
+          break;
         }
       }
     }
@@ -622,11 +625,6 @@ bool snr_config_supported(const sps_snr_config& c, std::string* why) {
     *why = "threads must be a multiple of 32 in [32, 512]";
     return false;
   }
-  if (c.samples != 0 && std::find(std::begin(kWinSegments), std::end(kWinSegments), c.samples) ==
-                            std::end(kWinSegments)) {
-    *why = "samples must be 0 (default) or one of 20, 28, 36, 44, 52";
-    return false;
-  }
   return true;
 }
 
@@ -646,62 +644,46 @@ SnrKernel snr_variant(int nwp) {
   }
 }
 
-typedef void (*WindowKernel)(SnrArgs, int32_t*);
+typedef void (*Vec4Kernel)(SnrArgs, int32_t*);
 
-template <int S>
-WindowKernel window_variant_s(int nw) {
+Vec4Kernel vec4_variant(int nw) {
   switch (nw) {
-    case 1: return snr_window_kernel<1, S>;
-    case 2: return snr_window_kernel<2, S>;
-    case 3: return snr_window_kernel<3, S>;
-    case 4: return snr_window_kernel<4, S>;
-    case 5: return snr_window_kernel<5, S>;
-    case 6: return snr_window_kernel<6, S>;
-    default: return snr_window_kernel<7, S>;
+    case 1: return snr_vec4_kernel<1>;
+    case 2: return snr_vec4_kernel<2>;
+    case 3: return snr_vec4_kernel<3>;
+    case 4: return snr_vec4_kernel<4>;
+    case 5: return snr_vec4_kernel<5>;
+    case 6: return snr_vec4_kernel<6>;
+    default: return snr_vec4_kernel<7>;
   }
 }
 
-WindowKernel window_variant(int nw, int S) {
-  switch (S) {
-    case 20: return window_variant_s<20>(nw);
-    case 36: return window_variant_s<36>(nw);
-    case 44: return window_variant_s<44>(nw);
-    case 52: return window_variant_s<52>(nw);
-    default: return window_variant_s<28>(nw);
-  }
-}
-
-int window_segment(const sps_snr_config& c) { return c.samples ? c.samples : kWinDefaultS; }
-
-// The register-window kernel serves sliding boxcars of widths 1, 2, ..., 2^(NW-1)
+// The vector kernel serves sliding boxcars of widths 1, 2, ..., 2^(NW-1)
 // (NW <= 7) whose sums of squares fit 64 bits per row; it has no decimating
-// form.  Its block is min(threads, 128) threads.
-bool window_form(const SnrArgs& a, const sps_snr_config& c, int* threads) {
+// form.
+bool vec4_form(const SnrArgs& a) {
   if (a.decimate || a.pow2_widths < 1 || a.pow2_widths > 7 || !tma_ok(a.D, a.n_t)) return false;
   const long double bmax = (long double)std::max<int64_t>(1, a.max_boxcar);
   // the block total of S2 (at most N_t squares) is kept in 64 bits
-  if ((long double)a.n_t * bmax * bmax >= 1.8e19L) return false;
-  *threads = std::min(c.threads, kWinThreads);
-  return true;
+  return (long double)a.n_t * bmax * bmax < 1.8e19L;
 }
 
-size_t window_smem(int n_t, int nw, int S) {
-  const int n_seg = (n_t + 3 + S - 1) / S;
-  return ((size_t)n_seg * S + (size_t)win_words(nw, S)) * sizeof(uint32_t);
+// Words of the row buffer: the groups' quadruples and the widest width's reach.
+size_t vec4_smem(int n_t, int nw) {
+  const int n_grp = (n_t + 6) / 4;
+  return ((size_t)4 * n_grp + 4 + (1 << (nw - 1)) + 4) * sizeof(uint32_t);
 }
 
 sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st) {
   std::string why;
   if (!snr_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
-  int wthreads = 0;
-  if (window_form(a, c, &wthreads)) {
-    const int S = window_segment(c);
-    const size_t smem = window_smem(a.n_t, a.pow2_widths, S);
-    if (sps_status s = check_row_fits(a.n_t, smem - prefix_smem(a.n_t) + 4096)) return s;
-    WindowKernel fn = window_variant(a.pow2_widths, S);
+  if (vec4_form(a)) {
+    const size_t smem = vec4_smem(a.n_t, a.pow2_widths);
+    if (sps_status s = check_row_fits(a.n_t, smem - prefix_smem(a.n_t) + 8192)) return s;
+    Vec4Kernel fn = vec4_variant(a.pow2_widths);
     SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (a.best) SPS_CUDA(cudaMemsetAsync(a.best, 0, 4 * sizeof(int32_t), st));
-    fn<<<a.n_dms, wthreads, smem, st>>>(a, a.best);
+    fn<<<a.n_dms, c.threads, smem, st>>>(a, a.best);
     SPS_CUDA(cudaGetLastError());
     return SPS_OK;
   }

@@ -25,6 +25,7 @@ median over three trials of the mean time of back-to-back searches.
 """
 import argparse
 import json
+import os
 import statistics
 import sys
 import time
@@ -241,6 +242,45 @@ def study_beam_table(seeds, budget_frac, reps, table_out=None):
                        "kernel_of": [int(k) for k in ko], "values": out["genes"],
                        "default_point": list(default_pt) if default_pt is not None else None,
                        "points": [[list(pt), (f if np.isfinite(f) else None)] for pt, f in table.items()]}, f)
+    return out
+
+
+# The committed table of the beam's reduced brute-force space (written by
+# `--beam-table`): every valid point's live fitness on a GB300.
+BEAM_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned", "gb300_apertif_brute_reduced.json")
+
+
+def load_table(path):
+    """A fitness table written by study_beam_table: {n_values, kernel_of,
+    values, default_point, table {point: ms (inf for a failed run)}, optimum_point,
+    optimum_ms, ...}; points outside `table` break the plan's boundary conditions."""
+    with open(path) as f:
+        rec = json.load(f)
+    table = {tuple(p): (float("inf") if v is None else float(v)) for p, v in rec["points"]}
+    finite = {p: v for p, v in table.items() if np.isfinite(v)}
+    opt = min(finite, key=finite.get)
+    rec["table"] = table
+    rec["optimum_point"] = list(opt)
+    rec["optimum_ms"] = finite[opt]
+    rec["valid"] = len(table)
+    return rec
+
+
+def replay(rec, seeds, budget_frac=0.1):
+    """GA and random search on a stored table at `budget_frac` of its valid
+    points: best-of-run relative to the table's optimum, and the default
+    configuration's ratio."""
+    table, nv, ko = rec["table"], rec["n_values"], rec["kernel_of"]
+    budget = max(1, int(budget_frac * len(table)))
+    valid = table.__contains__
+    opt = rec["optimum_ms"]
+    seeds = list(seeds)
+    out = {"table": os.path.basename(rec.get("path", "")) or "stored", "gpu": rec.get("gpu"),
+           "workload": rec.get("workload"), "valid_points": len(table), "budget": budget,
+           "optimum_ms": opt, "ga": _summary(_runs(nv, ko, table, TUNE_GA, seeds, budget, valid), opt),
+           "random": _summary(_runs(nv, ko, table, TUNE_RANDOM, seeds, budget, valid), opt)}
+    dp = rec.get("default_point")
+    out["default_ratio"] = table[tuple(dp)] / opt if dp is not None and tuple(dp) in table else None
     return out
 
 

@@ -68,8 +68,9 @@ def test_batch_matches_each_beam_alone(lib, branches):
     ref = _alone(plans, xs)
     batch = lib.Batch(plans, xs, branches=branches)
     # the pre-summed beams share their pass: one launch per kernel configuration
+    # (and occupancy class, which may split one)
     keys = {p.config.brute.as_tuple() for p in plans if p.config.brute.presum}
-    assert batch.list_launches == len(keys) == 3
+    assert len(keys) == 3 and 3 <= batch.list_launches <= 5
     for _ in range(2):  # a replay finds the previous launch's contents everywhere
         for o in batch.outs:
             o["D"].fill_(-1)

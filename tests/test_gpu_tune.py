@@ -138,3 +138,40 @@ def test_live_tuning_log_resume_and_saved_config(lib, tmp_path):
     other, _ = _setup(lib, other_wl)
     with pytest.raises(ValueError):
         other.load_config(str(cfg))
+
+
+def test_live_ga_on_the_beam_within_five_percent_of_its_table_optimum(lib):
+    """Live GA on the benchmark workload's reduced space at 10 % of its valid
+    points: its configuration, re-timed, is within 5 % of the committed
+    exhaustive table's optimum re-timed in the same run, and gives the same
+    results."""
+    import torch
+    from paper_1811_04165_gb300 import tune_study
+    wl = synth.apertif_beam()
+    p, x = _setup(lib, wl)
+    rec = tune_study.load_table(tune_study.BEAM_TABLE)
+    assert [int(v) for v in lib.sps_tune_space(p, lib.SPACE_REDUCED)[0]] == rec["n_values"]
+    want = {k: v.clone() for k, v in p.search(x).items()}
+    out, ws = p.alloc_outputs(), p.workspace()
+
+    def timed():
+        for _ in range(3):
+            p.search(x, out=out, workspace=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            p.search(x, out=out, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 20
+
+    best, res, _ = lib.sps_tune(p, x, which=lib.SPACE_REDUCED, reps=2,
+                                desc=lib.search_desc(max_evaluations=int(0.1 * rec["valid"]), seed=1))
+    assert res.evaluations <= int(0.1 * rec["valid"])
+    t_ga = timed()
+    for k in ("D", "snr", "peak_t", "peak_val", "best"):
+        assert torch.equal(out[k], want[k]), k
+    p.config = lib.sps_tune_config(p, lib.SPACE_REDUCED, rec["optimum_point"])
+    t_opt = timed()
+    assert t_ga <= 1.05 * t_opt, (t_ga, t_opt, best)
