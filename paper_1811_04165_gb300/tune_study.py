@@ -245,6 +245,92 @@ def study_beam_table(seeds, budget_frac, reps, table_out=None):
     return out
 
 
+def study_subband_joint(subbands=(16, 32, 64), evals=300, reps=2, seed=1):
+    """The beam's two-step path with the subband count as one more gene (the
+    joint space of step one, step two and S/N genes times S): the library GA
+    (sps_optimize) over it with live fitness -- the median over three trials of
+    the mean time of `reps` searches -- against random search at the same
+    budget.  Each S is its own plan (its own delay tables, and so its own
+    exact result); points a plan rejects are invalid."""
+    import torch
+    plans = {}
+    for S in subbands:
+        wl = synth.apertif_beam(subband=True)
+        wl.n_subbands = S
+        plans[S] = Plan.from_workload(wl)
+    pitch = max(p.pitch for p in plans.values())
+    wl = synth.apertif_beam()
+    x = torch.from_numpy(synth.filterbank(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, pitch, wl.seed, wl.pulses,
+                                          pitch=pitch)).cuda()
+    nv0, ko0, values0 = sps_tune_space(plans[subbands[0]], SPACE_REDUCED)
+    nv = [len(subbands)] + [int(v) for v in nv0]
+    ko = [0] + [int(k) + 1 for k in ko0]
+    outs = {S: p.alloc_outputs() for S, p in plans.items()}
+    wss = {S: p.workspace() for S, p in plans.items()}
+    defaults = {S: p.config for S, p in plans.items()}
+
+    def config_of(pt):
+        S = subbands[pt[0]]
+        return S, sps_tune_config(plans[S], SPACE_REDUCED, list(pt[1:]))
+
+    def valid(pt):
+        try:
+            config_of(pt)
+            return True
+        except Exception:
+            return False
+
+    def fitness(pt):
+        S, cfg = config_of(pt)
+        p = plans[S]
+        p.config = cfg
+        o, ws = outs[S], wss[S]
+        p.search(x, out=o, workspace=ws)
+        trials = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                p.search(x, out=o, workspace=ws)
+            e1.record()
+            torch.cuda.synchronize()
+            trials.append(e0.elapsed_time(e1) / reps)
+        return sorted(trials)[1]
+
+    res = {"workload": "apertif-1536ch-12500s-2048dm two-step", "subbands": list(subbands),
+           "genes": ["subbands"] + [f"gene{g}" for g in range(len(nv0))], "points": int(np.prod(nv)),
+           "budget": evals}
+    for name, alg in (("ga", TUNE_GA), ("random", TUNE_RANDOM)):
+        t0 = time.perf_counter()
+        best, r, trace = sps_optimize(nv, ko, fitness, valid,
+                                      search_desc(algorithm=alg, max_evaluations=evals, seed=seed))
+        S, cfg = config_of(best)
+        by_s = {}
+        for pt, f in trace:
+            if np.isfinite(f):
+                by_s.setdefault(subbands[pt[0]], []).append(f)
+        res[name] = {"best_ms": r.best_fitness, "subbands": S, "config": cfg.as_dict(), "evaluations": r.evaluations,
+                     "seconds": time.perf_counter() - t0,
+                     "best_ms_per_subbands": {str(k): min(v) for k, v in by_s.items()}}
+    for S, p in plans.items():
+        p.config = defaults[S]
+    res["default_ms"] = {str(S): fitness([i] + list(_point_of(plans[S], defaults[S], values0)))
+                         for i, S in enumerate(subbands)
+                         if _point_of(plans[S], defaults[S], values0) is not None}
+    return res
+
+
+def _point_of(plan, cfg, values):
+    """The reduced-space point of a configuration, or None if it lies outside."""
+    for pt in np.ndindex(*[len(v) for v in values]):
+        try:
+            if sps_tune_config(plan, SPACE_REDUCED, list(pt)).as_dict() == cfg.as_dict():
+                return pt
+        except Exception:
+            continue
+    return None
+
+
 # The committed table of the beam's reduced brute-force space (written by
 # `--beam-table`): every valid point's live fitness on a GB300.
 BEAM_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned", "gb300_apertif_brute_reduced.json")
@@ -293,7 +379,17 @@ def main(argv=None):
     ap.add_argument("--out", default=None)
     ap.add_argument("--beam-table", default=None, metavar="FILE",
                     help="only the beam's reduced-space study; writes its fitness table to FILE")
+    ap.add_argument("--subband-joint", type=int, default=0, metavar="EVALS",
+                    help="only the two-step joint study with the subband count as a gene, EVALS per search")
     a = ap.parse_args(argv)
+    if a.subband_joint:
+        res = {"subband_joint": study_subband_joint(evals=a.subband_joint, reps=a.reps)}
+        text = json.dumps(res, indent=1, default=lambda v: v.item() if hasattr(v, "item") else str(v))
+        if a.out:
+            with open(a.out, "w") as f:
+                f.write(text + "\n")
+        print(text)
+        return 0
     if a.beam_table:
         res = {"apertif_beam_table": study_beam_table(range(a.seeds), 0.1, a.reps, a.beam_table)}
         text = json.dumps(res, indent=1, default=lambda v: v.item() if hasattr(v, "item") else str(v))

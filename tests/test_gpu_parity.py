@@ -609,3 +609,26 @@ def test_snr_power_of_two_widths_edges(lib, n_t, n_w, threads):
     bi, bw = oracle.detect(s)
     assert _to_np(out["best"]).tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])]
     assert p.status() == 0
+
+
+@pytest.mark.parametrize("S", [16, 64])
+def test_apertif_subband_counts_full_tables(lib, S):
+    """The beam's two-step path with 16 and 64 subbands (the counts the joint
+    tuner explores beside 32): every element of D and the S/N tables against
+    the oracle's two steps with that subband count."""
+    torch = _torch()
+    wl = synth.apertif_beam(subband=True)
+    wl.n_subbands = S
+    d1, d2 = oracle.subband_tables(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, S, wl.coarse_dms, wl.dms)
+    n_1, n_in = oracle.subband_lengths(wl.n_t, d1, d2)
+    p = lib.Plan.from_workload(wl)
+    assert (p.step1_samples, p.input_samples) == (n_1, n_in)
+    x = synth.filterbank(wl.channels, wl.f_lo, wl.f_hi, wl.t_samp, n_in, wl.seed, wl.pulses, pitch=p.pitch)
+    out = p.search(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    Y = oracle_rows.subband_step1(x, d1, S, n_1)
+    Do = oracle_rows.subband_step2(Y, d2, oracle.coarse_index(wl.dms.size, wl.coarse_dms.size), wl.n_t)
+    assert np.array_equal(_to_np(out["D"]), Do)
+    s, pt, pv = oracle_rows.snr(Do, wl.widths)
+    _check_snr(_to_np(out["snr"]), _to_np(out["peak_t"]), _to_np(out["peak_val"]), s, pt, pv)
+    assert p.status() == 0
