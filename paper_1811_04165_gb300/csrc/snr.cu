@@ -406,45 +406,34 @@ detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
 }
 
 // ---------------------------------------------------------------------------
-// Vector form for width sets {1, 2, 4, ..., 2^(NW-1)} (the smoothing widths of
-// the search; AMBER's are powers of two as well).
+// Streaming vector form for width sets {1, 2, 4, ..., 2^(NW-1)} (the
+// smoothing widths of the search; AMBER's are powers of two as well).
 //
-// The row is staged and scanned into prefix sums as above (P[k] at buf[3 + k]),
-// here with 16-byte shared accesses.  Then the outputs are taken four at a
-// time: group j holds t = 4j - 3 .. 4j, whose P[t] are the aligned word
-// quadruple buf[4j .. 4j + 3].  With the widths known at compile time every
-// P[t + w] is a 16-byte load too: buf[4j + 4] serves w = 1, 2 and 4, and
-// buf[4j + w] (w a multiple of 4) the wider ones; consecutive lanes read
-// consecutive quadruples (no bank conflicts).  So a group costs NW - 1 shared
-// loads for 4 NW boxcars, each boxcar a subtract, a maximum (integer ALU) and
-// one 32 x 32 -> 64-bit multiply-add (FMA pipe).  Outputs outside [0, N_t - w]
-// contribute B = 0 (neither the sum of squares nor the maximum changes); only
-// the first and last groups need that test.  S1 comes in closed form as in
-// snr_kernel.
+// A persistent block owns rows blockIdx.x, blockIdx.x + gridDim.x, ... and
+// keeps two row buffers: while it scans and reduces one row, the next row's
+// bulk copy (TMA) is already in flight into the other buffer, so the row reads
+// stream from HBM under the arithmetic instead of stalling each block on its
+// row.  Each row is scanned in place into prefix sums (P[k] at buf[3 + k],
+// 16-byte shared accesses).  The outputs are then taken four at a time: group j
+// holds t = 4j - 3 .. 4j, whose P[t] are the aligned word quadruple
+// buf[4j .. 4j + 3]; with the widths known at compile time every P[t + w] is a
+// 16-byte load too (buf[4j + 4] serves w = 1, 2 and 4, buf[4j + w] the wider
+// ones), consecutive lanes reading consecutive quadruples.  A group costs
+// NW - 1 shared loads for 4 NW boxcars, each boxcar a subtract, a maximum
+// (integer ALU) and one 32 x 32 -> 64-bit multiply-add (FMA pipe).  Only the
+// first and last groups test validity (outputs outside [0, N_t - w] are
+// skipped).  S1 comes in closed form as in snr_kernel.
 //
 // Detection is folded in: `best` (int32[4]) is zeroed before the launch; each
-// block, once its outputs are written, counts itself in best[3]; the block
+// block, once all its rows are written, counts itself in best[3]; the block
 // that counts last reads the whole table (through L2) and writes the
 // detection over the counter.
 
-// Row i into buf[4 .. 4 + n_t), scanned in place into P[k] = buf[3 + k]
-// (k = 0 .. n_t); *seg = the sum of the samples this thread scanned.  Each
-// thread scans a run of `per` samples (a multiple of 4 with per / 4 odd, so the
-// 16-byte accesses of a warp are conflict-free).
-__device__ bool load_prefix_v4(const int32_t* row, int n_t, uint32_t* buf, uint32_t* scratch, uint64_t* bar,
-                               uint32_t* status, uint32_t* seg) {
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-    mbar_arrive_expect_tx(bar, (uint32_t)n_t * 4u);
-    bulk_g2s(buf + 4, row, (uint32_t)n_t * 4u, bar);
-  }
-  __syncthreads();
-  const bool ok = mbar_wait(bar, 0, status);
-  if (__syncthreads_or(ok ? 0 : 1)) {
-    if (threadIdx.x == 0) mbar_wait(bar, 0, status);
-    return false;
-  }
+// Scans the row at buf[4 .. 4 + n_t) in place into P[k] = buf[3 + k] (k = 0 ..
+// n_t); returns the sum of the samples this thread scanned.  Each thread scans
+// a run of `per` samples (a multiple of 4 with per / 4 odd, so the 16-byte
+// accesses of a warp are conflict-free).
+__device__ uint32_t scan_row_v4(uint32_t* buf, int n_t, uint32_t* scratch) {
   if (threadIdx.x == 0) buf[3] = 0u;
   int per = ((n_t + blockDim.x - 1) / blockDim.x + 3) / 4 * 4;
   if ((per / 4) % 2 == 0) per += 4;
@@ -456,7 +445,6 @@ __device__ bool load_prefix_v4(const int32_t* row, int n_t, uint32_t* buf, uint3
     s += v.x + v.y + v.z + v.w;
   }
   for (int t = ev; t < e; t++) s += buf[4 + t];
-  *seg = s;
   uint32_t run = block_exclusive_scan(s, scratch);
   for (int t = b; t < ev; t += 4) {
     uint4 v = *reinterpret_cast<const uint4*>(buf + 4 + t);
@@ -472,30 +460,24 @@ __device__ bool load_prefix_v4(const int32_t* row, int n_t, uint32_t* buf, uint3
     buf[4 + t] = run;
   }
   __syncthreads();
-  return true;
+  return s;
 }
 
 __device__ __forceinline__ uint32_t quad(const uint4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
+// Moments, maxima and first peak positions of one scanned row for widths 1, 2,
+// ..., 2^(NW-1), written to the row's S/N, peak_t and peak_val entries.
 template <int NW>
-__global__ void __launch_bounds__(kMaxThreads, 2) snr_vec4_kernel(SnrArgs a, int32_t* best) {
+__device__ void row_stats_v4(const SnrArgs& a, const uint32_t* buf, int row, uint32_t segsum) {
   constexpr int WMAX = 1 << (NW - 1);
-  extern __shared__ __align__(16) uint32_t buf[];
-  __shared__ uint32_t scratch[32];
-  __shared__ uint64_t bar;
   __shared__ unsigned long long ps1[kMaxThreads / 32][NW], ps2[kMaxThreads / 32][NW];
   __shared__ uint32_t pmx[kMaxThreads / 32][NW];
   __shared__ int gmax[NW], first[NW];
-  __shared__ int is_last;
-  const int row = blockIdx.x;
   const int n_t = a.n_t;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint32_t segsum = 0;
-  if (!load_prefix_v4(a.D + (int64_t)row * n_t, n_t, buf, scratch, &bar, a.status, &segsum)) return;
   const uint32_t* P = buf + 3;  // P[k], k = 0 .. n_t
-
   const int n_grp = (n_t + 3 + 3) / 4;  // groups of t = 4j - 3 .. 4j covering 0 .. n_t - 1
   uint32_t mx[NW];
   unsigned long long s2[NW];
@@ -504,27 +486,37 @@ __global__ void __launch_bounds__(kMaxThreads, 2) snr_vec4_kernel(SnrArgs a, int
   if (threadIdx.x < NW) first[threadIdx.x] = 0x7fffffff;
   for (int j = threadIdx.x; j < n_grp; j += blockDim.x) {
     const int t0 = 4 * j - 3;
-    const uint4 A = *reinterpret_cast<const uint4*>(buf + 4 * j);        // P[t0 .. t0 + 3]
-    const uint4 N = *reinterpret_cast<const uint4*>(buf + 4 * j + 4);    // P[t0 + 4 .. t0 + 7]
-    const bool full = t0 >= 0 && t0 + 3 + WMAX <= n_t;
+    if (t0 >= 0 && t0 + 3 + WMAX <= n_t) {
+      // every output of the group is valid for every width
+      const uint4 A = *reinterpret_cast<const uint4*>(buf + 4 * j);      // P[t0 .. t0 + 3]
+      const uint4 N = *reinterpret_cast<const uint4*>(buf + 4 * j + 4);  // P[t0 + 4 .. t0 + 7]
 #pragma unroll
-    for (int k = 0; k < NW; k++) {
-      constexpr int dummy = 0;
-      (void)dummy;
-      const int w = 1 << k;
-      uint4 Q;
-      if (w >= 8) Q = *reinterpret_cast<const uint4*>(buf + 4 * j + w);  // P[t0 + w .. t0 + w + 3]
+      for (int k = 0; k < NW; k++) {
+        const int w = 1 << k;
+        uint4 Q;
+        if (w >= 8) Q = *reinterpret_cast<const uint4*>(buf + 4 * j + w);  // P[t0 + w .. t0 + w + 3]
 #pragma unroll
-      for (int i = 0; i < 4; i++) {
-        // P[t0 + i + w]
-        const uint32_t hi = w >= 8 ? quad(Q, i) : (i + w < 4 ? quad(A, i + w) : quad(N, i + w - 4));
-        uint32_t B = hi - quad(A, i);
-        if (!full) {
-          const int t = t0 + i;
-          B = (t >= 0 && t + w <= n_t) ? B : 0u;
+        for (int i = 0; i < 4; i++) {
+          // P[t0 + i + w] - P[t0 + i]
+          const uint32_t hi = w >= 8 ? quad(Q, i) : (i + w < 4 ? quad(A, i + w) : quad(N, i + w - 4));
+          const uint32_t B = hi - quad(A, i);
+          s2[k] += (unsigned long long)B * B;
+          mx[k] = max(mx[k], B);
         }
-        s2[k] += (unsigned long long)B * B;
-        mx[k] = max(mx[k], B);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NW; k++) {
+        const int w = 1 << k;
+#pragma unroll 1
+        for (int i = 0; i < 4; i++) {
+          const int t = t0 + i;
+          if (t >= 0 && t + w <= n_t) {
+            const uint32_t B = P[t + w] - P[t];
+            s2[k] += (unsigned long long)B * B;
+            mx[k] = max(mx[k], B);
+          }
+        }
       }
     }
   }
@@ -593,9 +585,54 @@ __global__ void __launch_bounds__(kMaxThreads, 2) snr_vec4_kernel(SnrArgs a, int
     a.snr[o] = snr_from_moments(n_t - (1 << k) + 1, r);
     a.peak_t[o] = first[k];
     a.peak_val[o] = gmax[k];
-    if (best) __threadfence();
+  }
+}
+
+// `words`: 32-bit words of one row buffer (a multiple of 4).
+template <int NW>
+__global__ void __launch_bounds__(kMaxThreads, 2) snr_stream_kernel(SnrArgs a, int32_t* best, int words) {
+  extern __shared__ __align__(16) uint32_t sbuf[];
+  __shared__ uint32_t scratch[32];
+  __shared__ uint64_t bar[2];
+  __shared__ int is_last;
+  const int n_t = a.n_t;
+  const uint32_t bytes = (uint32_t)n_t * 4u;
+  const int stride = gridDim.x;
+  auto issue = [&](int b, int r) {  // one thread: the row's bulk copy into buffer b
+    mbar_arrive_expect_tx(&bar[b], bytes);
+    bulk_g2s(sbuf + b * words + 4, a.D + (int64_t)r * n_t, bytes, &bar[b]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    for (int b = 0; b < 2; b++)
+      if (blockIdx.x + b * stride < a.n_dms) issue(b, blockIdx.x + b * stride);
+  }
+  __syncthreads();
+  int k = 0;
+  for (int r = blockIdx.x; r < a.n_dms; r += stride, k++) {
+    const int cur = k & 1;
+    uint32_t* buf = sbuf + cur * words;
+    const bool ok = mbar_wait(&bar[cur], (k >> 1) & 1, a.status);
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      // this row's copy, and the next row's if one was issued, may still be in
+      // flight: one more bounded wait for each before the block leaves
+      if (threadIdx.x == 0) {
+        mbar_wait(&bar[cur], (k >> 1) & 1, nullptr);
+        if (r + stride < a.n_dms) mbar_wait(&bar[cur ^ 1], ((k + 1) >> 1) & 1, nullptr);
+      }
+      return;
+    }
+    const uint32_t segsum = scan_row_v4(buf, n_t, scratch);
+    row_stats_v4<NW>(a, buf, r, segsum);
+    // the buffer's generic-proxy reads and writes are done before the next bulk copy overwrites it
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0 && r + 2 * stride < a.n_dms) issue(cur, r + 2 * stride);
   }
   if (!best) return;
+  if (threadIdx.x < NW) __threadfence();  // this block's S/N entries before its count
   __syncthreads();
   if (threadIdx.x == 0) is_last = atomicAdd(reinterpret_cast<unsigned*>(best + 3), 1u) == gridDim.x - 1;
   __syncthreads();
@@ -644,48 +681,56 @@ SnrKernel snr_variant(int nwp) {
   }
 }
 
-typedef void (*Vec4Kernel)(SnrArgs, int32_t*);
+typedef void (*StreamKernel)(SnrArgs, int32_t*, int);
 
-Vec4Kernel vec4_variant(int nw) {
+StreamKernel stream_variant(int nw) {
   switch (nw) {
-    case 1: return snr_vec4_kernel<1>;
-    case 2: return snr_vec4_kernel<2>;
-    case 3: return snr_vec4_kernel<3>;
-    case 4: return snr_vec4_kernel<4>;
-    case 5: return snr_vec4_kernel<5>;
-    case 6: return snr_vec4_kernel<6>;
-    default: return snr_vec4_kernel<7>;
+    case 1: return snr_stream_kernel<1>;
+    case 2: return snr_stream_kernel<2>;
+    case 3: return snr_stream_kernel<3>;
+    case 4: return snr_stream_kernel<4>;
+    case 5: return snr_stream_kernel<5>;
+    case 6: return snr_stream_kernel<6>;
+    default: return snr_stream_kernel<7>;
   }
 }
 
-// The vector kernel serves sliding boxcars of widths 1, 2, ..., 2^(NW-1)
+// The streaming kernel serves sliding boxcars of widths 1, 2, ..., 2^(NW-1)
 // (NW <= 7) whose sums of squares fit 64 bits per row; it has no decimating
 // form.
-bool vec4_form(const SnrArgs& a) {
+bool stream_form(const SnrArgs& a) {
   if (a.decimate || a.pow2_widths < 1 || a.pow2_widths > 7 || !tma_ok(a.D, a.n_t)) return false;
   const long double bmax = (long double)std::max<int64_t>(1, a.max_boxcar);
   // the block total of S2 (at most N_t squares) is kept in 64 bits
   return (long double)a.n_t * bmax * bmax < 1.8e19L;
 }
 
-// Words of the row buffer: the groups' quadruples and the widest width's reach.
-size_t vec4_smem(int n_t, int nw) {
+// Words of one row buffer: the groups' quadruples and the widest width's reach.
+int stream_words(int n_t, int nw) {
   const int n_grp = (n_t + 6) / 4;
-  return ((size_t)4 * n_grp + 4 + (1 << (nw - 1)) + 4) * sizeof(uint32_t);
+  return 4 * n_grp + 4 + (1 << (nw - 1)) + 4;
 }
 
 sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st) {
   std::string why;
   if (!snr_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
-  if (vec4_form(a)) {
-    const size_t smem = vec4_smem(a.n_t, a.pow2_widths);
-    if (sps_status s = check_row_fits(a.n_t, smem - prefix_smem(a.n_t) + 8192)) return s;
-    Vec4Kernel fn = vec4_variant(a.pow2_widths);
-    SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (a.best) SPS_CUDA(cudaMemsetAsync(a.best, 0, 4 * sizeof(int32_t), st));
-    fn<<<a.n_dms, c.threads, smem, st>>>(a, a.best);
-    SPS_CUDA(cudaGetLastError());
-    return SPS_OK;
+  if (stream_form(a)) {
+    const int words = (stream_words(a.n_t, a.pow2_widths) + 3) / 4 * 4;
+    const size_t smem = 2 * (size_t)words * sizeof(uint32_t);
+    int dev = 0, max_smem = 0, sms = 0, per_sm = 0;
+    SPS_CUDA(cudaGetDevice(&dev));
+    SPS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    SPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (smem + 8192 <= (size_t)max_smem) {
+      StreamKernel fn = stream_variant(a.pow2_widths);
+      SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      SPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c.threads, smem));
+      const int grid = std::max(1, std::min(a.n_dms, std::max(1, per_sm) * sms));
+      if (a.best) SPS_CUDA(cudaMemsetAsync(a.best, 0, 4 * sizeof(int32_t), st));
+      fn<<<grid, c.threads, smem, st>>>(a, a.best, words);
+      SPS_CUDA(cudaGetLastError());
+      return SPS_OK;
+    }
   }
   if (sps_status s = check_row_fits(a.n_t, sizeof(Moments) * (kMaxThreads / 32) * kWidthsPerPass + 512)) return s;
   // largest boxcar value: 255 * channels * widest width (< 2^31, checked by the plan);
