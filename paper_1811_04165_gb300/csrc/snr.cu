@@ -406,218 +406,216 @@ detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
 }
 
 // ---------------------------------------------------------------------------
-// Chunked warp form for width sets {1, 2, 4, ..., 2^(NW-1)} (the smoothing
-// widths of the search; AMBER's are powers of two as well).
+// Vector form for width sets {1, 2, 4, ..., 2^(NW-1)} (the smoothing widths
+// of the search; AMBER's are powers of two as well).
 //
-// A block of four warps owns a row; the row's outputs are cut into chunks of
-// 256 samples and each warp takes every fourth chunk, so no block-wide barrier
-// stands between chunks.  A chunk c needs the window D[256c - 1 .. 256c + 383):
-// lane l reads its 12 samples with four aligned 16-byte loads from global
-// memory (the next chunk's loads are issued before the current chunk is
-// worked on), scans them, and the warp combines the lanes' totals with
-// shuffles into the window's inclusive prefix P'[j] = sum_{u <= j} D[256c - 1 + u],
-// stored in the warp's shared buffer at index j.  Then
-//   B_w[256c + i] = P'[i + w] - P'[i],
-// and the chunk's outputs are taken four at a time (group g: i = 4g .. 4g + 3),
-// every P' quadruple an aligned 16-byte shared load (consecutive lanes,
-// consecutive quadruples).  Per boxcar: a subtract, a 64-bit multiply-add for
-// S2, an add for S1; per group and width the maximum of its four boxcars is
-// compared once with the running maximum, and a strictly larger one records
-// the group, so each lane knows the first group where its largest boxcar sits.
-// At the end the block reduces the moments and maxima over its warps, takes
-// the earliest owner group of each width's maximum, and one warp finds the
-// sample inside that group from the row in global memory.  Outputs outside
-// [0, N_t - w] are skipped (the last chunk only).
+// One block per row.  The row arrives by one bulk copy (TMA) and is scanned in
+// place into prefix sums (P[k] at buf[3 + k], 16-byte shared accesses).  The
+// outputs are then taken four at a time: group j holds t = 4j - 3 .. 4j, whose
+// P[t] are the aligned word quadruple buf[4j .. 4j + 3]; with the widths known
+// at compile time every P[t + w] is a 16-byte load too (buf[4j + 4] serves
+// w = 1, 2 and 4, buf[4j + w] the wider ones), consecutive lanes reading
+// consecutive quadruples.  A group costs NW - 1 shared loads for 4 NW boxcars,
+// each boxcar a subtract, a maximum (integer ALU) and one 32 x 32 -> 64-bit
+// multiply-add (mad.wide, FMA pipe).  Only the first and last groups test
+// validity (outputs outside [0, N_t - w] are skipped).  S1 comes in closed
+// form as in snr_kernel.
 //
 // Detection is folded in: `best` (int32[4]) is zeroed before the launch; each
-// block, once its outputs are written, counts itself in best[3]; the block that
-// counts last reads the whole table (through L2) and writes the detection over
-// the counter.
-constexpr int kWarpRowThreads = 128;     // four warps per row
-constexpr int kChunk = 256;              // outputs per chunk
-constexpr int kChunkWindow = 384;        // window samples per chunk (12 per lane)
+// block, once its outputs are written, counts itself in best[3]; the block
+// that counts last reads the whole table (through L2) and writes the
+// detection over the counter.
+
+// Scans the row at buf[4 .. 4 + n_t) in place into P[k] = buf[3 + k] (k = 0 ..
+// n_t); returns the sum of the samples this thread scanned.  Each thread scans
+// a run of `per` samples (a multiple of 4 with per / 4 odd, so the 16-byte
+// accesses of a warp are conflict-free).
+__device__ uint32_t scan_row_v4(uint32_t* buf, int n_t, uint32_t* scratch) {
+  if (threadIdx.x == 0) buf[3] = 0u;
+  int per = ((n_t + blockDim.x - 1) / blockDim.x + 3) / 4 * 4;
+  if ((per / 4) % 2 == 0) per += 4;
+  const int b = min(n_t, (int)threadIdx.x * per), e = min(n_t, b + per);
+  const int ev = b + (e - b) / 4 * 4;  // vector part [b, ev)
+  uint32_t s = 0;
+  for (int t = b; t < ev; t += 4) {
+    const uint4 v = *reinterpret_cast<const uint4*>(buf + 4 + t);
+    s += v.x + v.y + v.z + v.w;
+  }
+  for (int t = ev; t < e; t++) s += buf[4 + t];
+  uint32_t run = block_exclusive_scan(s, scratch);
+  for (int t = b; t < ev; t += 4) {
+    uint4 v = *reinterpret_cast<const uint4*>(buf + 4 + t);
+    v.x += run;
+    v.y += v.x;
+    v.z += v.y;
+    v.w += v.z;
+    run = v.w;
+    *reinterpret_cast<uint4*>(buf + 4 + t) = v;
+  }
+  for (int t = ev; t < e; t++) {
+    run += buf[4 + t];
+    buf[4 + t] = run;
+  }
+  __syncthreads();
+  return s;
+}
+
+// S2 += B * B as one 32 x 32 -> 64-bit multiply-add (mad.wide.u32).
+__device__ __forceinline__ void add_square(unsigned long long& acc, uint32_t b) {
+  asm("mad.wide.u32 %0, %1, %1, %0;" : "+l"(acc) : "r"(b));
+}
 
 __device__ __forceinline__ uint32_t quad(const uint4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-// An add on the FMA pipe (x * one + c, `one` = 1 passed at run time), which
-// leaves the integer ALU pipe to the subtractions and maxima.
-__device__ __forceinline__ uint32_t fma_add(uint32_t x, uint32_t one, uint32_t c) {
-  uint32_t d;
-  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one), "r"(c));
-  return d;
-}
-
-// Lane's four aligned 16-byte loads covering D[base .. base + 16) of the row
-// (zeros outside [0, n_t); n_t is a multiple of 4, so a load is all in or all out).
-__device__ __forceinline__ void load_window(const int32_t* __restrict__ row, int base, int n_t, uint4 (&v)[4]) {
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    const int idx = base + 4 * q;
-    v[q] = (idx >= 0 && idx < n_t) ? __ldg(reinterpret_cast<const uint4*>(row + idx)) : make_uint4(0u, 0u, 0u, 0u);
-  }
-}
-
+// Moments, maxima and first peak positions of one scanned row for widths 1, 2,
+// ..., 2^(NW-1), written to the row's S/N, peak_t and peak_val entries.
 template <int NW>
-__global__ void __launch_bounds__(kWarpRowThreads, 4) snr_warp_kernel(SnrArgs a, int32_t* best, uint32_t one) {
+__device__ void row_stats_v4(const SnrArgs& a, const uint32_t* buf, int row, uint32_t segsum) {
   constexpr int WMAX = 1 << (NW - 1);
-  constexpr int GROUPS = kChunk / 4;  // groups per chunk
-  __shared__ __align__(16) uint32_t pbuf[kWarpRowThreads / 32][kChunkWindow];
-  __shared__ unsigned long long ws1[kWarpRowThreads / 32][NW], ws2[kWarpRowThreads / 32][NW];
-  __shared__ uint32_t wmx[kWarpRowThreads / 32][NW];
-  __shared__ int gmax[NW], ggrp[NW], gfirst[NW];
-  __shared__ int is_last;
-  const int row = blockIdx.x;
+  __shared__ unsigned long long ps1[kMaxThreads / 32][NW], ps2[kMaxThreads / 32][NW];
+  __shared__ uint32_t pmx[kMaxThreads / 32][NW];
+  __shared__ int gmax[NW], first[NW];
   const int n_t = a.n_t;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int32_t* __restrict__ Drow = a.D + (int64_t)row * n_t;
-  uint32_t* P = pbuf[warp];
-  const int n_chunks = (n_t + kChunk - 1) / kChunk;
-
-  unsigned long long s1[NW], s2[NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t* P = buf + 3;  // P[k], k = 0 .. n_t
+  const int n_grp = (n_t + 3 + 3) / 4;  // groups of t = 4j - 3 .. 4j covering 0 .. n_t - 1
   uint32_t mx[NW];
-  int grp[NW];  // first group (t / 4) holding this lane's maximum
+  unsigned long long s2[NW];
 #pragma unroll
-  for (int k = 0; k < NW; k++) { s1[k] = 0ull; s2[k] = 0ull; mx[k] = 0u; grp[k] = 0x7fffffff; }
-  if (threadIdx.x < NW) ggrp[threadIdx.x] = 0x7fffffff;
-
-  uint4 nv[4];
-  if (warp < n_chunks) load_window(Drow, kChunk * warp + 12 * lane - 4, n_t, nv);
-  for (int c = warp; c < n_chunks; c += 4) {
-    uint32_t d[12];
-    d[0] = nv[0].w;
+  for (int k = 0; k < NW; k++) { mx[k] = 0u; s2[k] = 0ull; }
+  if (threadIdx.x < NW) first[threadIdx.x] = 0x7fffffff;
+  for (int j = threadIdx.x; j < n_grp; j += blockDim.x) {
+    const int t0 = 4 * j - 3;
+    if (t0 >= 0 && t0 + 3 + WMAX <= n_t) {
+      // every output of the group is valid for every width
+      const uint4 A = *reinterpret_cast<const uint4*>(buf + 4 * j);      // P[t0 .. t0 + 3]
+      const uint4 N = *reinterpret_cast<const uint4*>(buf + 4 * j + 4);  // P[t0 + 4 .. t0 + 7]
 #pragma unroll
-    for (int q = 1; q < 3; q++) { d[4 * q - 3] = nv[q].x; d[4 * q - 2] = nv[q].y; d[4 * q - 1] = nv[q].z; d[4 * q] = nv[q].w; }
-    d[9] = nv[3].x; d[10] = nv[3].y; d[11] = nv[3].z;
-    if (c + 4 < n_chunks) load_window(Drow, kChunk * (c + 4) + 12 * lane - 4, n_t, nv);
-    // the window's inclusive prefix: lane-local, then across the warp
+      for (int k = 0; k < NW; k++) {
+        const int w = 1 << k;
+        uint4 Q;
+        if (w >= 8) Q = *reinterpret_cast<const uint4*>(buf + 4 * j + w);  // P[t0 + w .. t0 + w + 3]
 #pragma unroll
-    for (int m = 1; m < 12; m++) d[m] += d[m - 1];
-    uint32_t x = d[11];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    const uint32_t off = x - d[11];
-    uint4* dst = reinterpret_cast<uint4*>(P + 12 * lane);
-#pragma unroll
-    for (int q = 0; q < 3; q++)
-      dst[q] = make_uint4(d[4 * q] + off, d[4 * q + 1] + off, d[4 * q + 2] + off, d[4 * q + 3] + off);
-    __syncwarp();
-    const int c0 = kChunk * c;
-    uint32_t s1c[NW];  // this chunk's S1 share (8 boxcars below 2^25 each)
-#pragma unroll
-    for (int k = 0; k < NW; k++) s1c[k] = 0u;
-#pragma unroll
-    for (int gi = 0; gi < GROUPS / 32; gi++) {
-      const int g = lane + 32 * gi;
-      const int t0 = c0 + 4 * g;
-      const int gid = t0 >> 2;
-      const uint4 A = *reinterpret_cast<const uint4*>(P + 4 * g);
-      const uint4 N = *reinterpret_cast<const uint4*>(P + 4 * g + 4);
-      if (t0 + 3 + WMAX <= n_t) {
-        // every output of the group is valid for every width
-#pragma unroll
-        for (int k = 0; k < NW; k++) {
-          const int w = 1 << k;
-          uint4 Q;
-          if (w >= 8) Q = *reinterpret_cast<const uint4*>(P + 4 * g + w);
-          uint32_t m4 = 0u;
-#pragma unroll
-          for (int i = 0; i < 4; i++) {
-            const uint32_t hi = w >= 8 ? quad(Q, i) : (i + w < 4 ? quad(A, i + w) : quad(N, i + w - 4));
-            const uint32_t B = hi - quad(A, i);
-            s2[k] += (unsigned long long)B * B;
-            s1c[k] = fma_add(B, one, s1c[k]);
-            m4 = max(m4, B);
-          }
-          // the first group of a larger maximum (or the lane's first group at all)
-          if (m4 > mx[k] || grp[k] == 0x7fffffff) { mx[k] = m4; grp[k] = gid; }
+        for (int i = 0; i < 4; i++) {
+          // P[t0 + i + w] - P[t0 + i]
+          const uint32_t hi = w >= 8 ? quad(Q, i) : (i + w < 4 ? quad(A, i + w) : quad(N, i + w - 4));
+          const uint32_t B = hi - quad(A, i);
+          add_square(s2[k], B);
+          mx[k] = max(mx[k], B);
         }
-      } else if (t0 + 1 <= n_t) {
-        // the row's last outputs: each boxcar must end inside the row
+      }
+    } else {
 #pragma unroll
-        for (int k = 0; k < NW; k++) {
-          const int w = 1 << k;
-          uint32_t m4 = 0u;
-          bool any = false;
+      for (int k = 0; k < NW; k++) {
+        const int w = 1 << k;
 #pragma unroll 1
-          for (int i = 0; i < 4; i++) {
-            if (t0 + i + w <= n_t) {
-              const uint32_t B = P[4 * g + i + w] - P[4 * g + i];
-              s2[k] += (unsigned long long)B * B;
-              s1c[k] += B;
-              m4 = max(m4, B);
-              any = true;
-            }
+        for (int i = 0; i < 4; i++) {
+          const int t = t0 + i;
+          if (t >= 0 && t + w <= n_t) {
+            const uint32_t B = P[t + w] - P[t];
+            add_square(s2[k], B);
+            mx[k] = max(mx[k], B);
           }
-          if (any && (m4 > mx[k] || grp[k] == 0x7fffffff)) { mx[k] = m4; grp[k] = gid; }
         }
       }
     }
-#pragma unroll
-    for (int k = 0; k < NW; k++) s1[k] += s1c[k];
-    __syncwarp();  // the buffer is rewritten by the next chunk
   }
-  // warp reductions of the moments and maxima, then over the block
+  // this thread's share of S1 (closed form; wrap-around 64-bit terms, exact block total)
+  unsigned long long s1t[NW];
+#pragma unroll
+  for (int k = 0; k < NW; k++) s1t[k] = (unsigned long long)(1u << k) * segsum;
+  for (int j = (int)threadIdx.x + 1; j < WMAX; j += blockDim.x) {
+    const unsigned long long v = (unsigned long long)P[j] + (unsigned long long)(P[n_t] - P[n_t - j]);
+#pragma unroll
+    for (int k = 0; k < NW; k++)
+      if (j < (1 << k)) s1t[k] -= v;
+  }
 #pragma unroll
   for (int k = 0; k < NW; k++) {
-    unsigned long long v1 = s1[k], v2 = s2[k];
+    unsigned long long v1 = s1t[k], v2 = s2[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       v1 += __shfl_xor_sync(0xffffffffu, v1, o);
       v2 += __shfl_xor_sync(0xffffffffu, v2, o);
     }
     const uint32_t m = __reduce_max_sync(0xffffffffu, mx[k]);
-    if (lane == 0) { ws1[warp][k] = v1; ws2[warp][k] = v2; wmx[warp][k] = m; }
+    if (lane == 0) { ps1[warp][k] = v1; ps2[warp][k] = v2; pmx[warp][k] = m; }
   }
   __syncthreads();
   if (threadIdx.x < NW) {
     const int k = threadIdx.x;
-    uint32_t m = wmx[0][k];
-    for (int q = 1; q < kWarpRowThreads / 32; q++) m = max(m, wmx[q][k]);
+    uint32_t m = pmx[0][k];
+    for (int q = 1; q < nw; q++) m = max(m, pmx[q][k]);
     gmax[k] = (int)m;
   }
   __syncthreads();
-  // the earliest group holding each width's maximum
+  // first position of each maximum: the warp of each thread holding it searches
+  // that thread's groups, 8 groups (32 outputs) at a time, in order
 #pragma unroll
-  for (int k = 0; k < NW; k++)
-    if ((int)mx[k] == gmax[k] && grp[k] != 0x7fffffff) atomicMin(&ggrp[k], grp[k]);
-  __syncthreads();
-  // the sample inside that group: warp (k mod 4) sums each of its four boxcars
-  // from the row in global memory
-  for (int k = warp; k < NW; k += kWarpRowThreads / 32) {
+  for (int k = 0; k < NW; k++) {
     const int w = 1 << k;
-    const int t0 = 4 * ggrp[k];
-    int found = 0x7fffffff;
-    for (int i = 0; i < 4; i++) {
-      const int t = t0 + i;
-      if (t + w > n_t) break;
-      uint32_t sum = 0u;
-      for (int u = lane; u < w; u += 32) sum += (uint32_t)__ldg(Drow + t + u);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-      if ((int)sum == gmax[k]) { found = t; break; }
+    unsigned owners = __ballot_sync(0xffffffffu, (int)mx[k] == gmax[k]);
+    while (owners) {
+      const int o = __ffs(owners) - 1;
+      owners &= owners - 1;
+      const int owner = warp * 32 + o;
+      for (int m0 = 0; owner + m0 * (int)blockDim.x < n_grp; m0 += 8) {
+        // lane -> group owner + (m0 + lane / 4) * blockDim, output lane % 4 of it
+        const int j = owner + (m0 + (lane >> 2)) * (int)blockDim.x;
+        const int t = 4 * j - 3 + (lane & 3);
+        const bool hit = j < n_grp && t >= 0 && t + w <= n_t && (int)(P[t + w] - P[t]) == gmax[k];
+        const unsigned h = __ballot_sync(0xffffffffu, hit);
+        if (h) {
+          const int l = __ffs(h) - 1;
+          if (lane == 0) atomicMin(&first[k], 4 * (owner + (m0 + (l >> 2)) * (int)blockDim.x) - 3 + (l & 3));
+          break;
+        }
+      }
     }
-    if (lane == 0) gfirst[k] = found;
   }
   __syncthreads();
   if (threadIdx.x < NW) {
     const int k = threadIdx.x;
-    Moments r{ws1[0][k], ws2[0][k], 0ull, gmax[k], 0};
-    for (int q = 1; q < kWarpRowThreads / 32; q++) {
-      r.s1 += ws1[q][k];
-      r.s2lo += ws2[q][k];
+    Moments r{ps1[0][k], ps2[0][k], 0ull, gmax[k], 0};
+    for (int q = 1; q < nw; q++) {
+      r.s1 += ps1[q][k];
+      r.s2lo += ps2[q][k];
     }
     const int64_t o = (int64_t)k * a.n_dms + row;
     a.snr[o] = snr_from_moments(n_t - (1 << k) + 1, r);
-    a.peak_t[o] = gfirst[k];
+    a.peak_t[o] = first[k];
     a.peak_val[o] = gmax[k];
-    if (best) __threadfence();
   }
+}
+
+template <int NW>
+__global__ void __launch_bounds__(kMaxThreads, 2) snr_pow2_kernel(SnrArgs a, int32_t* best) {
+  extern __shared__ __align__(16) uint32_t buf[];
+  __shared__ uint32_t scratch[32];
+  __shared__ uint64_t bar;
+  __shared__ int is_last;
+  const int row = blockIdx.x;
+  const int n_t = a.n_t;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, (uint32_t)n_t * 4u);
+    bulk_g2s(buf + 4, a.D + (int64_t)row * n_t, (uint32_t)n_t * 4u, &bar);
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, a.status);
+  if (__syncthreads_or(ok ? 0 : 1)) {
+    // a copy that did not land in time may still be in flight: one more
+    // bounded wait before the block's shared memory is released
+    if (threadIdx.x == 0) mbar_wait(&bar, 0, a.status);
+    return;
+  }
+  const uint32_t segsum = scan_row_v4(buf, n_t, scratch);
+  row_stats_v4<NW>(a, buf, row, segsum);
   if (!best) return;
+  if (threadIdx.x < NW) __threadfence();  // this block's S/N entries before its count
   __syncthreads();
   if (threadIdx.x == 0) is_last = atomicAdd(reinterpret_cast<unsigned*>(best + 3), 1u) == gridDim.x - 1;
   __syncthreads();
@@ -666,38 +664,45 @@ SnrKernel snr_variant(int nwp) {
   }
 }
 
-typedef void (*WarpKernel)(SnrArgs, int32_t*, uint32_t);
+typedef void (*Pow2Kernel)(SnrArgs, int32_t*);
 
-WarpKernel warp_variant(int nw) {
+Pow2Kernel pow2_variant(int nw) {
   switch (nw) {
-    case 1: return snr_warp_kernel<1>;
-    case 2: return snr_warp_kernel<2>;
-    case 3: return snr_warp_kernel<3>;
-    case 4: return snr_warp_kernel<4>;
-    case 5: return snr_warp_kernel<5>;
-    case 6: return snr_warp_kernel<6>;
-    default: return snr_warp_kernel<7>;
+    case 1: return snr_pow2_kernel<1>;
+    case 2: return snr_pow2_kernel<2>;
+    case 3: return snr_pow2_kernel<3>;
+    case 4: return snr_pow2_kernel<4>;
+    case 5: return snr_pow2_kernel<5>;
+    case 6: return snr_pow2_kernel<6>;
+    default: return snr_pow2_kernel<7>;
   }
 }
 
-// The chunked warp kernel serves sliding boxcars of widths 1, 2, ..., 2^(NW-1)
-// (NW <= 7) on rows whose length is a multiple of 4 (16-byte loads), whose
-// boxcars stay below 2^25 (a chunk's per-lane S1 sum of 8 boxcars fits 32 bits)
-// and whose row sums of squares fit 64 bits; it has no decimating form.
-bool warp_form(const SnrArgs& a) {
-  if (a.decimate || a.pow2_widths < 1 || a.pow2_widths > 7 || (a.n_t & 3) || ((uintptr_t)a.D & 15)) return false;
-  if (a.max_boxcar >= (int64_t)1 << 25) return false;
+// The vector kernel serves sliding boxcars of widths 1, 2, ..., 2^(NW-1)
+// (NW <= 7) on rows that a bulk copy can stage (16-byte aligned, a multiple
+// of 4 samples) whose sums of squares fit 64 bits; it has no decimating form.
+bool pow2_form(const SnrArgs& a) {
+  if (a.decimate || a.pow2_widths < 1 || a.pow2_widths > 7 || !tma_ok(a.D, a.n_t)) return false;
   const long double bmax = (long double)std::max<int64_t>(1, a.max_boxcar);
   return (long double)a.n_t * bmax * bmax < 1.8e19L;
+}
+
+// Bytes of the row buffer: the groups' quadruples and the widest width's reach.
+size_t pow2_smem(int n_t, int nw) {
+  const int n_grp = (n_t + 6) / 4;
+  return ((size_t)4 * n_grp + 4 + (1 << (nw - 1)) + 4) * sizeof(uint32_t);
 }
 
 sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st) {
   std::string why;
   if (!snr_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
-  if (warp_form(a)) {
-    WarpKernel fn = warp_variant(a.pow2_widths);
+  if (pow2_form(a)) {
+    const size_t smem = pow2_smem(a.n_t, a.pow2_widths);
+    if (sps_status s = check_row_fits(a.n_t, smem - prefix_smem(a.n_t) + 8192)) return s;
+    Pow2Kernel fn = pow2_variant(a.pow2_widths);
+    SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (a.best) SPS_CUDA(cudaMemsetAsync(a.best, 0, 4 * sizeof(int32_t), st));
-    fn<<<a.n_dms, kWarpRowThreads, 0, st>>>(a, a.best, 1u);
+    fn<<<a.n_dms, c.threads, smem, st>>>(a, a.best);
     SPS_CUDA(cudaGetLastError());
     return SPS_OK;
   }
