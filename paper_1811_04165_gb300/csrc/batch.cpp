@@ -209,23 +209,25 @@ sps_status sps_batch_create(const sps_plan* const* plans, const sps_beam_buffers
         if (st == SPS_OK) cuda_ok(cudaEventRecord(pre_done[b], sk), "cudaEventRecord");
       }
     }
-    // phase 2: one batched pass per configuration, after its beams' pre-passes
+    // phase 2: one batched pass per group, after its beams' pre-passes; groups
+    // go to different branches so that one group's tail overlaps the next
     size_t gi = 0;
     for (auto it = groups.begin(); it != groups.end() && st == SPS_OK; ++it, ++gi) {
       const std::vector<int32_t>& beams = it->second;
+      cudaStream_t sg = streams[gi % B];
       const int32_t first = pass_of[beams[0]];
       const size_t w0 = work.size();
       int32_t max_data = 0;
       for (int32_t b : beams) {
-        cuda_ok(cudaStreamWaitEvent(cap, pre_done[b], 0), "cudaStreamWaitEvent");
+        cuda_ok(cudaStreamWaitEvent(sg, pre_done[b], 0), "cudaStreamWaitEvent");
         presum_pass_work(passes[pass_of[b]], plans[b]->cfg.brute, pass_of[b] - first, &work);
         max_data = std::max(max_data, passes[pass_of[b]].data_bytes);
       }
       if (st == SPS_OK)
         st = launch_presum_pass_list(batch->d_passes + first, batch->d_work + w0, (int64_t)(work.size() - w0),
-                                     plans[beams[0]]->cfg.brute, max_data, cap);
+                                     plans[beams[0]]->cfg.brute, max_data, sg);
       batch->list_launches++;
-      if (st == SPS_OK) cuda_ok(cudaEventRecord(group_done[gi], cap), "cudaEventRecord");
+      if (st == SPS_OK) cuda_ok(cudaEventRecord(group_done[gi], sg), "cudaEventRecord");
     }
     // phase 3: S/N of batched beams on their branches
     gi = 0;
