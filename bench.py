@@ -624,7 +624,8 @@ def main():
                 "peak_measured": int_peak_tadd, "frac_of_measured": achieved / int_peak_tadd,
                 "peak_measured_how": "sps_measure_int_add_rate: independent add chains on the ALU and FMA pipes",
                 "kernel_own_bound": {
-                    2: "shared-memory data path: the pass runs at 72 % of L1/shared throughput and executes a "
+                    2: "shared-memory data path: shared loads on 71 % of the pass's cycles (94 % of the quad "
+                       "layout's algorithmic wavefronts) plus 15.5 % stage fills by bulk copies; the pass executes a "
                        "quarter of the brute-force adds (ncu, " + summary + ")",
                     1: "shared-memory data path (pairs: half the brute-force adds; no committed ncu capture)",
                     0: "instruction issue: 82 % issue-active, 1.72 instructions per add (ncu, " + summary + ")"}[presum]}
