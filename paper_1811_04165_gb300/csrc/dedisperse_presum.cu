@@ -302,12 +302,8 @@ template <int ND, int NW>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 presum_pass_list_kernel(const PresumPassArgs* __restrict__ passes, const int4* __restrict__ work, int wd,
                         int cp_max) {
-  // the pass's arguments in shared memory: every thread reads them as broadcasts
-  __shared__ PresumPassArgs a;
   const int4 w = work[blockIdx.x];
-  for (int i = threadIdx.x; i < (int)(sizeof(PresumPassArgs) / 4); i += blockDim.x)
-    reinterpret_cast<uint32_t*>(&a)[i] = __ldg(reinterpret_cast<const uint32_t*>(passes + w.x) + i);
-  __syncthreads();
+  const PresumPassArgs& a = passes[w.x];
   presum_pass_block<ND, NW>(a, w.y, w.z, w.w, wd, cp_max, a.window_bytes);
 }
 

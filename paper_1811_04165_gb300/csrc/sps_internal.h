@@ -101,7 +101,6 @@ struct PresumUnit {
   int32_t c0, n, s_begin, s_end, max_rel, lo, hi, pad;
 };
 static_assert(sizeof(PresumSeries) == 32 && sizeof(PresumUnit) == 32, "read as two int4 by the pre-pass");
-static_assert(sizeof(PresumPassArgs) % 4 == 0, "copied word by word into shared memory by the batched pass");
 
 struct PresumTables {
   std::vector<PresumSeries> series;
