@@ -440,14 +440,17 @@ def events_ms(torch, fn, reps, warm=2):
 
 def leg_batched(torch, dev, reps=5):
     """The batched-beam workload: 40 beams (alternately 1536 and 384 channels,
-    512-4096 DM trials with steps 0.1-0.5, 1-7 widths) per 1.024 s batch, as one
-    graph launch (sps_batch_*) against plain per-beam sps_search launches on one
-    stream; every beam's batched outputs must equal its own search's."""
+    512-4096 DM trials with steps 0.1-0.5, 1-7 widths) per 1.024 s batch, on the
+    GA-tuned tiles stored per channel count, as one graph launch (sps_batch_*)
+    against plain per-beam sps_search launches on one stream; every beam's
+    batched outputs must equal its own search's."""
     import paper_1811_04165_gb300 as sps
     from paper_1811_04165_gb300 import synth
+    from paper_1811_04165_gb300 import batch_study
     wls = synth.batch_beams(40)
     t0 = time.perf_counter()
     plans = [sps.Plan.from_workload(wl) for wl in wls]
+    tuned = batch_study.apply_tuned(plans)
     plan_s = time.perf_counter() - t0
     xs = [device_noise(torch, (p.channels, p.pitch), 1000 + b, dev) for b, p in enumerate(plans)]
     ws = torch.empty(max(sps.batch_workspace_bytes([p], 1) for p in plans), dtype=torch.uint8, device=dev)
@@ -468,7 +471,8 @@ def leg_batched(torch, dev, reps=5):
            "value": samples / (t_batch * 1e-3), "unit": UNIT, "ms_per_batch": t_batch,
            "per_beam_ms_per_batch": t_beam, "speedup_vs_per_beam": t_beam / t_batch,
            "real_time_beams": len(wls) * 1024.0 / t_batch, "exact_vs_per_beam": exact,
-           "shared_pass_launches": batch.list_launches, "kernel_configs": "library defaults",
+           "shared_pass_launches": batch.list_launches,
+           "kernel_configs": f"GA-tuned per channel count (stored), taken by {tuned} of {len(plans)} beams",
            "plan_s": plan_s, "inputs": "device-drawn noise (timing and exactness do not depend on values)"}
     del batch
     torch.cuda.empty_cache()

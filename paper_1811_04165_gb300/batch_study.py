@@ -14,6 +14,7 @@ outputs are checked equal to its own search.
 """
 import argparse
 import json
+import os
 import sys
 import time
 
@@ -44,6 +45,34 @@ def _time(fn, n, warm=2):
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / n
+
+
+# GA-tuned configurations per channel count for the batched-beam mix, written
+# by `--save-tuned` on a GB300 (applied where a beam's tables fit them).
+TUNED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned", "gb300_batch_beams_configs.json")
+
+
+def apply_tuned(plans, path=TUNED):
+    """Put each plan on the stored tuned configuration of its channel count
+    where that configuration fits it; returns how many plans took one."""
+    from . import DedispConfig, KernelConfig, SnrConfig
+    with open(path) as f:
+        cfgs = json.load(f)["configs"]
+    n = 0
+    for p in plans:
+        c = cfgs.get(str(p.channels))
+        if c is None:
+            continue
+        k = KernelConfig()
+        for name in ("brute", "step1", "step2"):
+            setattr(k, name, DedispConfig(*c[name]))
+        k.snr = SnrConfig(*c["snr"])
+        try:
+            p.config = k
+            n += 1
+        except SpsError:
+            pass
+    return n
 
 
 def tune_shapes(plans, wls, xs, evals, ws_limit):
@@ -82,6 +111,8 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--batch-ws-gb", type=float, default=48.0, help="largest batch workspace to allocate")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--save-tuned", default=None, metavar="FILE",
+                    help="write the tuned configuration per channel count (JSON) for later batches")
     a = ap.parse_args(argv)
     wls = synth.batch_beams(a.beams)
     t0 = time.perf_counter()
@@ -93,6 +124,13 @@ def main(argv=None):
     ws_limit = int(a.ws_limit_gb * 2 ** 30)
     if a.tune_evals:
         res["tuning"] = tune_shapes(plans, wls, xs, a.tune_evals, ws_limit)
+        if a.save_tuned:
+            import torch
+            with open(a.save_tuned, "w") as f:
+                json.dump({"how": "python -m paper_1811_04165_gb300.batch_study (live GA, full space, "
+                                  f"{a.tune_evals} evaluations per channel count)",
+                           "gpu": torch.cuda.get_device_name(), "workload": "batched beams (synth.batch_beams)",
+                           "configs": {ch: r["config"] for ch, r in res["tuning"].items()}}, f, indent=1)
     # plain per-beam launches on one stream, one workspace sized for the largest beam
     res["workspace_gb_per_beam_max"] = max(batch_workspace_bytes([p], 1) for p in plans) / 2 ** 30
     ws = torch.empty(max(batch_workspace_bytes([p], 1) for p in plans), dtype=torch.uint8, device="cuda")
