@@ -460,9 +460,19 @@ __device__ uint32_t scan_row_v4(uint32_t* buf, int n_t, uint32_t* scratch) {
   return s;
 }
 
-// S2 += B * B as one 32 x 32 -> 64-bit multiply-add (mad.wide.u32).
+// S2 += B * B, a 32 x 32 -> 64-bit product added to a 64-bit sum (written in
+// C++: measured slightly faster on sm_103a than the explicit mad.wide.u32).
 __device__ __forceinline__ void add_square(unsigned long long& acc, uint32_t b) {
-  asm("mad.wide.u32 %0, %1, %1, %0;" : "+l"(acc) : "r"(b));
+  acc += (unsigned long long)b * b;
+}
+
+// Sum over the warp of a 64-bit value below 2^64 (every lane gets it), by three
+// 22/22/20-bit limbs whose warp sums fit 32 bits (redux.sync).
+__device__ __forceinline__ unsigned long long warp_sum64_redux(unsigned long long v) {
+  const uint32_t r0 = __reduce_add_sync(0xffffffffu, (uint32_t)v & 0x3FFFFFu);
+  const uint32_t r1 = __reduce_add_sync(0xffffffffu, (uint32_t)(v >> 22) & 0x3FFFFFu);
+  const uint32_t r2 = __reduce_add_sync(0xffffffffu, (uint32_t)(v >> 44));
+  return (unsigned long long)r0 + ((unsigned long long)r1 << 22) + ((unsigned long long)r2 << 44);
 }
 
 __device__ __forceinline__ uint32_t quad(const uint4& v, int i) {
@@ -474,7 +484,7 @@ __device__ __forceinline__ uint32_t quad(const uint4& v, int i) {
 template <int NW>
 __device__ void row_stats_v4(const SnrArgs& a, const uint32_t* buf, int row, uint32_t segsum) {
   constexpr int WMAX = 1 << (NW - 1);
-  __shared__ unsigned long long ps1[kMaxThreads / 32][NW], ps2[kMaxThreads / 32][NW];
+  __shared__ unsigned long long ps2[kMaxThreads / 32][NW], ptot[kMaxThreads / 32], s1v[NW];
   __shared__ uint32_t pmx[kMaxThreads / 32][NW];
   __shared__ int gmax[NW], first[NW];
   const int n_t = a.n_t;
@@ -522,26 +532,16 @@ __device__ void row_stats_v4(const SnrArgs& a, const uint32_t* buf, int row, uin
       }
     }
   }
-  // this thread's share of S1 (closed form; wrap-around 64-bit terms, exact block total)
-  unsigned long long s1t[NW];
-#pragma unroll
-  for (int k = 0; k < NW; k++) s1t[k] = (unsigned long long)(1u << k) * segsum;
-  for (int j = (int)threadIdx.x + 1; j < WMAX; j += blockDim.x) {
-    const unsigned long long v = (unsigned long long)P[j] + (unsigned long long)(P[n_t] - P[n_t - j]);
-#pragma unroll
-    for (int k = 0; k < NW; k++)
-      if (j < (1 << k)) s1t[k] -= v;
-  }
+  // warp sums: S2 per width, the maximum, and the row total (for S1)
 #pragma unroll
   for (int k = 0; k < NW; k++) {
-    unsigned long long v1 = s1t[k], v2 = s2[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-      v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-    }
+    const unsigned long long v2 = warp_sum64_redux(s2[k]);
     const uint32_t m = __reduce_max_sync(0xffffffffu, mx[k]);
-    if (lane == 0) { ps1[warp][k] = v1; ps2[warp][k] = v2; pmx[warp][k] = m; }
+    if (lane == 0) { ps2[warp][k] = v2; pmx[warp][k] = m; }
+  }
+  {
+    const unsigned long long t = warp_sum64_redux(segsum);
+    if (lane == 0) ptot[warp] = t;
   }
   __syncthreads();
   if (threadIdx.x < NW) {
@@ -551,6 +551,21 @@ __device__ void row_stats_v4(const SnrArgs& a, const uint32_t* buf, int row, uin
     gmax[k] = (int)m;
   }
   __syncthreads();
+  if (warp == nw - 1) {
+    // S1 = w T - sum_{j<w} P[j] - sum_{j<w} (T - P[N_t - j]): every sample lies
+    // in w boxcars except within w - 1 of either end (end terms below 2^31 each)
+    unsigned long long T = 0ull;
+    for (int q = 0; q < nw; q++) T += ptot[q];
+#pragma unroll
+    for (int k = 0; k < NW; k++) {
+      unsigned long long e = 0ull;
+      for (int j = lane + 1; j < (1 << k); j += 32)
+        e += (unsigned long long)P[j] + (unsigned long long)(P[n_t] - P[n_t - j]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+      if (lane == 0) s1v[k] = (unsigned long long)(1u << k) * T - e;
+    }
+  }
   // first position of each maximum: the warp of each thread holding it searches
   // that thread's groups, 8 groups (32 outputs) at a time, in order
 #pragma unroll
@@ -578,11 +593,8 @@ __device__ void row_stats_v4(const SnrArgs& a, const uint32_t* buf, int row, uin
   __syncthreads();
   if (threadIdx.x < NW) {
     const int k = threadIdx.x;
-    Moments r{ps1[0][k], ps2[0][k], 0ull, gmax[k], 0};
-    for (int q = 1; q < nw; q++) {
-      r.s1 += ps1[q][k];
-      r.s2lo += ps2[q][k];
-    }
+    Moments r{s1v[k], ps2[0][k], 0ull, gmax[k], 0};
+    for (int q = 1; q < nw; q++) r.s2lo += ps2[q][k];
     const int64_t o = (int64_t)k * a.n_dms + row;
     a.snr[o] = snr_from_moments(n_t - (1 << k) + 1, r);
     a.peak_t[o] = first[k];
