@@ -72,6 +72,22 @@ def dist_init(n):
     return rank, world
 
 
+def local_device_index() -> int:
+    """The GPU this rank drives: torchrun's LOCAL_RANK (one process per GPU)."""
+    return int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def rank_beam(rank: int, dms: int = 2048):
+    """The beam rank `rank` searches: replicas search independent beams (seed
+    2 + rank), so no data moves between ranks."""
+    from paper_1811_04165_gb300 import synth
+    wl = synth.apertif_beam(seed=2 + rank)
+    if dms != 2048:
+        wl.dms = wl.dms[:dms].copy()
+        wl.name += f"-first{dms}dm"
+    return wl
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -568,13 +584,10 @@ def main():
     import paper_1811_04165_gb300 as sps
     from paper_1811_04165_gb300 import synth
 
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    local = local_device_index()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = synth.apertif_beam(seed=2 + rank)
-    if args.dms != 2048:
-        wl.dms = wl.dms[:args.dms].copy()
-        wl.name += f"-first{args.dms}dm"
+    wl = rank_beam(rank, args.dms)
     plan = sps.Plan.from_workload(wl, mode=sps.MODE_BRUTE)
     if args.presum is not None:
         c = plan.config
