@@ -463,9 +463,12 @@ sps_status sps_server_destroy(sps_server* server);
 
 /* ---------------------------------------------------------------- misc */
 
-/* Reads (synchronously) the plan's device status word, which kernels set when
- * a bounded wait for an asynchronous copy runs out; clears it if `clear`.
- * Returns TIMEOUT when it is non-zero. */
+/* Reads (synchronously) the plan's device status word; clears it if `clear`.
+ * Bit 0 (1): a kernel's bounded wait for an asynchronous copy ran out.
+ * Bit 1 (2): only in the bounds-checked build of the library (compiled with
+ * SPS_BOUNDS_CHECK=1): a de-dispersion pass would have read outside a
+ * shared-memory stage; the read was not made.
+ * Returns TIMEOUT when the word is non-zero. */
 sps_status sps_plan_status(const sps_plan* plan, uint32_t* host_status, int32_t clear);
 
 /* Failure-detection self-check (the paper has no counterpart): launches on

@@ -29,6 +29,9 @@ from ._lib import SpsError, check, lib, lib_path  # noqa: F401
 MODE_BRUTE = 0
 MODE_SUBBAND = 1
 SPS_OK, SPS_ERR_INVALID_ARG, SPS_ERR_UNSUPPORTED, SPS_ERR_CUDA, SPS_ERR_OOM, SPS_ERR_TIMEOUT = 0, 1, 2, 3, 4, 5
+# bits of the plan's device status word (Plan.status)
+STATUS_WAIT_TIMEOUT = 1   # a kernel's bounded wait ran out
+STATUS_BOUNDS = 2         # bounds-checked build: a staged read would have left its stage
 SMOOTH_SLIDING = 0
 SMOOTH_DECIMATE = 1
 
@@ -326,7 +329,9 @@ class Plan:
         return ws
 
     def status(self, clear: bool = True) -> int:
-        """Device status word (non-zero when a kernel's bounded wait ran out); synchronises."""
+        """Device status word: STATUS_WAIT_TIMEOUT when a kernel's bounded wait ran
+        out, STATUS_BOUNDS (bounds-checked build only) when a staged read would
+        have left its stage; synchronises."""
         v = ctypes.c_uint32()
         _L.sps_plan_status(self.handle, ctypes.byref(v), int(clear))
         return int(v.value)

@@ -8,7 +8,9 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-_PATH = os.path.join(_PKG, "libsps.so")
+# SPS_BUILD=checked loads the bounds-checked build (libsps_checked.so, built by
+# `python -m paper_1811_04165_gb300.build --checked`); the default is libsps.so.
+_PATH = os.path.join(_PKG, "libsps_checked.so" if os.environ.get("SPS_BUILD") == "checked" else "libsps.so")
 _lib = None
 
 # every exported entry point with (restype, argtypes)

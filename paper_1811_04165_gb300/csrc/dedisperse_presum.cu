@@ -91,6 +91,10 @@ __device__ __forceinline__ void presum_pass_block(const PresumPassArgs& a, int t
   const uint32_t toff = (uint32_t)(t_sub * 128 * NW + lane * 4);  // bytes
   const int64_t chunk_row = ((int64_t)tile * a.n_groups + g) * n_chunks;
   const bool clip = t0 + wb / 2 + a.max_start > a.q_pitch;  // windows may be cut at the row end
+  // bounds-checked build: the largest staged offset whose NW words fit the
+  // stage's windows, and the warp's trials inside a row of the offset table
+  const int64_t lim = (int64_t)a.data_bytes - (int64_t)(toff + 128 * (NW - 1) + 4);
+  if (kBoundsCheck && (dm_sub + 1) * ND > a.di_pad) stage_read_ok(1u, -1, a.status);
 
   if (tid == 0) {
     aborted = 0;
@@ -214,9 +218,9 @@ __device__ __forceinline__ void presum_pass_block(const PresumPassArgs& a, int t
         load_offs<ND>(tb + (p + 1) * a.di_pad, e1);
 #pragma unroll
         for (int r = 0; r < ND; r++) {
-          uint32_t A[NW], B[NW];
-          lds_row<NW>(base + e0[r], A);
-          lds_row<NW>(base + e1[r], B);
+          uint32_t A[NW] = {}, B[NW] = {};
+          if (stage_read_ok(e0[r], lim, a.status)) lds_row<NW>(base + e0[r], A);
+          if (stage_read_ok(e1[r], lim, a.status)) lds_row<NW>(base + e1[r], B);
 #pragma unroll
           for (int m = 0; m < NW; m++) lanes[r][m] += A[m] + B[m];
         }
@@ -226,8 +230,8 @@ __device__ __forceinline__ void presum_pass_block(const PresumPassArgs& a, int t
         load_offs<ND>(tb + p * a.di_pad, e0);
 #pragma unroll
         for (int r = 0; r < ND; r++) {
-          uint32_t A[NW];
-          lds_row<NW>(base + e0[r], A);
+          uint32_t A[NW] = {};
+          if (stage_read_ok(e0[r], lim, a.status)) lds_row<NW>(base + e0[r], A);
 #pragma unroll
           for (int m = 0; m < NW; m++) lanes[r][m] += A[m];
         }

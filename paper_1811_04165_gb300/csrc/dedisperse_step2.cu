@@ -46,6 +46,9 @@ step2_kernel(Step2Args a, int wd, int cs_max, int wb) {
   const int k = a.tiles[3 * blockIdx.y], ib = a.tiles[3 * blockIdx.y + 1], nd = a.tiles[3 * blockIdx.y + 2];
   const int n_chunks = (S + cs_max - 1) / cs_max;
   const uint32_t toff = (uint32_t)(t_sub * 128 * NW + lane * 4);  // bytes
+  // bounds-checked build: the largest staged offset whose NW words fit the
+  // stage's two copies
+  const int64_t lim = (int64_t)stage_bytes - (int64_t)(toff + 128 * (NW - 1) + 4);
   const int32_t* d2row0 = a.d2 + (int64_t)ib * S;
   const uint16_t* ybase = a.y + (int64_t)k * S * a.y_pitch;
 
@@ -136,7 +139,9 @@ step2_kernel(Step2Args a, int wd, int cs_max, int wb) {
     for (int sl = 0; sl < cs; sl++) {
 #pragma unroll
       for (int r = 0; r < ND; r++) {
-        const uint8_t* p = stage + trow[r * S + sl] + toff;
+        const uint32_t off = trow[r * S + sl];
+        if (!stage_read_ok(off, lim, a.status)) continue;
+        const uint8_t* p = stage + off + toff;
 #pragma unroll
         for (int m = 0; m < NW; m++) lanes[r][m] += *reinterpret_cast<const uint32_t*>(p + 128 * m);
       }

@@ -83,6 +83,10 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
   const int n_chunks = (G + cc_max - 1) / cc_max;
   const int pairs = (G + 1) >> 1;
   const uint32_t toff = (uint32_t)(t_sub * 128 * NW + lane * 4);
+  // bounds-checked build: the largest staged offset whose NW words fit the four
+  // copies of the stage, and the warp's trials inside a row of the offset table
+  const int64_t lim = (int64_t)4 * copy_stride - (int64_t)(toff + 128 * (NW - 1) + 4);
+  if (kBoundsCheck && (dm_sub + 1) * ND > a.di_pad) stage_read_ok(1u, -1, a.status);
   const uint32_t one = a.one;
 
   for (int c = tid; c < G; c += blockDim.x) b0s[c] = a.b0[(int64_t)tile * a.channels + c_lo + c];
@@ -173,9 +177,9 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
 #pragma unroll
         for (int r = 0; r < ND; r++) {
           const uint2 o = e[r];
-          uint32_t W1[NW], W2[NW];
-          lds_row<NW>(base + o.x, W1);
-          lds_row<NW>(base + o.y, W2);
+          uint32_t W1[NW] = {}, W2[NW] = {};
+          if (stage_read_ok(o.x, lim, a.status)) lds_row<NW>(base + o.x, W1);
+          if (stage_read_ok(o.y, lim, a.status)) lds_row<NW>(base + o.y, W2);
 #pragma unroll
           for (int m = 0; m < NW; m++) {
             lo[r][m] = madd(W2[m] & kEvenBytes, one, madd(W1[m] & kEvenBytes, one, lo[r][m]));
@@ -187,8 +191,8 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
         const uint2* e = tb + (cl >> 1) * a.di_pad;
 #pragma unroll
         for (int r = 0; r < ND; r++) {
-          uint32_t W1[NW];
-          lds_row<NW>(base + e[r].x, W1);
+          uint32_t W1[NW] = {};
+          if (stage_read_ok(e[r].x, lim, a.status)) lds_row<NW>(base + e[r].x, W1);
 #pragma unroll
           for (int m = 0; m < NW; m++) {
             lo[r][m] = madd(W1[m] & kEvenBytes, one, lo[r][m]);

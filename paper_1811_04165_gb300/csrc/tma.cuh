@@ -8,7 +8,25 @@
 namespace sps {
 
 // Status bits written by kernels into the plan's device status word.
-enum : uint32_t { kStatusWaitTimeout = 1u };
+enum : uint32_t { kStatusWaitTimeout = 1u, kStatusBounds = 2u };
+
+// Bounds-checked build (compiled with -DSPS_BOUNDS_CHECK=1): the de-dispersion
+// passes test every staged shared-memory read against the extent of its stage;
+// a read that would leave the stage is not made (zeros are added instead) and
+// sets kStatusBounds in the status word.  Off in the normal build.
+#ifndef SPS_BOUNDS_CHECK
+#define SPS_BOUNDS_CHECK 0
+#endif
+constexpr bool kBoundsCheck = SPS_BOUNDS_CHECK != 0;
+
+// In the bounds-checked build: true when a read of a staged row at byte offset
+// `off` stays within `limit` (the largest offset whose whole row fits the
+// stage); otherwise records the violation and returns false.
+__device__ __forceinline__ bool stage_read_ok(uint32_t off, int64_t limit, uint32_t* status) {
+  if (!kBoundsCheck || (int64_t)off <= limit) return true;
+  if (status) atomicOr(status, kStatusBounds);
+  return false;
+}
 
 // About 2^22 polls of try_wait (each may suspend briefly): seconds, far longer
 // than any copy this library issues takes.
