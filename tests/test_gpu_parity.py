@@ -632,3 +632,43 @@ def test_apertif_subband_counts_full_tables(lib, S):
     s, pt, pv = oracle_rows.snr(Do, wl.widths)
     _check_snr(_to_np(out["snr"]), _to_np(out["peak_t"]), _to_np(out["peak_val"]), s, pt, pv)
     assert p.status() == 0
+
+
+@pytest.mark.parametrize("presum", [0, 2])
+def test_one_plan_on_concurrent_streams(lib, presum):
+    """A plan is read-only once configured, so one plan serves searches on several
+    streams at once (each with its own workspace and outputs), as the benchmark's
+    pipelined run does: four streams, three rounds of interleaved searches on
+    different inputs, every result against the oracle."""
+    torch = _torch()
+    C, n_t, n_dms = 256, 3000, 96
+    dms = synth.dm_grid(n_dms, 0.5)
+    p = lib.Plan(C, 1250.0, 1550.0, 81.92e-6, n_t, dms, [1, 2, 4, 8, 16])
+    c = p.config
+    c.brute.presum = presum
+    p.config = c
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    xs, wss, outs = [], [], []
+    for k in range(4):
+        x = synth.filterbank(C, 1250.0, 1550.0, 81.92e-6, p.input_samples, 300 + k,
+                             [synth.Pulse(float(dms[20 + 15 * k]), 2.0 + k, 25.0, 500.0 + 400 * k)], pitch=p.pitch)
+        xs.append(x)
+        wss.append(torch.empty(p.workspace_bytes, dtype=torch.uint8, device="cuda"))
+        outs.append(p.alloc_outputs())
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    torch.cuda.synchronize()
+    for _ in range(3):
+        for k, s in enumerate(streams):
+            o = outs[k]
+            lib.sps_search(p, xd[k], o["D"], o["snr"], o["peak_t"], o["peak_val"], o["best"], workspace=wss[k],
+                           stream=s)
+    torch.cuda.synchronize()
+    delays = oracle.delay_table(1250.0, 1550.0, C, 81.92e-6, dms)
+    for k in range(4):
+        Do = oracle.dedisperse(xs[k], delays, n_t)
+        assert np.array_equal(_to_np(outs[k]["D"]), Do), k
+        s, pt, pv = oracle.snr(Do, [1, 2, 4, 8, 16])
+        _check_snr(_to_np(outs[k]["snr"]), _to_np(outs[k]["peak_t"]), _to_np(outs[k]["peak_val"]), s, pt, pv)
+        bi, bw = oracle.detect(s)
+        assert _to_np(outs[k]["best"]).tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])]
+    assert p.status() == 0
