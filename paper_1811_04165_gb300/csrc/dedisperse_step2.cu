@@ -88,12 +88,15 @@ step2_kernel(Step2Args a, int wd, int cs_max, int wb) {
 #pragma unroll
     for (int m = 0; m < NW; m++) { lanes[r][m] = 0u; acc[r][m][0] = 0; acc[r][m][1] = 0; }
 
+  // acc[.][.][0] sums whole lane words (low lanes + 2^16 high lanes, mod 2^32),
+  // acc[.][.][1] the high lanes; the low sums are recovered at the end as
+  // acc0 - 2^16 acc1 (exact: they stay far below 2^32)
   auto fold = [&]() {
 #pragma unroll
     for (int r = 0; r < ND; r++)
 #pragma unroll
       for (int m = 0; m < NW; m++) {
-        acc[r][m][0] += (int32_t)(lanes[r][m] & 0xFFFFu);
+        acc[r][m][0] += (int32_t)lanes[r][m];
         acc[r][m][1] += (int32_t)(lanes[r][m] >> 16);
         lanes[r][m] = 0u;
       }
@@ -149,6 +152,10 @@ step2_kernel(Step2Args a, int wd, int cs_max, int wb) {
     }
   }
   fold();
+#pragma unroll
+  for (int r = 0; r < ND; r++)
+#pragma unroll
+    for (int m = 0; m < NW; m++) acc[r][m][0] = (int32_t)((uint32_t)acc[r][m][0] - ((uint32_t)acc[r][m][1] << 16));
 
   const bool vec = (a.n_t & 1) == 0;
 #pragma unroll

@@ -150,9 +150,11 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
     for (int r = 0; r < ND; r++)
 #pragma unroll
       for (int m = 0; m < NW; m++) {
-        acc[r][m][0] += (int32_t)(lo[r][m] & 0xFFFFu);
+        // whole lane words (low + 2^16 high, mod 2^32) and the high lanes; the
+        // low sums are recovered after the last fold as word sum - 2^16 high sum
+        acc[r][m][0] += (int32_t)lo[r][m];
         acc[r][m][2] += (int32_t)(lo[r][m] >> 16);
-        acc[r][m][1] += (int32_t)(hi[r][m] & 0xFFFFu);
+        acc[r][m][1] += (int32_t)hi[r][m];
         acc[r][m][3] += (int32_t)(hi[r][m] >> 16);
         lo[r][m] = 0u; hi[r][m] = 0u;
       }
@@ -213,6 +215,13 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
     return;
   }
   fold();
+#pragma unroll
+  for (int r = 0; r < ND; r++)
+#pragma unroll
+    for (int m = 0; m < NW; m++) {
+      acc[r][m][0] = (int32_t)((uint32_t)acc[r][m][0] - ((uint32_t)acc[r][m][2] << 16));
+      acc[r][m][1] = (int32_t)((uint32_t)acc[r][m][1] - ((uint32_t)acc[r][m][3] << 16));
+    }
 
   // Each lane holds 4 consecutive samples per (trial, word).
   const bool vec = (a.out_pitch & 3) == 0;
