@@ -18,6 +18,8 @@
 // Nothing is materialised; the integrate kernel writes B for checking.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "sps_internal.h"
 #include "tma.cuh"
 
@@ -340,41 +342,39 @@ __device__ __forceinline__ bool better(double v, int i, int w, double bv, int bi
   return w < bw;
 }
 
-// The detection over the whole S/N table by one block (any multiple of 32
-// threads); `ld` reads through L2 when other blocks of the same launch wrote
-// the table.
-template <bool L2>
-__device__ void detect_block(const double* snr, const int32_t* peak_t, const int32_t* peak_val, int n_dms,
-                             int n_widths, int32_t* best) {
+// The detection over the whole S/N table by one cluster of kDetectBlocks
+// blocks: every thread takes entries e = w n_dms + i at a stride of the
+// cluster's thread count (a couple each for a beam), the blocks reduce their
+// threads, and block 0 reduces the blocks' results through distributed shared
+// memory and writes best = {i, w, peak_t, peak_val}.  Launched after the S/N
+// kernel on the same stream, so the table is complete and visible; no fence,
+// counter or zeroed buffer is involved.
+constexpr int kDetectBlocks = 8;
+constexpr int kDetectThreads = 1024;
+
+__global__ void __cluster_dims__(kDetectBlocks, 1, 1) __launch_bounds__(kDetectThreads, 1)
+detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val, int n_dms, int n_widths,
+              int32_t* best) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
   __shared__ double sv[32];
   __shared__ int si[32], sw[32];
+  __shared__ double cv[kDetectBlocks];  // block 0: the blocks' results
+  __shared__ int ci[kDetectBlocks], cw[kDetectBlocks];
+  const int rank = (int)cluster.block_rank();
+  const int64_t total = (int64_t)n_widths * n_dms;
   double bv = -1.0;
   int bi = 0x7fffffff, bw = 0x7fffffff;
-  // every (width, DM) entry once; the tie rules make the visiting order
-  // irrelevant.  Eight loads are issued before any is compared, so that one
-  // thread has eight table reads in flight.
-  constexpr int kBatch = 8;
-  for (int w = 0; w < n_widths; w++) {
-    const double* row = snr + (int64_t)w * n_dms;
-    for (int i0 = threadIdx.x; i0 < n_dms; i0 += kBatch * blockDim.x) {
-      double v[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; u++) {
-        const int i = i0 + u * blockDim.x;
-        v[u] = i < n_dms ? (L2 ? __ldcg(row + i) : __ldg(row + i)) : -1.0;
-      }
-#pragma unroll
-      for (int u = 0; u < kBatch; u++) {
-        const int i = i0 + u * blockDim.x;
-        if (i < n_dms && better(v[u], i, w, bv, bi, bw)) { bv = v[u]; bi = i; bw = w; }
-      }
-    }
+  for (int64_t e = (int64_t)rank * blockDim.x + threadIdx.x; e < total; e += (int64_t)kDetectBlocks * blockDim.x) {
+    const int w = (int)(e / n_dms), i = (int)(e - (int64_t)w * n_dms);
+    const double v = snr[e];
+    if (better(v, i, w, bv, bi, bw)) { bv = v; bi = i; bw = w; }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    double v = __shfl_down_sync(0xffffffffu, bv, o);
-    int i = __shfl_down_sync(0xffffffffu, bi, o), w = __shfl_down_sync(0xffffffffu, bw, o);
+    const double v = __shfl_down_sync(0xffffffffu, bv, o);
+    const int i = __shfl_down_sync(0xffffffffu, bi, o), w = __shfl_down_sync(0xffffffffu, bw, o);
     if (better(v, i, w, bv, bi, bw)) { bv = v; bi = i; bw = w; }
   }
   if (lane == 0) { sv[warp] = bv; si[warp] = bi; sw[warp] = bw; }
@@ -385,24 +385,29 @@ __device__ void detect_block(const double* snr, const int32_t* peak_t, const int
     bw = lane < nw ? sw[lane] : 0x7fffffff;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double v = __shfl_down_sync(0xffffffffu, bv, o);
-      int i = __shfl_down_sync(0xffffffffu, bi, o), w = __shfl_down_sync(0xffffffffu, bw, o);
+      const double v = __shfl_down_sync(0xffffffffu, bv, o);
+      const int i = __shfl_down_sync(0xffffffffu, bi, o), w = __shfl_down_sync(0xffffffffu, bw, o);
       if (better(v, i, w, bv, bi, bw)) { bv = v; bi = i; bw = w; }
     }
     if (lane == 0) {
-      const int64_t o = (int64_t)bw * n_dms + bi;
-      best[0] = bi;
-      best[1] = bw;
-      best[2] = L2 ? __ldcg(peak_t + o) : peak_t[o];
-      best[3] = L2 ? __ldcg(peak_val + o) : peak_val[o];
+      *cluster.map_shared_rank(&cv[rank], 0) = bv;
+      *cluster.map_shared_rank(&ci[rank], 0) = bi;
+      *cluster.map_shared_rank(&cw[rank], 0) = bw;
     }
   }
-}
-
-__global__ void __launch_bounds__(1024, 1)
-detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val, int n_dms, int n_widths,
-              int32_t* best) {
-  detect_block<false>(snr, peak_t, peak_val, n_dms, n_widths, best);
+  cluster.sync();  // every block's result is in block 0's shared memory
+  if (rank == 0 && threadIdx.x == 0) {
+    bv = cv[0];
+    bi = ci[0];
+    bw = cw[0];
+    for (int q = 1; q < kDetectBlocks; q++)
+      if (better(cv[q], ci[q], cw[q], bv, bi, bw)) { bv = cv[q]; bi = ci[q]; bw = cw[q]; }
+    const int64_t o = (int64_t)bw * n_dms + bi;
+    best[0] = bi;
+    best[1] = bw;
+    best[2] = peak_t[o];
+    best[3] = peak_val[o];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -421,10 +426,7 @@ detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
 // validity (outputs outside [0, N_t - w] are skipped).  S1 comes in closed
 // form as in snr_kernel.
 //
-// Detection is folded in: `best` (int32[4]) is zeroed before the launch; each
-// block, once its outputs are written, counts itself in best[3]; the block
-// that counts last reads the whole table (through L2) and writes the
-// detection over the counter.
+// The detection follows as its own one-cluster launch (detect_kernel).
 
 // Scans the row at buf[4 .. 4 + n_t) in place into P[k] = buf[3 + k] (k = 0 ..
 // n_t); returns the sum of the samples this thread scanned.  Each thread scans
@@ -603,11 +605,10 @@ __device__ void row_stats_v4(const SnrArgs& a, const uint32_t* buf, int row, uin
 }
 
 template <int NW>
-__global__ void __launch_bounds__(kMaxThreads, 2) snr_pow2_kernel(SnrArgs a, int32_t* best) {
+__global__ void __launch_bounds__(kMaxThreads, 2) snr_pow2_kernel(SnrArgs a) {
   extern __shared__ __align__(16) uint32_t buf[];
   __shared__ uint32_t scratch[32];
   __shared__ uint64_t bar;
-  __shared__ int is_last;
   const int row = blockIdx.x;
   const int n_t = a.n_t;
   if (threadIdx.x == 0) {
@@ -626,15 +627,6 @@ __global__ void __launch_bounds__(kMaxThreads, 2) snr_pow2_kernel(SnrArgs a, int
   }
   const uint32_t segsum = scan_row_v4(buf, n_t, scratch);
   row_stats_v4<NW>(a, buf, row, segsum);
-  if (!best) return;
-  if (threadIdx.x < NW) __threadfence();  // this block's S/N entries before its count
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(reinterpret_cast<unsigned*>(best + 3), 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (is_last) {
-    __threadfence();
-    detect_block<true>(a.snr, a.peak_t, a.peak_val, a.n_dms, NW, best);
-  }
 }
 
 size_t prefix_smem(int n_t) { return ((size_t)n_t + kPad + 3) / 4 * 4 * sizeof(uint32_t); }
@@ -676,7 +668,7 @@ SnrKernel snr_variant(int nwp) {
   }
 }
 
-typedef void (*Pow2Kernel)(SnrArgs, int32_t*);
+typedef void (*Pow2Kernel)(SnrArgs);
 
 Pow2Kernel pow2_variant(int nw) {
   switch (nw) {
@@ -713,9 +705,13 @@ sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st
     if (sps_status s = check_row_fits(a.n_t, smem - prefix_smem(a.n_t) + 8192)) return s;
     Pow2Kernel fn = pow2_variant(a.pow2_widths);
     SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (a.best) SPS_CUDA(cudaMemsetAsync(a.best, 0, 4 * sizeof(int32_t), st));
-    fn<<<a.n_dms, c.threads, smem, st>>>(a, a.best);
+    fn<<<a.n_dms, c.threads, smem, st>>>(a);
     SPS_CUDA(cudaGetLastError());
+    if (a.best) {
+      detect_kernel<<<kDetectBlocks, kDetectThreads, 0, st>>>(a.snr, a.peak_t, a.peak_val, a.n_dms, a.n_widths,
+                                                              a.best);
+      SPS_CUDA(cudaGetLastError());
+    }
     return SPS_OK;
   }
   if (sps_status s = check_row_fits(a.n_t, sizeof(Moments) * (kMaxThreads / 32) * kWidthsPerPass + 512)) return s;
@@ -740,7 +736,8 @@ sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st
     SPS_CUDA(cudaGetLastError());
   }
   if (a.best) {
-    detect_kernel<<<1, 1024, 0, st>>>(a.snr, a.peak_t, a.peak_val, a.n_dms, a.n_widths, a.best);
+    detect_kernel<<<kDetectBlocks, kDetectThreads, 0, st>>>(a.snr, a.peak_t, a.peak_val, a.n_dms, a.n_widths,
+                                                            a.best);
     SPS_CUDA(cudaGetLastError());
   }
   return SPS_OK;
