@@ -555,16 +555,19 @@ __device__ void row_stats_v4(const SnrArgs& a, const uint32_t* buf, int row, uin
   __syncthreads();
   if (warp == nw - 1) {
     // S1 = w T - sum_{j<w} P[j] - sum_{j<w} (T - P[N_t - j]): every sample lies
-    // in w boxcars except within w - 1 of either end (end terms below 2^31 each)
+    // in w boxcars except within w - 1 of either end.  Each lane reads the end
+    // terms of j = lane + 1 and lane + 33 once (each below 2^31) and adds them
+    // into every width they belong to; one limb sum per width.
     unsigned long long T = 0ull;
     for (int q = 0; q < nw; q++) T += ptot[q];
+    uint32_t e0 = 0u, e1 = 0u;
+    const int j0 = lane + 1, j1 = lane + 33;
+    if (j0 < WMAX) e0 = P[j0] + (P[n_t] - P[n_t - j0]);
+    if (j1 < WMAX) e1 = P[j1] + (P[n_t] - P[n_t - j1]);
 #pragma unroll
     for (int k = 0; k < NW; k++) {
-      unsigned long long e = 0ull;
-      for (int j = lane + 1; j < (1 << k); j += 32)
-        e += (unsigned long long)P[j] + (unsigned long long)(P[n_t] - P[n_t - j]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+      const unsigned long long e = warp_sum64_redux((unsigned long long)(j0 < (1 << k) ? e0 : 0u) +
+                                                    (unsigned long long)(j1 < (1 << k) ? e1 : 0u));
       if (lane == 0) s1v[k] = (unsigned long long)(1u << k) * T - e;
     }
   }
