@@ -362,13 +362,22 @@ detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
   __shared__ double cv[kDetectBlocks];  // block 0: the blocks' results
   __shared__ int ci[kDetectBlocks], cw[kDetectBlocks];
   const int rank = (int)cluster.block_rank();
-  const int64_t total = (int64_t)n_widths * n_dms;
+  const int total = n_widths * n_dms;  // below 2^31 (checked by the launcher)
+  const int stride = kDetectBlocks * (int)blockDim.x;
   double bv = -1.0;
   int bi = 0x7fffffff, bw = 0x7fffffff;
-  for (int64_t e = (int64_t)rank * blockDim.x + threadIdx.x; e < total; e += (int64_t)kDetectBlocks * blockDim.x) {
-    const int w = (int)(e / n_dms), i = (int)(e - (int64_t)w * n_dms);
-    const double v = snr[e];
-    if (better(v, i, w, bv, bi, bw)) { bv = v; bi = i; bw = w; }
+  constexpr int kIn = 4;  // table reads in flight per thread
+  for (int e0 = rank * (int)blockDim.x + (int)threadIdx.x; e0 < total; e0 += kIn * stride) {
+    double v[kIn];
+#pragma unroll
+    for (int u = 0; u < kIn; u++) v[u] = e0 + u * stride < total ? snr[e0 + u * stride] : -1.0;
+#pragma unroll
+    for (int u = 0; u < kIn; u++) {
+      const int e = e0 + u * stride;
+      if (e >= total) break;
+      const int w = e / n_dms, i = e - w * n_dms;
+      if (better(v[u], i, w, bv, bi, bw)) { bv = v[u]; bi = i; bw = w; }
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -710,6 +719,8 @@ sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st
     SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     fn<<<a.n_dms, c.threads, smem, st>>>(a);
     SPS_CUDA(cudaGetLastError());
+    if (a.best && (int64_t)a.n_widths * a.n_dms >= (int64_t)1 << 31)
+      return fail(SPS_ERR_UNSUPPORTED, "S/N table too large for the detection's 32-bit indices");
     if (a.best) {
       detect_kernel<<<kDetectBlocks, kDetectThreads, 0, st>>>(a.snr, a.peak_t, a.peak_val, a.n_dms, a.n_widths,
                                                               a.best);
