@@ -436,10 +436,11 @@ def e2e_pipelined(torch, plan, xh, steps, warmup, device, n_workers=3):
 
 def launches_per_step(plan):
     """Kernels of one brute-force search: the pre-pass (pre-summed series, or the
-    shifted copies) and the pass, then the S/N kernel -- with the detection
-    folded in for power-of-two widths, else followed by the detection kernel."""
+    shifted copies) and the pass, then the S/N kernel (one launch for widths
+    1, 2, 4, ...; one per eight widths otherwise) and the detection kernel."""
     pow2 = list(plan.widths) == [1 << k for k in range(plan.n_widths)] and plan.n_widths <= 7
-    return 2 + (1 if pow2 and plan.smoothing == 0 else 2)
+    snr = 1 if pow2 and plan.smoothing == 0 else (plan.n_widths + 7) // 8
+    return 2 + snr + 1
 
 
 def device_noise(torch, shape, seed, dev):

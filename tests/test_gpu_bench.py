@@ -24,8 +24,8 @@ def test_bench_prints_one_contract_line():
               "vs_baseline", "dtype", "data", "config", "roofline", "clocks", "e2e", "gpu_launches"):
         assert k in d, k
     assert d["n_gpus"] == 1 and d["steps"] == 5 and d["warmup"] == 3 and d["value"] > 0
-    # pre-summed series, the pass, and the S/N kernel with the detection folded in
-    assert d["gpu_launches"] == 3 * 5 and d["config"]["workload"].startswith("apertif")
+    # pre-summed series, the pass, the S/N kernel and the detection kernel
+    assert d["gpu_launches"] == 4 * 5 and d["config"]["workload"].startswith("apertif")
     rf = d["roofline"]
     for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
         assert k in rf, k
