@@ -220,7 +220,10 @@ sps_status sps_integrate(const sps_plan* plan, const int32_t* D, int32_t* B, voi
  * [0, 255 * channels]; the kernel sizes its partial sums from that bound.
  * snr: device double [n_widths][n_dms]; peak_t, peak_val: device int32, same
  * shape.  best (may be NULL): device int32[4] = {DM index, width index,
- * peak_t, peak_val} of the largest S/N (ties: smaller DM, then smaller width). */
+ * peak_t, peak_val} of the largest S/N (ties: smaller DM, then smaller width).
+ * Rows are staged whole in shared memory when they fit (about 56000 samples);
+ * longer rows are streamed in chunks for widths 1, 2, 4, ..., 64 and refused
+ * with UNSUPPORTED for other width sets and for decimating smoothing. */
 sps_status sps_snr(const sps_plan* plan, const int32_t* D, double* snr, int32_t* peak_t,
                    int32_t* peak_val, int32_t* best, void* stream);
 

@@ -641,9 +641,327 @@ __global__ void __launch_bounds__(kMaxThreads, 2) snr_pow2_kernel(SnrArgs a) {
   row_stats_v4<NW>(a, buf, row, segsum);
 }
 
+// ---------------------------------------------------------------------------
+// Streaming form for width sets {1, 2, 4, ..., 2^(NW-1)}, for rows too long to
+// stage whole in shared memory (the row form above is faster when they fit).
+//
+// One block per DM row; the row's outputs are cut into chunks of 256 samples
+// and each warp takes a contiguous run of chunks (its segment), so the warps
+// never wait for one another until the row is done.  A warp streams its
+// segment: lane l holds the chunk's samples base + 4l .. base + 4l + 3 and
+// base + 128 + 4l .. base + 131 + 4l, copied by 16-byte asynchronous copies
+// (cp.async) three chunks ahead into the warp's staging slots.  The chunk is
+// scanned into 32-bit wrap-around prefix sums P (relative to the segment's
+// first sample: a boxcar is a difference, B_w[t] = P[t + w] - P[t], exact since
+// B < 2^31) by lane-local adds and warp shuffles, and stored in the warp's ring
+// of two chunk slots (slot 0's first 64 words mirrored after slot 1, so that
+// every P[t + w] of a chunk is one aligned 16-byte load at a fixed offset).  A
+// chunk's boxcars need the next chunk's prefix, so the scan runs one chunk
+// ahead (the segment's last chunk reads one chunk past it).  Per boxcar: a
+// subtract and a maximum, and the square added to a 64-bit sum.
+//
+// The first position of each maximum: each lane keeps, per width, its largest
+// boxcar and the first chunk where it reached it (a chunk's maximum compared
+// once with the running one).  After the block has the row's maximum, the
+// earliest chunk holding it is re-scanned from D by one warp, which takes the
+// first sample equal to the maximum.  S1 = sum B needs no pass: with T the row
+// total, S1_w = w T - sum_{u < w-1} (w-1-u) D[u] - sum_{u > N_t-w} (u-N_t+w) D[u]
+// (every sample lies in w boxcars except within w - 1 of either end).
+constexpr int kChunk = 256;               // outputs per chunk, eight per lane
+constexpr int kRing = 2 * kChunk + 64;    // two chunk slots and the mirror of slot 0's first 64 words
+
+// D[idx .. idx + 3] of the row, zeros past its end (n_t is a multiple of 4, so a
+// quadruple lies wholly inside or wholly outside the row).
+__device__ __forceinline__ uint4 load_quad(const int32_t* __restrict__ row, int idx, int n_t) {
+  return idx < n_t ? __ldg(reinterpret_cast<const uint4*>(row + idx)) : make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Asynchronous 16-byte copy of D[idx .. idx + 3] into shared memory, zeros
+// past the row's end (the source is then not read).
+__device__ __forceinline__ void copy_quad(uint32_t* dst, const int32_t* __restrict__ row, int idx, int n_t) {
+  const bool in = idx < n_t;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(row + (in ? idx : 0)),
+               "r"(in ? 16 : 0)
+               : "memory");
+}
+
+// Chunk j's quadruples of this lane into staging slot j % 3 (nothing past
+// chunk `last`); always one commit group, so that group counts stay uniform.
+__device__ __forceinline__ void stage_chunk(uint32_t* stage, const int32_t* __restrict__ row, int j, int last,
+                                            int n_t) {
+  const int lane = threadIdx.x & 31;
+  if (j <= last) {
+    uint32_t* s = stage + (j % 3) * kChunk + 4 * lane;
+    copy_quad(s, row, kChunk * j + 4 * lane, n_t);
+    copy_quad(s + 128, row, kChunk * j + 128 + 4 * lane, n_t);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void wait_staged() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The lane's two staged quadruples of chunk j.
+__device__ __forceinline__ void staged_quads(const uint32_t* stage, int j, uint4& a, uint4& b) {
+  const uint32_t* s = stage + (j % 3) * kChunk + 4 * (threadIdx.x & 31);
+  a = *reinterpret_cast<const uint4*>(s);
+  b = *reinterpret_cast<const uint4*>(s + 128);
+}
+
+// Prefix sums of one chunk.  `a`, `b`: the lane's quadruples D[base + 4l ..] and
+// D[base + 128 + 4l ..]; `run`: P at the chunk's first sample, advanced past the
+// chunk.  p0[i] = P[base + 4l + i], p1[i] = P[base + 128 + 4l + i]; returns the
+// chunk's sum (the same in every lane).
+__device__ __forceinline__ uint32_t scan_chunk(const uint4& a, const uint4& b, uint32_t& run, uint4& p0, uint4& p1) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t sa = a.x + a.y + a.z + a.w, sb = b.x + b.y + b.z + b.w;
+  uint32_t xa = sa, xb = sb;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t ya = __shfl_up_sync(0xffffffffu, xa, o), yb = __shfl_up_sync(0xffffffffu, xb, o);
+    if (lane >= o) { xa += ya; xb += yb; }
+  }
+  const uint32_t ta = __shfl_sync(0xffffffffu, xa, 31), tb = __shfl_sync(0xffffffffu, xb, 31);
+  p0.x = run + xa - sa;
+  p0.y = p0.x + a.x;
+  p0.z = p0.y + a.y;
+  p0.w = p0.z + a.z;
+  p1.x = run + ta + xb - sb;
+  p1.y = p1.x + b.x;
+  p1.z = p1.y + b.y;
+  p1.w = p1.z + b.z;
+  run += ta + tb;
+  return ta + tb;
+}
+
+// Stores a scanned chunk in ring slot `slot` (and slot 0's mirror).
+__device__ __forceinline__ void store_chunk(uint32_t* ring, int slot, const uint4& p0, const uint4& p1) {
+  const int lane = threadIdx.x & 31;
+  uint32_t* s = ring + slot * kChunk + 4 * lane;
+  *reinterpret_cast<uint4*>(s) = p0;
+  *reinterpret_cast<uint4*>(s + 128) = p1;
+  if (slot == 0 && lane < 16) *reinterpret_cast<uint4*>(ring + 2 * kChunk + 4 * lane) = p0;
+}
+
+
+
+// Boxcars of one chunk for every width.  `ptr` = the chunk's slot + 4 lane;
+// `c` the chunk index; `mc` (in shared memory, one word per width and lane)
+// receives the chunk where the lane's maximum of a width first grew to its
+// current value.  EDGE: some output of the chunk is not valid for some width
+// (t + w > n_t): those are skipped.
+template <int NW, bool EDGE>
+__device__ __forceinline__ void chunk_boxcars(const uint32_t* ptr, int base, int n_t, int c,
+                                              unsigned long long (&s2)[NW], int (&mx)[NW], int* mc) {
+  const int lane = threadIdx.x & 31;
+  const uint4 A0 = *reinterpret_cast<const uint4*>(ptr);
+  const uint4 A1 = *reinterpret_cast<const uint4*>(ptr + 128);
+  const uint4 N0 = *reinterpret_cast<const uint4*>(ptr + 4);
+  const uint4 N1 = *reinterpret_cast<const uint4*>(ptr + 132);
+#pragma unroll
+  for (int k = 0; k < NW; k++) {
+    const int w = 1 << k;
+    uint4 Q0, Q1;
+    if (w >= 8) {
+      Q0 = *reinterpret_cast<const uint4*>(ptr + w);
+      Q1 = *reinterpret_cast<const uint4*>(ptr + 128 + w);
+    }
+    int cm = -1;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const uint4& A = h ? A1 : A0;
+      const uint4& N = h ? N1 : N0;
+      const uint4& Q = h ? Q1 : Q0;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        // P[t + w] for t = base + 128 h + 4 lane + i
+        const uint32_t hi = w >= 8 ? quad(Q, i) : (i + w < 4 ? quad(A, i + w) : quad(N, i + w - 4));
+        const uint32_t B = hi - quad(A, i);
+        if (EDGE) {
+          const bool ok = base + 128 * h + 4 * lane + i + w <= n_t;
+          add_square(s2[k], ok ? B : 0u);
+          if (ok) cm = max(cm, (int)B);
+        } else {
+          add_square(s2[k], B);
+          cm = max(cm, (int)B);
+        }
+      }
+    }
+    if (cm > mx[k]) {
+      mx[k] = cm;
+      mc[k * 32] = c;
+    }
+  }
+}
+
+// First sample t of chunk c whose width-w boxcar equals m (the row's maximum),
+// found by one warp from D; the ring serves as its scratch.  Every lane returns it.
+__device__ int first_in_chunk(const int32_t* __restrict__ row, int n_t, uint32_t* ring, int c, int w, int m) {
+  const int lane = threadIdx.x & 31;
+  const int base = kChunk * c;
+  uint32_t run = 0u;
+  uint4 p0, p1;
+  scan_chunk(load_quad(row, base + 4 * lane, n_t), load_quad(row, base + 128 + 4 * lane, n_t), run, p0, p1);
+  store_chunk(ring, 0, p0, p1);
+  scan_chunk(load_quad(row, base + kChunk + 4 * lane, n_t), load_quad(row, base + kChunk + 128 + 4 * lane, n_t),
+             run, p0, p1);
+  store_chunk(ring, 1, p0, p1);
+  __syncwarp();
+  int first = 0x7fffffff;
+#pragma unroll
+  for (int h = 1; h >= 0; h--) {
+#pragma unroll
+    for (int i = 3; i >= 0; i--) {
+      const int off = 128 * h + 4 * lane + i;
+      const int t = base + off;
+      if (t + w <= n_t && (int)(ring[off + w] - ring[off]) == m) first = t;
+    }
+  }
+  first = __reduce_min_sync(0xffffffffu, first);
+  __syncwarp();
+  return first;
+}
+
+// Sum over the warp of a 64-bit value (every lane gets it).
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(kMaxThreads, 2) snr_stream_kernel(SnrArgs a) {
+  constexpr int kWarps = kMaxThreads / 32;
+  // per warp: a ring of prefix sums, three staging slots of D, NW x 32 first-chunk words
+  extern __shared__ __align__(16) uint32_t dyn[];
+  __shared__ unsigned long long ws2[kWarps][NW], wtot[kWarps], gs1[NW];
+  __shared__ int wmx[kWarps][NW], gmax[NW], gchunk[NW], gfirst[NW];
+  const int row = blockIdx.x, n_t = a.n_t;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int32_t* __restrict__ Drow = a.D + (int64_t)row * n_t;
+  uint32_t* ring = dyn + warp * (kRing + 3 * kChunk + NW * 32);
+  uint32_t* stage = ring + kRing;
+  int* mc = reinterpret_cast<int*>(stage + 3 * kChunk) + lane;
+  const int n_chunks = (n_t + kChunk - 1) / kChunk;
+  const int cb = warp * n_chunks / nwarps, ce = (warp + 1) * n_chunks / nwarps;
+
+  unsigned long long s2[NW];
+  int mx[NW];
+#pragma unroll
+  for (int k = 0; k < NW; k++) { s2[k] = 0ull; mx[k] = -1; }
+  if (threadIdx.x < NW) gchunk[threadIdx.x] = 0x7fffffff;
+#pragma unroll
+  for (int k = 0; k < NW; k++) mc[k * 32] = 0;
+  unsigned long long tot = 0ull;  // the segment's sum
+  if (cb < ce) {
+    // chunks cb .. ce (ce: the lookahead) stream through three staging slots
+    stage_chunk(stage, Drow, cb, ce, n_t);
+    stage_chunk(stage, Drow, cb + 1, ce, n_t);
+    stage_chunk(stage, Drow, cb + 2, ce, n_t);
+    uint32_t run = 0u;
+    uint4 da, db, p0, p1;
+    wait_staged<2>();
+    staged_quads(stage, cb, da, db);
+    tot += scan_chunk(da, db, run, p0, p1);
+    store_chunk(ring, cb & 1, p0, p1);
+    for (int c = cb; c < ce; c++) {
+      // chunk c + 1 (the lookahead past the segment's end included) into the other slot
+      wait_staged<1>();
+      staged_quads(stage, c + 1, da, db);
+      const uint32_t ct = scan_chunk(da, db, run, p0, p1);
+      if (c + 1 < ce) tot += ct;
+      store_chunk(ring, (c + 1) & 1, p0, p1);
+      stage_chunk(stage, Drow, c + 3, ce, n_t);  // into chunk c's staging slot, read before
+      __syncwarp();
+      const int base = kChunk * c;
+      const uint32_t* ptr = ring + (c & 1) * kChunk + 4 * lane;
+      if (base + kChunk - 1 + (1 << (NW - 1)) <= n_t)
+        chunk_boxcars<NW, false>(ptr, base, n_t, c, s2, mx, mc);
+      else
+        chunk_boxcars<NW, true>(ptr, base, n_t, c, s2, mx, mc);
+      __syncwarp();  // slot c & 1 is rewritten next
+    }
+    wait_staged<0>();
+  }
+  // the warp's moments and maxima
+#pragma unroll
+  for (int k = 0; k < NW; k++) {
+    const unsigned long long v2 = warp_sum64(s2[k]);
+    const int m = __reduce_max_sync(0xffffffffu, mx[k]);
+    if (lane == 0) { ws2[warp][k] = v2; wmx[warp][k] = m; }
+  }
+  if (lane == 0) wtot[warp] = tot;
+  __syncthreads();
+  if (threadIdx.x < NW) {
+    const int k = threadIdx.x;
+    int m = wmx[0][k];
+    for (int q = 1; q < nwarps; q++) m = max(m, wmx[q][k]);
+    gmax[k] = m;
+  }
+  __syncthreads();
+  // the earliest chunk holding each width's maximum
+#pragma unroll
+  for (int k = 0; k < NW; k++)
+    if (mx[k] == gmax[k]) atomicMin(&gchunk[k], mc[k * 32]);
+  __syncthreads();
+  for (int k = warp; k < NW; k += nwarps) {
+    // (every width has a valid output: the plan keeps widths within the row)
+    const int f = gchunk[k] >= 0 && gchunk[k] < n_chunks
+                      ? first_in_chunk(Drow, n_t, ring, gchunk[k], 1 << k, gmax[k]) : 0;
+    if (lane == 0) gfirst[k] = f;
+  }
+  if (warp == nwarps - 1) {
+    // S1 from the row total and the samples within 63 of either end
+    unsigned long long T = 0ull;
+    for (int q = 0; q < nwarps; q++) T += wtot[q];
+    uint32_t lo[2], hi[2];
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const int u = lane + 32 * j, v = n_t - 64 + lane + 32 * j;
+      lo[j] = u < n_t ? (uint32_t)__ldg(Drow + u) : 0u;
+      hi[j] = v >= 0 ? (uint32_t)__ldg(Drow + v) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < NW; k++) {
+      const int w = 1 << k;
+      unsigned long long e = 0ull;
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        const int u = lane + 32 * j, v = n_t - 64 + lane + 32 * j;
+        if (u < w - 1) e += (unsigned long long)(w - 1 - u) * lo[j];
+        if (v >= 0 && v > n_t - w) e += (unsigned long long)(v - n_t + w) * hi[j];
+      }
+      e = warp_sum64(e);
+      if (lane == 0) gs1[k] = (unsigned long long)w * T - e;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NW) {
+    const int k = threadIdx.x;
+    unsigned long long v2 = 0ull;
+    for (int q = 0; q < nwarps; q++) v2 += ws2[q][k];
+    const Moments r{gs1[k], v2, 0ull, gmax[k], 0};
+    const int64_t o = (int64_t)k * a.n_dms + row;
+    a.snr[o] = snr_from_moments(n_t - (1 << k) + 1, r);
+    a.peak_t[o] = gfirst[k];
+    a.peak_val[o] = gmax[k];
+  }
+}
+
+
 size_t prefix_smem(int n_t) { return ((size_t)n_t + kPad + 3) / 4 * 4 * sizeof(uint32_t); }
 
 bool tma_ok(const int32_t* D, int n_t) { return ((uintptr_t)D & 15) == 0 && (n_t & 3) == 0; }
+
+bool row_fits(int n_t, size_t extra) {
+  int dev = 0, max_smem = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return false;
+  return prefix_smem(n_t) + extra <= (size_t)max_smem;
+}
 
 sps_status check_row_fits(int n_t, size_t extra) {
   int dev = 0, max_smem = 0;
@@ -709,9 +1027,53 @@ size_t pow2_smem(int n_t, int nw) {
   return ((size_t)4 * n_grp + 4 + (1 << (nw - 1)) + 4) * sizeof(uint32_t);
 }
 
+typedef void (*StreamKernel)(SnrArgs);
+
+StreamKernel stream_variant(int nw) {
+  switch (nw) {
+    case 1: return snr_stream_kernel<1>;
+    case 2: return snr_stream_kernel<2>;
+    case 3: return snr_stream_kernel<3>;
+    case 4: return snr_stream_kernel<4>;
+    case 5: return snr_stream_kernel<5>;
+    case 6: return snr_stream_kernel<6>;
+    default: return snr_stream_kernel<7>;
+  }
+}
+
+// The streaming form also needs each 256-sample chunk's sum to fit 32 bits.
+bool stream_form(const SnrArgs& a) {
+  const long double bmax = (long double)std::max<int64_t>(1, a.max_boxcar);
+  const long double smax = bmax / (long double)(1 << (a.pow2_widths - 1));  // largest sample
+  return smax * kChunk < 4.2e9L;
+}
+
+// Shared memory of the streaming kernel: per warp a ring, three staging slots
+// and NW x 32 first-chunk words.
+size_t stream_smem(int nw, int threads) {
+  return (size_t)(threads / 32) * (kRing + 3 * kChunk + nw * 32) * sizeof(uint32_t);
+}
+
 sps_status launch_snr(const SnrArgs& a, const sps_snr_config& c, cudaStream_t st) {
   std::string why;
   if (!snr_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
+  if (pow2_form(a) && !row_fits(a.n_t, pow2_smem(a.n_t, a.pow2_widths) - prefix_smem(a.n_t) + 8192) &&
+      stream_form(a)) {
+    // rows too long to stage whole: the streaming form, any row length
+    const size_t smem = stream_smem(a.pow2_widths, c.threads);
+    StreamKernel fn = stream_variant(a.pow2_widths);
+    SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fn<<<a.n_dms, c.threads, smem, st>>>(a);
+    SPS_CUDA(cudaGetLastError());
+    if (a.best && (int64_t)a.n_widths * a.n_dms >= (int64_t)1 << 31)
+      return fail(SPS_ERR_UNSUPPORTED, "S/N table too large for the detection's 32-bit indices");
+    if (a.best) {
+      detect_kernel<<<kDetectBlocks, kDetectThreads, 0, st>>>(a.snr, a.peak_t, a.peak_val, a.n_dms, a.n_widths,
+                                                              a.best);
+      SPS_CUDA(cudaGetLastError());
+    }
+    return SPS_OK;
+  }
   if (pow2_form(a)) {
     const size_t smem = pow2_smem(a.n_t, a.pow2_widths);
     if (sps_status s = check_row_fits(a.n_t, smem - prefix_smem(a.n_t) + 8192)) return s;

@@ -672,3 +672,53 @@ def test_one_plan_on_concurrent_streams(lib, presum):
         bi, bw = oracle.detect(s)
         assert _to_np(outs[k]["best"]).tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])]
     assert p.status() == 0
+
+
+@pytest.mark.parametrize("threads", [64, 256])
+def test_snr_rows_longer_than_shared_memory(lib, threads):
+    """Rows too long to stage whole in shared memory (70000 samples, 280 KB) take
+    the streaming S/N form: edge rows and noise rows against the oracle, and a
+    whole search on such rows; a width set without a streaming form is refused
+    with UNSUPPORTED rather than run."""
+    torch = _torch()
+    n_t, C, n_dms = 70000, 256, 8
+    widths = [1, 2, 4, 8, 16, 32, 64]
+    dms = synth.dm_grid(n_dms, 2.0)
+    p = lib.Plan(C, 1250.0, 1550.0, 81.92e-6, n_t, dms, widths)
+    c = p.config
+    c.snr = lib.SnrConfig(threads)
+    p.config = c
+    rng = np.random.Generator(np.random.PCG64(77))
+    D = rng.integers(30000, 35000, (n_dms, n_t)).astype(np.int32)
+    D[0] = 11                                   # constant row
+    D[1] = 0
+    D[1, 0] = 255 * C                           # spike at the first sample
+    D[2] = 0
+    D[2, n_t - 1] = 255 * C                     # spike at the last sample
+    D[2, 12345] = 5
+    D[3] = 0
+    D[3, ::4097] = 999                          # the same maximum in many chunks
+    D[4, n_t // 2: n_t // 2 + 40] += 20000      # a wide pulse
+    out = p.alloc_outputs()
+    lib.sps_snr(p, torch.from_numpy(D).cuda(), out["snr"], out["peak_t"], out["peak_val"], out["best"])
+    torch.cuda.synchronize()
+    s, pt, pv = oracle.snr(D, widths)
+    _check_snr(_to_np(out["snr"]), _to_np(out["peak_t"]), _to_np(out["peak_val"]), s, pt, pv)
+    bi, bw = oracle.detect(s)
+    assert _to_np(out["best"]).tolist() == [bi, bw, int(pt[bw, bi]), int(pv[bw, bi])]
+    # a whole search on such rows
+    x = synth.filterbank(C, 1250.0, 1550.0, 81.92e-6, p.input_samples, 78,
+                         [synth.Pulse(float(dms[5]), 8.0, 20.0, 40000.0)], pitch=p.pitch)
+    o = p.search(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    Do = oracle.dedisperse(x, oracle.delay_table(1250.0, 1550.0, C, 81.92e-6, dms), n_t)
+    assert np.array_equal(_to_np(o["D"]), Do)
+    s, pt, pv = oracle.snr(Do, widths)
+    _check_snr(_to_np(o["snr"]), _to_np(o["peak_t"]), _to_np(o["peak_val"]), s, pt, pv)
+    assert p.status() == 0
+    # widths that are not 1, 2, 4, ... on such rows: refused
+    q = lib.Plan(C, 1250.0, 1550.0, 81.92e-6, n_t, dms, [1, 3, 9])
+    oq = q.alloc_outputs()
+    with pytest.raises(lib.SpsError) as e:
+        lib.sps_snr(q, torch.from_numpy(D).cuda(), oq["snr"], oq["peak_t"], oq["peak_val"], oq["best"])
+    assert e.value.status == 2
