@@ -676,7 +676,18 @@ def main():
     hbm_gbs, hbm_src = measured_hbm_gbs()
     snr_ms_mean = statistics.mean(snr_ms)
     snr_bytes = 4.0 * wl.dm_trial_samples + wl.widths.size * wl.dms.size * 16.0
-    line["kernel_rooflines"] = {"snr_detect": {
+    # the pass's own bound, the shared-memory data path: the bytes its layout
+    # must read from shared memory (a 16-bit lane per unit of 2^presum channels,
+    # a byte per channel for single channels) per DM-trial sample
+    units = wl.channels / (1 << presum) if presum else wl.channels
+    shared_bytes = float(wl.dm_trial_samples) * units * (2 if presum else 1)
+    shared_peak = N_SM * 128 * SM_MAX_MHZ * 1e6 / 1e12  # TB/s: 128 B per clock per SM
+    line["kernel_rooflines"] = {"dedisperse_shared": {
+        "bound": "shared", "algorithmic_shared_bytes_per_launch": shared_bytes, "ms_per_launch": dd_ms,
+        "achieved_tbs": shared_bytes / (dd_ms * 1e-3) / 1e12, "peak_tbs": shared_peak,
+        "frac": shared_bytes / (dd_ms * 1e-3) / 1e12 / shared_peak,
+        "peak_derivation": "152 SMs x 128 B/clk x 2070 MHz", "note": "time of the whole call, pre-pass included"},
+        "snr_detect": {
         "bound": "hbm", "algorithmic_bytes_per_launch": snr_bytes, "ms_per_launch": snr_ms_mean,
         "achieved_gbs": snr_bytes / (snr_ms_mean * 1e-3) / 1e9, "peak_gbs": hbm_gbs, "peak_source": hbm_src,
         "frac": snr_bytes / (snr_ms_mean * 1e-3) / 1e9 / hbm_gbs,
