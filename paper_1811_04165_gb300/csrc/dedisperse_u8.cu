@@ -19,12 +19,15 @@
 //     shifted copies 1..3 of the whole batch once; all four copies and the
 //     chunk's shared-memory offset table arrive by bulk asynchronous copies
 //     (TMA) into a two-stage ring guarded by mbarriers, so the warps only add.
-//   * SWAR: a word of 4 samples is split into even and odd bytes in 16-bit
-//     lanes (one AND, one byte permute: the integer ALU pipe, 64 lanes per SM)
-//     and the lanes are accumulated with integer multiply-adds by 1 on the FMA
-//     pipe, which the ALU work would otherwise saturate.  16-bit lanes stay
-//     exact for 257 channels of 255; partial sums are folded into int32
-//     registers every <= 256 channels.
+//   * SWAR: the words of 4 samples are summed whole (one three-input add per
+//     two channels), and their odd bytes, moved into 16-bit lanes by one byte
+//     permute, are summed apart with integer multiply-adds by 1 on the FMA
+//     pipe (the integer ALU pipe, 64 lanes per SM, would otherwise saturate).
+//     With sums b_k of byte k over <= 257 channels of 255, both below 2^16,
+//       raw = b0 + 2^8 b1 + 2^16 b2 + 2^24 b3,   odd = b1 + 2^16 b3,
+//       raw - (odd << 8) = b0 + 2^16 b2   (mod 2^32),
+//     so the even bytes' 16-bit lanes come back exactly; partial sums are
+//     folded into int32 registers every <= 256 channels.
 //   * Shared loads use 32-bit shared-window addresses with immediate offsets.
 //   * The offset of (trial, channel) inside the staged windows does not depend
 //     on the time tile (tiles start at multiples of 128), so the plan
@@ -37,7 +40,6 @@
 namespace sps {
 namespace {
 
-constexpr uint32_t kEvenBytes = 0x00FF00FFu;
 constexpr int kMaxThreads = 512;
 
 __device__ __forceinline__ uint32_t odd_bytes(uint32_t w) { return __byte_perm(w, 0u, 0x4341); }
@@ -135,13 +137,13 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
     }
   };
 
-  uint32_t lo[ND][NW], hi[ND][NW];
+  uint32_t raw[ND][NW], hi[ND][NW];  // whole-word sums; odd bytes in 16-bit lanes
   int32_t acc[ND][NW][4];
 #pragma unroll
   for (int r = 0; r < ND; r++)
 #pragma unroll
     for (int m = 0; m < NW; m++) {
-      lo[r][m] = 0u; hi[r][m] = 0u;
+      raw[r][m] = 0u; hi[r][m] = 0u;
 #pragma unroll
       for (int q = 0; q < 4; q++) acc[r][m][q] = 0;
     }
@@ -150,13 +152,14 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
     for (int r = 0; r < ND; r++)
 #pragma unroll
       for (int m = 0; m < NW; m++) {
+        const uint32_t lo = raw[r][m] - (hi[r][m] << 8);  // even bytes in 16-bit lanes
         // whole lane words (low + 2^16 high, mod 2^32) and the high lanes; the
         // low sums are recovered after the last fold as word sum - 2^16 high sum
-        acc[r][m][0] += (int32_t)lo[r][m];
-        acc[r][m][2] += (int32_t)(lo[r][m] >> 16);
+        acc[r][m][0] += (int32_t)lo;
+        acc[r][m][2] += (int32_t)(lo >> 16);
         acc[r][m][1] += (int32_t)hi[r][m];
         acc[r][m][3] += (int32_t)(hi[r][m] >> 16);
-        lo[r][m] = 0u; hi[r][m] = 0u;
+        raw[r][m] = 0u; hi[r][m] = 0u;
       }
   };
 
@@ -184,7 +187,7 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
           if (stage_read_ok(o.y, lim, a.status)) lds_row<NW>(base + o.y, W2);
 #pragma unroll
           for (int m = 0; m < NW; m++) {
-            lo[r][m] = madd(W2[m] & kEvenBytes, one, madd(W1[m] & kEvenBytes, one, lo[r][m]));
+            raw[r][m] += W1[m] + W2[m];
             hi[r][m] = madd(odd_bytes(W2[m]), one, madd(odd_bytes(W1[m]), one, hi[r][m]));
           }
         }
@@ -197,7 +200,7 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
           if (stage_read_ok(e[r].x, lim, a.status)) lds_row<NW>(base + e[r].x, W1);
 #pragma unroll
           for (int m = 0; m < NW; m++) {
-            lo[r][m] = madd(W1[m] & kEvenBytes, one, lo[r][m]);
+            raw[r][m] += W1[m];
             hi[r][m] = madd(odd_bytes(W1[m]), one, hi[r][m]);
           }
         }
