@@ -656,7 +656,8 @@ def main():
                        "layout's algorithmic wavefronts) plus 15.5 % stage fills by bulk copies; the pass executes a "
                        "quarter of the brute-force adds (ncu, " + summary + ")",
                     1: "shared-memory data path (pairs: half the brute-force adds; no committed ncu capture)",
-                    0: "instruction issue: 82 % issue-active, 1.72 instructions per add (ncu, " + summary + ")"}[presum]}
+                    0: "instruction issue and the shared-memory data path: 75 % issue-active, 1.33 instructions "
+                       "per add, L1/shared 68 % (ncu, " + summary + ")"}[presum]}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
