@@ -386,7 +386,7 @@ def time_pipelined(torch, plan, xs, steps, warmup, n_streams=2):
     return e0.elapsed_time(e1), held
 
 
-def e2e_pipelined(torch, plan, xh, steps, warmup, device, n_workers=3):
+def e2e_pipelined(torch, plan, xh, steps, warmup, device, n_workers=8):
     """Wall time (s) of `steps` batches through the host entry point
     (sps_search_host: pinned host batch in, S/N tables and detection back,
     stream synchronised) on `n_workers` host threads, each with its own stream
@@ -756,7 +756,7 @@ def main():
                    "h2d_bytes_per_step": wl.channels * pitch,
                    "d2h_bytes_per_step": int(hs.numel() * 8 + ht.numel() * 4 + hv.numel() * 4 + 16),
                    "ms_per_step": 1e3 * e2e_total / args.steps,
-                   "how": "sps_search_host on 3 host threads taking steps in turn (own stream and buffers each); "
+                   "how": "sps_search_host on 8 host threads taking steps in turn (own stream and buffers each); "
                           "every step copies its pinned batch in and its S/N tables and detection out",
                    "sequential_ms_per_step": 1e3 * e2e_seq / args.steps}
 

@@ -185,6 +185,17 @@ def test_brute_saturated_and_edges(lib):
     lib.sps_dedisperse(pq, torch.from_numpy(x).cuda(), D)
     torch.cuda.synchronize()
     assert np.all(_to_np(D) == 255 * C)
+    # single channels at their limit: 256 channels of 255 per fold (chunks of 16 fold at exactly 256, chunks
+    # of 6 at 252), every byte of a word at 255, so the whole-word sums wrap and the even lanes come back only
+    # through the odd-lane sums
+    c = p.config
+    for cfg in [(4, 16, 8, 1, 16, 0), (4, 8, 2, 2, 6, 0)]:
+        c.brute = lib.DedispConfig(*cfg)
+        p.config = c
+        D.fill_(0)
+        lib.sps_dedisperse(p, torch.from_numpy(x).cuda(), D)
+        torch.cuda.synchronize()
+        assert np.all(_to_np(D) == 255 * C), cfg
     # a single channel, single DM, single sample
     p1 = lib.Plan(1, 1250.0, 1550.0, 81.92e-6, 1, [0.0], [1])
     x1 = np.zeros((1, 16), np.uint8)
