@@ -17,6 +17,7 @@
 // i.e. (peak - mean) / population sigma, since N S2 - S1^2 = N^2 sigma^2.
 // Nothing is materialised; the integrate kernel writes B for checking.
 #include <algorithm>
+#include <climits>
 
 #include <cooperative_groups.h>
 
@@ -335,8 +336,13 @@ integrate_kernel(const int32_t* D, int n_dms, int n_t, const int32_t* widths, in
   }
 }
 
-// Largest S/N over (width, DM); ties -> smaller DM index, then smaller width index.
-__device__ __forceinline__ bool better(double v, int i, int w, double bv, int bi, int bw) {
+// Largest S/N over (width, DM); ties -> smaller DM index, then smaller width
+// index.  Every S/N this library writes is a finite double >= +0 (the peak is
+// never below the mean; a constant series gives 0), and the bit patterns of
+// such doubles, read as signed 64-bit integers, order exactly as the values, so
+// the comparison runs on the integer pipe (the FP64 pipe of this part is
+// narrow).  The sentinel LLONG_MIN loses to every entry.
+__device__ __forceinline__ bool better(long long v, int i, int w, long long bv, int bi, int bw) {
   if (v != bv) return v > bv;
   if (i != bi) return i < bi;
   return w < bw;
@@ -357,20 +363,22 @@ detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
               int32_t* best) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  __shared__ double sv[32];
+  __shared__ long long sv[32];
   __shared__ int si[32], sw[32];
-  __shared__ double cv[kDetectBlocks];  // block 0: the blocks' results
+  __shared__ long long cv[kDetectBlocks];  // block 0: the blocks' results
   __shared__ int ci[kDetectBlocks], cw[kDetectBlocks];
+  cluster.barrier_arrive();  // matched before the remote writes into block 0
   const int rank = (int)cluster.block_rank();
   const int total = n_widths * n_dms;  // below 2^31 (checked by the launcher)
   const int stride = kDetectBlocks * (int)blockDim.x;
-  double bv = -1.0;
+  const long long* key = reinterpret_cast<const long long*>(snr);
+  long long bv = LLONG_MIN;
   int bi = 0x7fffffff, bw = 0x7fffffff;
   constexpr int kIn = 4;  // table reads in flight per thread
   for (int e0 = rank * (int)blockDim.x + (int)threadIdx.x; e0 < total; e0 += kIn * stride) {
-    double v[kIn];
+    long long v[kIn];
 #pragma unroll
-    for (int u = 0; u < kIn; u++) v[u] = e0 + u * stride < total ? snr[e0 + u * stride] : -1.0;
+    for (int u = 0; u < kIn; u++) v[u] = e0 + u * stride < total ? key[e0 + u * stride] : LLONG_MIN;
 #pragma unroll
     for (int u = 0; u < kIn; u++) {
       const int e = e0 + u * stride;
@@ -382,27 +390,28 @@ detect_kernel(const double* snr, const int32_t* peak_t, const int32_t* peak_val,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double v = __shfl_down_sync(0xffffffffu, bv, o);
+    const long long v = __shfl_down_sync(0xffffffffu, bv, o);
     const int i = __shfl_down_sync(0xffffffffu, bi, o), w = __shfl_down_sync(0xffffffffu, bw, o);
     if (better(v, i, w, bv, bi, bw)) { bv = v; bi = i; bw = w; }
   }
   if (lane == 0) { sv[warp] = bv; si[warp] = bi; sw[warp] = bw; }
   __syncthreads();
   if (warp == 0) {
-    bv = lane < nw ? sv[lane] : -1.0;
+    bv = lane < nw ? sv[lane] : LLONG_MIN;
     bi = lane < nw ? si[lane] : 0x7fffffff;
     bw = lane < nw ? sw[lane] : 0x7fffffff;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double v = __shfl_down_sync(0xffffffffu, bv, o);
+      const long long v = __shfl_down_sync(0xffffffffu, bv, o);
       const int i = __shfl_down_sync(0xffffffffu, bi, o), w = __shfl_down_sync(0xffffffffu, bw, o);
       if (better(v, i, w, bv, bi, bw)) { bv = v; bi = i; bw = w; }
     }
-    if (lane == 0) {
-      *cluster.map_shared_rank(&cv[rank], 0) = bv;
-      *cluster.map_shared_rank(&ci[rank], 0) = bi;
-      *cluster.map_shared_rank(&cw[rank], 0) = bw;
-    }
+  }
+  cluster.barrier_wait();  // every block of the cluster has started
+  if (warp == 0 && lane == 0) {
+    *cluster.map_shared_rank(&cv[rank], 0) = bv;
+    *cluster.map_shared_rank(&ci[rank], 0) = bi;
+    *cluster.map_shared_rank(&cw[rank], 0) = bw;
   }
   cluster.sync();  // every block's result is in block 0's shared memory
   if (rank == 0 && threadIdx.x == 0) {
