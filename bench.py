@@ -707,6 +707,17 @@ def main():
                            "dedisperse_ms": statistics.mean(a for a, _ in ts),
                            "snr_detect_ms": statistics.mean(b for _, b in ts),
                            "subbands": 32, "coarse_dms": 64}
+        # the same path streamed like the headline (batches on two streams in turn);
+        # each stream's last batch must equal a search of its input on its own
+        sub_pipe_ms, held_s = time_pipelined(torch, ps, xs, args.steps, args.warmup)
+        same = True
+        for _, o, xi in held_s:
+            r = ps.search(xs[xi])
+            same = same and all(torch.equal(o[k], r[k]) for k in ("D", "snr", "peak_t", "peak_val", "best"))
+        torch.cuda.synchronize()
+        line["subband"]["pipelined"] = {"value": samples * args.steps / (sub_pipe_ms * 1e-3), "unit": UNIT,
+                                        "ms_per_step": sub_pipe_ms / args.steps, "outputs_equal_own_search": same,
+                                        "how": "batches on two streams in turn, as the headline"}
         # roofline of the two steps: the slower of their algorithmic bytes over HBM
         # (x in, Y written and read, D out) and their adds at the derived ALU peak
         n_1 = ps.step1_samples
@@ -790,6 +801,8 @@ def main():
         dist.destroy_process_group()
     if not parity_ok:
         sys.exit("bench: the timed run's outputs differ from the oracle")
+    if not line.get("subband", {}).get("pipelined", {}).get("outputs_equal_own_search", True):
+        sys.exit("bench: the streamed two-step path's outputs differ from a search of the same input")
 
 
 if __name__ == "__main__":
