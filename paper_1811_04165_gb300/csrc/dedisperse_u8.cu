@@ -63,7 +63,7 @@ __device__ __forceinline__ void lds_row(uint32_t addr, uint32_t (&w)[NW]) {
 
 template <int ND, int NW>
 __global__ void __launch_bounds__(kMaxThreads, 1)
-u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
+u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb, int gpb) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int wt = (int)(blockDim.x >> 5) / wd;
   const int Tt = wt * 128 * NW;
@@ -71,7 +71,7 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
   const int copy_stride = cc_max * wb;
   const int stage_bytes = 4 * copy_stride + cc_max * a.di_pad * 4;
   int32_t* b0s = reinterpret_cast<int32_t*>(smem + 2 * stage_bytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes + ((a.group_channels * 4 + 15) & ~15));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes + ((gpb * a.group_channels * 4 + 15) & ~15));
   __shared__ int aborted;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -79,10 +79,14 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
   const int tile = blockIdx.x;
   const int i0 = tile * Di;
   const int t0 = blockIdx.y * Tt;
-  const int g = blockIdx.z;
+  // the block's groups g0 .. g0 + ng - 1, walked as one stream of chunks so
+  // that the stage ring keeps running from one group into the next
+  const int g0 = blockIdx.z * gpb;
+  const int ng = min(gpb, a.n_groups - g0);
   const int G = a.group_channels;
-  const int c_lo = g * G;
-  const int n_chunks = (G + cc_max - 1) / cc_max;
+  const int c_lo = g0 * G;
+  const int chunks_g = (G + cc_max - 1) / cc_max;  // chunks per group
+  const int n_chunks = ng * chunks_g;
   const int pairs = (G + 1) >> 1;
   const uint32_t toff = (uint32_t)(t_sub * 128 * NW + lane * 4);
   // bounds-checked build: the largest staged offset whose NW words fit the four
@@ -91,7 +95,7 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
   if (kBoundsCheck && (dm_sub + 1) * ND > a.di_pad) stage_read_ok(1u, -1, a.status);
   const uint32_t one = a.one;
 
-  for (int c = tid; c < G; c += blockDim.x) b0s[c] = a.b0[(int64_t)tile * a.channels + c_lo + c];
+  for (int c = tid; c < ng * G; c += blockDim.x) b0s[c] = a.b0[(int64_t)tile * a.channels + c_lo + c];
   if (tid == 0) {
     aborted = 0;
     mbar_init(&bars[0], blockDim.x >> 5);
@@ -103,12 +107,15 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
   // Every warp stages its share of chunk `ch` (channels warp, warp + nwarps,
   // ...) into stage ch & 1: the four shifted copies of each channel window;
   // warp 0 also copies the chunk's offset table.  Each warp's lane 0 arrives
-  // on the stage barrier with the bytes its warp issued.
+  // on the stage barrier with the bytes its warp issued.  Chunk ch is chunk
+  // ch % chunks_g of the block's group ch / chunks_g; cb is its first channel
+  // inside the block's channel range.
   const int nwarps = (int)(blockDim.x >> 5);
   auto issue = [&](int ch) {
     const int st = ch & 1;
     uint8_t* sb = smem + st * stage_bytes;
-    const int cb = ch * cc_max, cc = min(cc_max, G - cb);
+    const int gi = ch / chunks_g, cg = ch - gi * chunks_g;
+    const int cb = gi * G + cg * cc_max, cc = min(cc_max, G - cg * cc_max);
     const int npair = (cc + 1) >> 1;
     const uint32_t tbl_bytes = (uint32_t)(npair * a.di_pad * 8);
     // lanes 4q..4q+3 of a warp handle copies 0..3 of channels warp + (q + 8k) * nwarps
@@ -132,7 +139,8 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
       bulk_g2s(sb + j * copy_stride + l * wb, src, bytes, &bars[st]);
     }
     if (warp == 0 && lane == 0) {
-      const uint32_t* src = a.offs + (((int64_t)tile * a.n_groups + g) * pairs + (cb >> 1)) * a.di_pad * 2;
+      const uint32_t* src =
+          a.offs + (((int64_t)tile * a.n_groups + g0 + gi) * pairs + ((cg * cc_max) >> 1)) * a.di_pad * 2;
       bulk_g2s(sb + 4 * copy_stride, src, tbl_bytes, &bars[st]);
     }
   };
@@ -163,14 +171,65 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
       }
   };
 
+  // A group's sums: the last fold, the low lanes recovered, the rows stored
+  // (each lane holds 4 consecutive samples per (trial, word)), the registers
+  // cleared for the block's next group.
+  const bool vec = (a.out_pitch & 3) == 0;
+  auto finish_group = [&](int g) {
+    fold();
+#pragma unroll
+    for (int r = 0; r < ND; r++)
+#pragma unroll
+      for (int m = 0; m < NW; m++) {
+        acc[r][m][0] = (int32_t)((uint32_t)acc[r][m][0] - ((uint32_t)acc[r][m][2] << 16));
+        acc[r][m][1] = (int32_t)((uint32_t)acc[r][m][1] - ((uint32_t)acc[r][m][3] << 16));
+      }
+#pragma unroll
+    for (int r = 0; r < ND; r++) {
+      const int i = i0 + dm_sub * ND + r;
+      if (i >= a.n_dm) continue;
+      const int64_t row = (int64_t)i * a.n_groups + g;
+#pragma unroll
+      for (int m = 0; m < NW; m++) {
+        const int t = t0 + (int)toff + 128 * m;
+        if (t >= a.n_out) continue;
+        if (a.out_u16) {
+          uint16_t* o = static_cast<uint16_t*>(a.out) + row * a.out_pitch + t;
+          if (t + 3 < a.n_out && vec) {
+            uint2 v;
+            v.x = (uint32_t)acc[r][m][0] | ((uint32_t)acc[r][m][1] << 16);
+            v.y = (uint32_t)acc[r][m][2] | ((uint32_t)acc[r][m][3] << 16);
+            *reinterpret_cast<uint2*>(o) = v;
+          } else {
+            for (int q = 0; q < 4 && t + q < a.n_out; q++) o[q] = (uint16_t)acc[r][m][q];
+          }
+        } else {
+          int32_t* o = static_cast<int32_t*>(a.out) + row * a.out_pitch + t;
+          if (t + 3 < a.n_out && vec) {
+            *reinterpret_cast<int4*>(o) = make_int4(acc[r][m][0], acc[r][m][1], acc[r][m][2], acc[r][m][3]);
+          } else {
+            for (int q = 0; q < 4 && t + q < a.n_out; q++) o[q] = acc[r][m][q];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < ND; r++)
+#pragma unroll
+      for (int m = 0; m < NW; m++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[r][m][q] = 0;
+  };
+
   issue(0);
   if (n_chunks > 1) issue(1);
 
   int pending = 0;
   int ch = 0;
+  int gi = 0, cg = 0;  // group and chunk inside it of chunk ch
   for (; ch < n_chunks; ch++) {
     const int st = ch & 1;
-    const int cc = min(cc_max, G - ch * cc_max);
+    const int cc = min(cc_max, G - cg * cc_max);
     if (pending + cc > 256) { fold(); pending = 0; }
     if (!mbar_wait(&bars[st], (ch >> 1) & 1, a.status)) aborted = 1;
     if (!aborted) {
@@ -210,52 +269,18 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb) {
     __syncthreads();
     if (aborted) break;
     if (ch + 2 < n_chunks) issue(ch + 2);
+    if (++cg == chunks_g) {
+      // the group's last chunk: its sums go out while the next chunks land
+      finish_group(g0 + gi);
+      pending = 0;
+      cg = 0;
+      gi++;
+    }
   }
   if (aborted) {
     // let copies already in flight land before the block's shared memory goes away
     if (tid == 0)
       for (int k = ch; k < min(ch + 2, n_chunks); k++) mbar_wait(&bars[k & 1], (k >> 1) & 1, a.status);
-    return;
-  }
-  fold();
-#pragma unroll
-  for (int r = 0; r < ND; r++)
-#pragma unroll
-    for (int m = 0; m < NW; m++) {
-      acc[r][m][0] = (int32_t)((uint32_t)acc[r][m][0] - ((uint32_t)acc[r][m][2] << 16));
-      acc[r][m][1] = (int32_t)((uint32_t)acc[r][m][1] - ((uint32_t)acc[r][m][3] << 16));
-    }
-
-  // Each lane holds 4 consecutive samples per (trial, word).
-  const bool vec = (a.out_pitch & 3) == 0;
-#pragma unroll
-  for (int r = 0; r < ND; r++) {
-    const int i = i0 + dm_sub * ND + r;
-    if (i >= a.n_dm) continue;
-    const int64_t row = (int64_t)i * a.n_groups + g;
-#pragma unroll
-    for (int m = 0; m < NW; m++) {
-      const int t = t0 + (int)toff + 128 * m;
-      if (t >= a.n_out) continue;
-      if (a.out_u16) {
-        uint16_t* o = static_cast<uint16_t*>(a.out) + row * a.out_pitch + t;
-        if (t + 3 < a.n_out && vec) {
-          uint2 v;
-          v.x = (uint32_t)acc[r][m][0] | ((uint32_t)acc[r][m][1] << 16);
-          v.y = (uint32_t)acc[r][m][2] | ((uint32_t)acc[r][m][3] << 16);
-          *reinterpret_cast<uint2*>(o) = v;
-        } else {
-          for (int q = 0; q < 4 && t + q < a.n_out; q++) o[q] = (uint16_t)acc[r][m][q];
-        }
-      } else {
-        int32_t* o = static_cast<int32_t*>(a.out) + row * a.out_pitch + t;
-        if (t + 3 < a.n_out && vec) {
-          *reinterpret_cast<int4*>(o) = make_int4(acc[r][m][0], acc[r][m][1], acc[r][m][2], acc[r][m][3]);
-        } else {
-          for (int q = 0; q < 4 && t + q < a.n_out; q++) o[q] = acc[r][m][q];
-        }
-      }
-    }
   }
 }
 
@@ -302,7 +327,7 @@ __global__ void __launch_bounds__(256) expand_kernel(const uint8_t* x, int64_t p
                  __byte_perm(r[2], r[3], 0x6543), __byte_perm(r[3], r[4], 0x6543));
 }
 
-typedef void (*U8Kernel)(U8PassArgs, int, int, int);
+typedef void (*U8Kernel)(U8PassArgs, int, int, int, int);
 
 template <int ND, int NW>
 constexpr U8Kernel k() { return u8_pass_kernel<ND, NW>; }
@@ -347,9 +372,23 @@ bool u8_config_supported(const sps_dedisp_config& c, std::string* why) {
   return true;
 }
 
-size_t u8_smem_bytes(const sps_dedisp_config& c, int32_t dmax_tile, int32_t group_channels) {
+// Groups one block walks in turn.  In subband step one a block that walks
+// several subbands keeps its stage ring running from one into the next instead
+// of filling it anew (measured on the beam's 32 subbands, batches streamed on
+// two streams: 0.249 ms per two-step search with one group per block, 0.238
+// with four); up to four, while the grid keeps at least 512 blocks (here
+// `tiles` = DM tiles x time tiles).  Brute force has one group.
+int u8_groups_per_block(int32_t n_groups, int64_t tiles) {
+  int g = 1;
+  while (g < 4 && 2 * g <= n_groups && tiles * ((n_groups + 2 * g - 1) / (2 * g)) >= 512) g *= 2;
+  return g;
+}
+
+size_t u8_smem_bytes(const sps_dedisp_config& c, int32_t dmax_tile, int32_t group_channels, int32_t n_groups) {
   const size_t stage = 4 * (size_t)c.chunk * u8_window_bytes(c, dmax_tile) + (size_t)c.chunk * u8_di_pad(c) * 4;
-  return 2 * stage + (((size_t)group_channels * 4 + 15) & ~(size_t)15) + 16;
+  // room for the channel window starts of the most groups a block may walk
+  const size_t b0 = (size_t)std::min<int32_t>(4, std::max<int32_t>(1, n_groups)) * group_channels;
+  return 2 * stage + ((b0 * 4 + 15) & ~(size_t)15) + 16;
 }
 
 sps_status launch_expand(const uint8_t* x, int64_t pitch, int32_t in_len, int32_t channels, uint8_t* x4,
@@ -366,11 +405,14 @@ sps_status launch_u8_pass(const U8PassArgs& a, const sps_dedisp_config& c, cudaS
   U8Kernel fn = find(c.dms_per_thread, c.samples_per_thread / 4);
   const int Di = c.warps_dm * c.dms_per_thread;
   const int Tt = c.warps_time * 32 * c.samples_per_thread;
-  const size_t smem = u8_smem_bytes(c, a.dmax_tile, a.group_channels);
-  dim3 grid((a.n_dm + Di - 1) / Di, (a.n_out + Tt - 1) / Tt, a.n_groups);
+  const size_t smem = u8_smem_bytes(c, a.dmax_tile, a.group_channels, a.n_groups);
+  const int64_t tiles = (int64_t)((a.n_dm + Di - 1) / Di) * ((a.n_out + Tt - 1) / Tt);
+  const int gpb = u8_groups_per_block(a.n_groups, tiles);
+  dim3 grid((a.n_dm + Di - 1) / Di, (a.n_out + Tt - 1) / Tt, (a.n_groups + gpb - 1) / gpb);
   if (grid.y > 65535 || grid.z > 65535) return fail(SPS_ERR_UNSUPPORTED, "too many time tiles or groups");
   SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  fn<<<grid, 32 * c.warps_dm * c.warps_time, smem, st>>>(a, c.warps_dm, c.chunk, u8_window_bytes(c, a.dmax_tile));
+  fn<<<grid, 32 * c.warps_dm * c.warps_time, smem, st>>>(a, c.warps_dm, c.chunk, u8_window_bytes(c, a.dmax_tile),
+                                                          gpb);
   SPS_CUDA(cudaGetLastError());
   return SPS_OK;
 }

@@ -176,7 +176,7 @@ sps_status check_config(const sps_plan* p, const sps_kernel_config& cfg, ConfigC
     const size_t need =
         cfg.brute.presum
             ? presum_smem_bytes(cfg.brute, cached_presum_stage(p, 0, cfg.brute))
-            : u8_smem_bytes(cfg.brute, c.dmax_b, p->channels);
+            : u8_smem_bytes(cfg.brute, c.dmax_b, p->channels, 1);
     if (need > (size_t)p->max_smem)
       return fail(SPS_ERR_INVALID_ARG, "brute config needs more shared memory than a block may use");
   } else {
@@ -199,7 +199,7 @@ sps_status check_config(const sps_plan* p, const sps_kernel_config& cfg, ConfigC
     const size_t need1 =
         cfg.step1.presum
             ? presum_smem_bytes(cfg.step1, cached_presum_stage(p, 1, cfg.step1))
-            : u8_smem_bytes(cfg.step1, c.dmax_1, p->channels / S);
+            : u8_smem_bytes(cfg.step1, c.dmax_1, p->channels / S, S);
     if (need1 > (size_t)p->max_smem)
       return fail(SPS_ERR_INVALID_ARG, "step1 config needs more shared memory than a block may use");
     if (step2_smem_bytes(cfg.step2, c.dmax_2, p->n_subbands) > (size_t)p->max_smem)

@@ -187,7 +187,7 @@ bool verify_presum_tables(const std::vector<int32_t>& d, int32_t rows, int32_t C
 bool u8_config_supported(const sps_dedisp_config& cfg, std::string* why);
 bool step2_config_supported(const sps_dedisp_config& cfg, std::string* why);
 bool snr_config_supported(const sps_snr_config& cfg, std::string* why);
-size_t u8_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile, int32_t group_channels);
+size_t u8_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile, int32_t group_channels, int32_t n_groups);
 int u8_window_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile);
 int u8_di_pad(const sps_dedisp_config& cfg);
 size_t step2_smem_bytes(const sps_dedisp_config& cfg, int32_t dmax_tile, int32_t n_subbands);

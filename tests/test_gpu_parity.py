@@ -316,6 +316,37 @@ def test_subband_small_exact(lib, S):
     assert np.array_equal(oracle.dedisperse(x, p.delay_table(), wl.n_t), Do)
 
 
+@pytest.mark.parametrize("C,S", [(63, 3), (60, 5), (60, 6)])
+def test_subband_step1_blocks_walking_several_subbands(lib, C, S):
+    """Step-one blocks walk several subbands in turn when the grid has tiles to
+    spare (here 16 coarse DMs x about 36 time tiles of 128 samples, so up to four
+    subbands per block); subband counts that leave the last block fewer, and a
+    group of 21 channels whose last chunk holds one, give Y and D equal to the
+    oracle's."""
+    torch = _torch()
+    n_coarse, per = 16, 4
+    dms = synth.dm_grid(n_coarse * per, 1.3)
+    wl = synth.Workload("walk-subbands", C, 1250.0, 1550.0, 81.92e-6, 4096, dms, np.array([1, 2, 4], np.int32),
+                        seed=40 + S, n_subbands=S, coarse_dms=dms[::per].copy())
+    p = lib.Plan.from_workload(wl)
+    c = p.config
+    c.step1 = lib.DedispConfig(1, 4, 1, 1, 4)
+    p.config = c
+    x = _x_for(p, wl, pulses=[synth.Pulse(60.0, 2.0, 25.0, 900.0)])
+    xd = torch.from_numpy(x).cuda()
+    Y = torch.empty(p.y_shape, dtype=torch.uint16, device="cuda")
+    lib.sps_subband_step1(p, xd, Y)
+    D = torch.empty((wl.dms.size, wl.n_t), dtype=torch.int32, device="cuda")
+    lib.sps_subband_step2(p, Y, D)
+    torch.cuda.synchronize()
+    d1, d2 = oracle.subband_tables(wl.f_lo, wl.f_hi, wl.channels, wl.t_samp, S, wl.coarse_dms, wl.dms)
+    n_1, _ = oracle.subband_lengths(wl.n_t, d1, d2)
+    Yo = oracle.subband_step1(x, d1, S, n_1)
+    assert np.array_equal(_to_np(Y)[:, :, :n_1].astype(np.int32), Yo)
+    Do = oracle.subband_step2(Yo, d2, oracle.coarse_index(wl.dms.size, wl.coarse_dms.size), wl.n_t)
+    assert np.array_equal(_to_np(D), Do)
+
+
 @pytest.mark.parametrize("cfg1,cfg2", [
     # pre-summed kernels on 4.7 MHz channels: relative delays vary widely, so small chunks
     ((1, 4, 1, 1, 2, 1), (1, 4, 1, 1, 1)),
