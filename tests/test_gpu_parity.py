@@ -319,18 +319,19 @@ def test_subband_small_exact(lib, S):
 @pytest.mark.parametrize("C,S", [(63, 3), (60, 5), (60, 6)])
 def test_subband_step1_blocks_walking_several_subbands(lib, C, S):
     """Step-one blocks walk several subbands in turn when the grid has tiles to
-    spare (here 16 coarse DMs x about 36 time tiles of 128 samples, so up to four
+    spare (here 16 coarse DMs x about 37 time tiles of 128 samples, so up to four
     subbands per block); subband counts that leave the last block fewer, and a
     group of 21 channels whose last chunk holds one, give Y and D equal to the
-    oracle's."""
+    oracle's (step two on single-trial tiles of 128 samples)."""
     torch = _torch()
     n_coarse, per = 16, 4
     dms = synth.dm_grid(n_coarse * per, 1.3)
-    wl = synth.Workload("walk-subbands", C, 1250.0, 1550.0, 81.92e-6, 4096, dms, np.array([1, 2, 4], np.int32),
+    wl = synth.Workload("walk-subbands", C, 1250.0, 1550.0, 81.92e-6, 4100, dms, np.array([1, 2, 4], np.int32),
                         seed=40 + S, n_subbands=S, coarse_dms=dms[::per].copy())
     p = lib.Plan.from_workload(wl)
     c = p.config
     c.step1 = lib.DedispConfig(1, 4, 1, 1, 4)
+    c.step2 = lib.DedispConfig(1, 4, 1, 1, 2)
     p.config = c
     x = _x_for(p, wl, pulses=[synth.Pulse(60.0, 2.0, 25.0, 900.0)])
     xd = torch.from_numpy(x).cuda()
