@@ -32,6 +32,8 @@
 //   * The offset of (trial, channel) inside the staged windows does not depend
 //     on the time tile (tiles start at multiples of 128), so the plan
 //     precomputes it once per configuration.
+//   * In subband step one a block may walk several groups (subbands) as one
+//     stream of chunks, storing each group's sums while the next chunks land.
 #include <algorithm>
 
 #include "sps_internal.h"

@@ -354,6 +354,30 @@ def test_detect_tie_break():
 
 
 
+
+def test_snr_values_order_like_their_bit_patterns():
+    """The detection compares S/N values by their IEEE-754 bit patterns read as
+    signed 64-bit integers.  That ordering equals the values' own ordering
+    exactly when every value is a finite double >= +0, which the definition
+    guarantees (the peak is never below the mean; a constant series gives 0).
+    Checked on the oracle's S/N of random rows, constant rows and single spikes,
+    and on values one ulp apart."""
+    rng = np.random.default_rng(11)
+    D = rng.integers(0, 391681, size=(40, 300), dtype=np.int64).astype(np.int32)
+    D[3] = 7
+    D[5] = 0
+    D[8, 150] = 391680
+    s, _, _ = oracle.snr(D, [1, 2, 4, 8, 300])
+    v = s.ravel()
+    assert np.all(np.isfinite(v)) and np.all(v >= 0.0) and not np.any(np.signbit(v))
+    k = v.view(np.int64)
+    assert np.array_equal(np.argsort(v, kind="stable"), np.argsort(k, kind="stable"))
+    near = np.array([0.0, 5e-324, 1.0, np.nextafter(1.0, 2.0), 28.97, np.nextafter(28.97, 0.0)])
+    for a in near:
+        for b in near:
+            assert (a > b) == (np.float64(a).view(np.int64) > np.float64(b).view(np.int64))
+
+
 # ----------------------------------------------------------------------------- RFI zapping, downsampling
 def test_zapping_is_linear_in_the_channel_set():
     """Zapped + zapped-only de-dispersions add up to the full one; zapping every
