@@ -8,7 +8,7 @@ is timed on the same batch and reported beside it.
 
 Metric: DM-trial samples per second (n_dms * n_samples per step / step time),
 device time from CUDA events, inputs resident in HBM.  Headline: K steps on
-two streams in turn, eight distinct input batches (210 MB, more than L2)
+--streams streams (four by default) in turn, eight distinct input batches (210 MB, more than L2)
 rotated, events around all K steps.  Breakdown: the same steps on one stream,
 events around each kernel call, L2 flushed (a 256 MiB write) before every
 step outside the events.  `e2e` repeats the metric through the host entry
@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-beam leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the real-time serving leg")
     ap.add_argument("--no-tuning", action="store_true", help="skip the tuning leg")
+    ap.add_argument("--streams", type=int, default=4,
+                    help="streams the headline's (and the streamed two-step path's) batches take in turn")
     return ap.parse_args()
 
 
@@ -336,14 +338,14 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(wl, mode):
+def workload_config(wl, mode, streams=2):
     return {"workload": wl.name, "channels": wl.channels, "band_mhz": [wl.f_lo, wl.f_hi], "t_samp_s": wl.t_samp,
             "samples_per_batch": wl.n_t, "dm_trials": int(wl.dms.size), "dm_step": 0.2,
             "widths": [int(w) for w in wl.widths], "dedispersion": mode,
             "l2": "headline: 8 rotating input batches (210 MB > L2); kernel breakdown: L2 flushed before every "
                   "step (256 MiB write)",
-            "pipeline": "headline: consecutive batches on 2 streams in turn (each batch's full path on its stream, "
-                        "own workspace and outputs); kernel breakdown: one stream, sequential",
+            "pipeline": f"headline: consecutive batches on {streams} streams in turn (each batch's full path on its "
+                        "stream, own workspace and outputs); kernel breakdown: one stream, sequential",
             "parallelism": "replicas (one beam per GPU)"}
 
 
@@ -620,7 +622,7 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        pipe_ms, held = time_pipelined(torch, plan, xs, args.steps, args.warmup)
+        pipe_ms, held = time_pipelined(torch, plan, xs, args.steps, args.warmup, args.streams)
         times = time_path(torch, plan, xs, outs, args.steps, args.warmup, None, flush)
     barrier(world)
     dedisp_ms = [a for a, _ in times]
@@ -662,7 +664,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": workload_config(wl, "brute"),
+            "config": workload_config(wl, "brute", args.streams),
             "kernels_ms": {"dedisperse": dd_ms, "snr_detect": statistics.mean(snr_ms)},
             "kernel_config": plan.config.as_dict(),
             "sequential_ms_per_step": 1e3 * seq_s / args.steps,
@@ -707,9 +709,9 @@ def main():
                            "dedisperse_ms": statistics.mean(a for a, _ in ts),
                            "snr_detect_ms": statistics.mean(b for _, b in ts),
                            "subbands": 32, "coarse_dms": 64}
-        # the same path streamed like the headline (batches on two streams in turn);
+        # the same path streamed like the headline (batches on the headline's streams in turn);
         # each stream's last batch must equal a search of its input on its own
-        sub_pipe_ms, held_s = time_pipelined(torch, ps, xs, args.steps, args.warmup)
+        sub_pipe_ms, held_s = time_pipelined(torch, ps, xs, args.steps, args.warmup, args.streams)
         same = True
         for _, o, xi in held_s:
             r = ps.search(xs[xi])
@@ -717,7 +719,7 @@ def main():
         torch.cuda.synchronize()
         line["subband"]["pipelined"] = {"value": samples * args.steps / (sub_pipe_ms * 1e-3), "unit": UNIT,
                                         "ms_per_step": sub_pipe_ms / args.steps, "outputs_equal_own_search": same,
-                                        "how": "batches on two streams in turn, as the headline"}
+                                        "how": f"batches on {args.streams} streams in turn, as the headline"}
         # roofline of the two steps: the slower of their algorithmic bytes over HBM
         # (x in, Y written and read, D out) and their adds at the derived ALU peak
         n_1 = ps.step1_samples
