@@ -63,7 +63,9 @@ __device__ __forceinline__ void lds_row(uint32_t addr, uint32_t (&w)[NW]) {
   }
 }
 
-template <int ND, int NW>
+// WALK: the block walks gpb > 1 groups in turn (subband step one); without it
+// the block has one group, compiled as a plain loop over its chunks.
+template <int ND, int NW, bool WALK>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb, int gpb) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -116,7 +118,7 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb, int gpb) {
   auto issue = [&](int ch) {
     const int st = ch & 1;
     uint8_t* sb = smem + st * stage_bytes;
-    const int gi = ch / chunks_g, cg = ch - gi * chunks_g;
+    const int gi = WALK ? ch / chunks_g : 0, cg = WALK ? ch - gi * chunks_g : ch;
     const int cb = gi * G + cg * cc_max, cc = min(cc_max, G - cg * cc_max);
     const int npair = (cc + 1) >> 1;
     const uint32_t tbl_bytes = (uint32_t)(npair * a.di_pad * 8);
@@ -228,10 +230,10 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb, int gpb) {
 
   int pending = 0;
   int ch = 0;
-  int gi = 0, cg = 0;  // group and chunk inside it of chunk ch
+  int gi = 0, cg = 0;  // group and chunk inside it of chunk ch (WALK)
   for (; ch < n_chunks; ch++) {
     const int st = ch & 1;
-    const int cc = min(cc_max, G - cg * cc_max);
+    const int cc = min(cc_max, G - (WALK ? cg : ch) * cc_max);
     if (pending + cc > 256) { fold(); pending = 0; }
     if (!mbar_wait(&bars[st], (ch >> 1) & 1, a.status)) aborted = 1;
     if (!aborted) {
@@ -271,19 +273,23 @@ u8_pass_kernel(U8PassArgs a, int wd, int cc_max, int wb, int gpb) {
     __syncthreads();
     if (aborted) break;
     if (ch + 2 < n_chunks) issue(ch + 2);
-    if (++cg == chunks_g) {
-      // the group's last chunk: its sums go out while the next chunks land
-      finish_group(g0 + gi);
-      pending = 0;
-      cg = 0;
-      gi++;
+    if constexpr (WALK) {
+      if (++cg == chunks_g) {
+        // the group's last chunk: its sums go out while the next chunks land
+        finish_group(g0 + gi);
+        pending = 0;
+        cg = 0;
+        gi++;
+      }
     }
   }
   if (aborted) {
     // let copies already in flight land before the block's shared memory goes away
     if (tid == 0)
       for (int k = ch; k < min(ch + 2, n_chunks); k++) mbar_wait(&bars[k & 1], (k >> 1) & 1, a.status);
+    return;
   }
+  if constexpr (!WALK) finish_group(g0);
 }
 
 // Bytes [p, p + 20) of a channel row, zero at and beyond `len`.
@@ -332,19 +338,22 @@ __global__ void __launch_bounds__(256) expand_kernel(const uint8_t* x, int64_t p
 typedef void (*U8Kernel)(U8PassArgs, int, int, int, int);
 
 template <int ND, int NW>
-constexpr U8Kernel k() { return u8_pass_kernel<ND, NW>; }
+constexpr U8Kernel k() { return u8_pass_kernel<ND, NW, false>; }
+template <int ND, int NW>
+constexpr U8Kernel kw() { return u8_pass_kernel<ND, NW, true>; }
 
-struct Variant { int nd, nw; U8Kernel fn; };
+struct Variant { int nd, nw; U8Kernel fn, walk; };
 const Variant kVariants[] = {
-    {1, 1, k<1, 1>()}, {1, 2, k<1, 2>()}, {1, 4, k<1, 4>()}, {1, 8, k<1, 8>()},
-    {2, 1, k<2, 1>()}, {2, 2, k<2, 2>()}, {2, 4, k<2, 4>()}, {2, 8, k<2, 8>()},
-    {4, 1, k<4, 1>()}, {4, 2, k<4, 2>()}, {4, 4, k<4, 4>()},
-    {8, 1, k<8, 1>()}, {8, 2, k<8, 2>()},
+    {1, 1, k<1, 1>(), kw<1, 1>()}, {1, 2, k<1, 2>(), kw<1, 2>()}, {1, 4, k<1, 4>(), kw<1, 4>()},
+    {1, 8, k<1, 8>(), kw<1, 8>()}, {2, 1, k<2, 1>(), kw<2, 1>()}, {2, 2, k<2, 2>(), kw<2, 2>()},
+    {2, 4, k<2, 4>(), kw<2, 4>()}, {2, 8, k<2, 8>(), kw<2, 8>()}, {4, 1, k<4, 1>(), kw<4, 1>()},
+    {4, 2, k<4, 2>(), kw<4, 2>()}, {4, 4, k<4, 4>(), kw<4, 4>()}, {8, 1, k<8, 1>(), kw<8, 1>()},
+    {8, 2, k<8, 2>(), kw<8, 2>()},
 };
 
-U8Kernel find(int nd, int nw) {
+U8Kernel find(int nd, int nw, bool walk = false) {
   for (const Variant& v : kVariants)
-    if (v.nd == nd && v.nw == nw) return v.fn;
+    if (v.nd == nd && v.nw == nw) return walk ? v.walk : v.fn;
   return nullptr;
 }
 
@@ -404,12 +413,12 @@ sps_status launch_expand(const uint8_t* x, int64_t pitch, int32_t in_len, int32_
 sps_status launch_u8_pass(const U8PassArgs& a, const sps_dedisp_config& c, cudaStream_t st) {
   std::string why;
   if (!u8_config_supported(c, &why)) return fail(SPS_ERR_INVALID_ARG, why);
-  U8Kernel fn = find(c.dms_per_thread, c.samples_per_thread / 4);
   const int Di = c.warps_dm * c.dms_per_thread;
   const int Tt = c.warps_time * 32 * c.samples_per_thread;
   const size_t smem = u8_smem_bytes(c, a.dmax_tile, a.group_channels, a.n_groups);
   const int64_t tiles = (int64_t)((a.n_dm + Di - 1) / Di) * ((a.n_out + Tt - 1) / Tt);
   const int gpb = u8_groups_per_block(a.n_groups, tiles);
+  U8Kernel fn = find(c.dms_per_thread, c.samples_per_thread / 4, gpb > 1);
   dim3 grid((a.n_dm + Di - 1) / Di, (a.n_out + Tt - 1) / Tt, (a.n_groups + gpb - 1) / gpb);
   if (grid.y > 65535 || grid.z > 65535) return fail(SPS_ERR_UNSUPPORTED, "too many time tiles or groups");
   SPS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
