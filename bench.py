@@ -732,6 +732,16 @@ def main():
             "bound": "alu" if sb_adds / (peak_tadd * 1e12) > sb_bytes / (hbm_gbs * 1e9) else "hbm",
             "algorithmic_bytes_per_launch": sb_bytes, "algorithmic_adds_per_launch": sb_adds,
             "roofline_ms": 1e3 * t_roof, "ms_per_launch": sb_ms, "frac": 1e3 * t_roof / sb_ms}
+        # the two steps against their own bound, the shared-memory data path: step one
+        # reads one staged byte per channel-sample add (four samples per 32-bit load),
+        # step two two bytes per (trial, subband, sample) (uint16 subband series)
+        sb_shared = float(wls.coarse_dms.size) * wls.channels * n_1 + 2.0 * wls.dms.size * 32 * wls.n_t
+        line["kernel_rooflines"]["subband_shared"] = {
+            "bound": "shared", "algorithmic_shared_bytes_per_launch": sb_shared, "ms_per_launch": sb_ms,
+            "achieved_tbs": sb_shared / (sb_ms * 1e-3) / 1e12, "peak_tbs": shared_peak,
+            "frac": sb_shared / (sb_ms * 1e-3) / 1e12 / shared_peak,
+            "peak_derivation": "152 SMs x 128 B/clk x 2070 MHz",
+            "note": "time of the three launches (shifted copies, step one, step two)"}
 
     # ---- the batched-beam, serving and tuning workloads (rank 0 of a single-GPU run)
     if world == 1 and args.dms == 2048:
