@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-beam leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the real-time serving leg")
     ap.add_argument("--no-tuning", action="store_true", help="skip the tuning leg")
+    ap.add_argument("--e2e-threads", type=int, default=12,
+                    help="host threads taking the end-to-end leg's steps in turn")
     ap.add_argument("--streams", type=int, default=4,
                     help="streams the headline's (and the streamed two-step path's) batches take in turn")
     return ap.parse_args()
@@ -774,13 +776,14 @@ def main():
         if s >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
     e2e_seq = max_over_ranks(sum(e2e_t), world, dev)
-    e2e_total = max_over_ranks(e2e_pipelined(torch, plan, xh, args.steps, args.warmup, dev), world, dev)
+    e2e_total = max_over_ranks(e2e_pipelined(torch, plan, xh, args.steps, args.warmup, dev, args.e2e_threads),
+                               world, dev)
     line["e2e"] = {"value": world * samples * args.steps / e2e_total, "unit": UNIT,
                    "h2d_bytes_per_step": wl.channels * pitch,
                    "d2h_bytes_per_step": int(hs.numel() * 8 + ht.numel() * 4 + hv.numel() * 4 + 16),
                    "ms_per_step": 1e3 * e2e_total / args.steps,
-                   "how": "sps_search_host on 8 host threads taking steps in turn (own stream and buffers each); "
-                          "every step copies its pinned batch in and its S/N tables and detection out",
+                   "how": f"sps_search_host on {args.e2e_threads} host threads taking steps in turn (own stream and "
+                          "buffers each); every step copies its pinned batch in and its S/N tables and detection out",
                    "sequential_ms_per_step": 1e3 * e2e_seq / args.steps}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1); its
