@@ -333,14 +333,14 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": workload_config(wl, "brute"),
+            "data": "synthetic", "config": workload_config(wl, "brute", args.streams),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
                              "cpu": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def workload_config(wl, mode, streams=2):
+def workload_config(wl, mode, streams):
     return {"workload": wl.name, "channels": wl.channels, "band_mhz": [wl.f_lo, wl.f_hi], "t_samp_s": wl.t_samp,
             "samples_per_batch": wl.n_t, "dm_trials": int(wl.dms.size), "dm_step": 0.2,
             "widths": [int(w) for w in wl.widths], "dedispersion": mode,
